@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Throughput of the CAPT configuration query on GB300 (one JSON line on rank 0).
+
+Workload (timed): the tabletop scene (30,000 surface points, Morton-order filter at
+1 cm, CAPT with r_min = 0.02, r_max = 0.08) and 1,048,576 configurations per GPU of a
+7-joint arm with 60 spheres; one step = one capt_query_configs over all of them, the
+centres (755 MB, larger than L2) already in HBM.  Metric: sphere queries per second
+(configurations x 60 / time; a configuration stops at its first colliding sphere).
+Also reported: the same through the host-buffer entry point (e2e), edges validated per
+second (4,096 edges, persistent graph launch vs one launch per edge), the roofline of
+the query kernel and the oracle timed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--all]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "sphere-vs-cloud CAPT queries/sec (configuration queries, flags bit-exact)"
+UNIT = "sphere queries/s"
+SPHERES = 60
+R_MIN, R_MAX, R_FILTER = 0.02, 0.08, 0.01
+SM_MAX_MHZ = 2070.0
+# DRAM bytes (read + write) per launch of the configuration-query kernel from an ncu
+# capture, keyed by the hash of the kernel source it was taken on (null when stale).
+TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--configs", type=int, default=1 << 20, help="configurations per GPU")
+    ap.add_argument("--all", action="store_true", help="also time the clearance and the other clouds")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, v in zip(names, r[5:9]):
+                    if v.strip() == "Active":
+                        reasons.add(k)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def src_hash(*names):
+    h = hashlib.sha256()
+    for n in names:
+        h.update(open(os.path.join(ROOT, "paper_2406_02807_gb300", "csrc", n), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def tabletop_tree(capt):
+    raw, _, arm = W.tabletop_scene(1001)
+    t0 = time.perf_counter()
+    kept = capt.sfc_filter(raw, R_FILTER)
+    filt_ms = (time.perf_counter() - t0) * 1e3
+    pts = raw[kept]
+    t0 = time.perf_counter()
+    tree1 = capt.capt_build_threads(pts, R_MIN, R_MAX, 1)
+    build1_ms = (time.perf_counter() - t0) * 1e3
+    del tree1
+    tree = capt.capt_build(pts, R_MIN, R_MAX)
+    st = capt.capt_stats(tree)
+    return raw, pts, arm, tree, dict(filter_ms=round(filt_ms, 3), build_ms_1thread=round(build1_ms, 3),
+                                     build_ms=round(st["build_ms"], 3), build_threads=st["build_threads"],
+                                     n_points=int(st["n_points"]), n_leaves=int(st["n_leaves"]),
+                                     mean_set=round(st["total_afforded"] / st["n_leaves"], 2),
+                                     max_set=int(st["max_set"]))
+
+
+def time_events(torch, fn, steps, stream):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def cpu_baseline(pts, arm, sample_cfgs):
+    """The oracle as it stands: FP32 brute force on all host cores, plus its plain CAPT
+    single-threaded (the paper's setting: one CPU thread)."""
+    import oracle
+    cores = oracle.default_threads()
+    cen = W.fk_centers(arm, W.random_configs(sample_cfgs, 1001))
+    t0 = time.perf_counter()
+    oracle.brute_config_flags(pts, cen, arm.sphere_radius, threads=cores)
+    dt = time.perf_counter() - t0
+    ot = oracle.PlainCAPT(pts, R_MIN, R_MAX)
+    cen2 = W.fk_centers(arm, W.random_configs(16 * sample_cfgs, 1001))
+    t0 = time.perf_counter()
+    _, counts = ot.query_configs(cen2, arm.sphere_radius)
+    dt2 = time.perf_counter() - t0
+    return {"value": sample_cfgs * SPHERES / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP32 brute force over all {len(pts)} points for the first {sample_cfgs} configurations "
+                      f"of the workload, {cores} threads",
+            "plain_capt_1thread": {"ns_per_sphere_query_examined": dt2 * 1e9 / max(int(counts[0]), 1),
+                                   "sphere_queries_per_s": 16 * sample_cfgs * SPHERES / dt2,
+                                   "sample": f"{16 * sample_cfgs} configurations, 1 thread"}}
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm: each step is a bounded sample of the workload."""
+    if rank != 0:
+        return
+    import oracle
+    raw, _, arm = W.tabletop_scene(1001)
+    kept = oracle.sfc_filter(raw, R_FILTER)
+    pts = raw[kept]
+    sample = 1024
+    cores = oracle.default_threads()
+    cen = W.fk_centers(arm, W.random_configs(sample, 1001))
+    for _ in range(args.warmup):
+        oracle.brute_config_flags(pts, cen, arm.sphere_radius, threads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.brute_config_flags(pts, cen, arm.sphere_radius, threads=cores)
+    dt = (time.perf_counter() - t0) / args.steps
+    v = sample * SPHERES / dt
+    print(json.dumps({
+        "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "reference",
+        "config": {"workload": "tabletop_configs", "n_points": int(len(pts)), "spheres_per_config": SPHERES,
+                   "configs_per_step": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"first {sample} configurations per step, FP32 brute force, {cores} threads"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    import paper_2406_02807_gb300 as capt
+    capt.build()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    raw, pts, arm, tree, host = tabletop_tree(capt)
+    capt.capt_upload(tree, local)
+    C = args.configs
+    q = W.random_configs(C, 1001, first=rank * C)
+    cen_host = torch.from_numpy(W.fk_centers(arm, q)).pin_memory()
+    del q
+    cen = cen_host.to(dev, non_blocking=False)
+    r_host = torch.from_numpy(arm.sphere_radius.copy())
+    r = r_host.to(dev)
+    flags = torch.empty(C, dtype=torch.uint8, device=dev)
+
+    tuned, tuned_ms = capt.capt_autotune_configs(tree, cen, r, flags)
+    counts = capt.capt_count_config_work(tree, cen, r).cpu().numpy().astype(np.int64)
+    L = capt.capt_stats(tree)["depth"]
+    ops_per_launch = int(counts[0]) * (L + 15) + int(counts[2]) * 9
+    bytes_per_launch = int(counts[0]) * (12 + 32 + 4 * L) + int(counts[2]) * 12
+
+    def step():
+        capt.capt_query_configs(tree, cen, r, flags)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    ms = time_events(torch, step, args.steps, stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if pg:
+        pg.barrier()
+        tt = torch.tensor([ms], device=dev)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * C * SPHERES / (ms / 1e3)
+    collide = float(flags.float().mean().item())
+
+    # end to end through the host-buffer entry point (copies inside the timed region)
+    h_flags = torch.empty(C, dtype=torch.uint8).pin_memory()
+    capt.capt_query_configs_host(tree, cen_host, r_host, h_flags)
+    e2e_steps = max(1, min(args.steps, 10))
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        capt.capt_query_configs_host(tree, cen_host, r_host, h_flags)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if pg:
+        tt = torch.tensor([e2e_s], device=dev)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_ok = bool(torch.equal(h_flags, flags.cpu()))
+
+    # batched edge validation: persistent graph launch vs one launch per edge
+    qa, qb, ns = W.random_edges(4096, 1002)
+    dqa, dqb, dns = (torch.from_numpy(a).to(dev) for a in (qa, qb, ns))
+    valid = torch.empty(4096, dtype=torch.uint8, device=dev)
+    plan = capt.capt_edge_plan_create(tree, arm, dqa, dqb, dns, valid)
+    ecfg, _ = capt.capt_edge_plan_info(plan)
+    for _ in range(3):
+        capt.capt_edge_plan_launch(plan)
+    edge_ms = time_events(torch, lambda: capt.capt_edge_plan_launch(plan), max(args.steps, 5), stream)
+    v_plan = valid.clone()
+    valid2 = torch.empty_like(valid)
+    capt.capt_set_launch_cfg(tree, capt.CAPT_KERNEL_EDGES, ecfg["warps_per_block"], ecfg["spheres_per_lane"],
+                             0, ecfg["chunk"])
+    capt.capt_validate_edges(tree, arm, dqa, dqb, dns, valid2, mode=capt.CAPT_EDGES_PER_EDGE)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    per_edge_steps = 3
+    for _ in range(per_edge_steps):
+        capt.capt_validate_edges(tree, arm, dqa, dqb, dns, valid2, mode=capt.CAPT_EDGES_PER_EDGE)
+    torch.cuda.synchronize()
+    per_edge_ms = (time.perf_counter() - t0) * 1e3 / per_edge_steps
+    edges_equal = bool(torch.equal(v_plan, valid2))
+
+    out = None
+    if rank == 0:
+        props = torch.cuda.get_device_properties(dev)
+        sms = props.multi_processor_count
+        peak_tops = sms * 128 * SM_MAX_MHZ * 1e6 / 1e12
+        achieved = ops_per_launch / (ms / 1e3) / 1e12
+        h = src_hash("kernels_query.cu", "device_common.cuh")
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "tabletop_configs", "cloud": f"30,000-point tabletop, Morton filter at 1 cm -> "
+                                                                f"{len(pts)} points", "configs_per_gpu": C,
+                       "spheres_per_config": SPHERES, "r_min": R_MIN, "r_max": R_MAX,
+                       "l2": "inputs larger than L2 (755 MB of centres per step); the tree stays resident by design",
+                       "parallelism": f"replicas x{world}, configurations sharded by rank", "launch_cfg": tuned},
+            "ns_per_sphere_query": 1e9 / value * world,
+            "configs_per_s": world * C / (ms / 1e3),
+            "collision_fraction": collide,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "TFLOP/s",
+                         "frac": achieved / peak_tops, "traffic": TRAFFIC.get(h),
+                         "peak_basis": f"{sms} SMs x 128 FP32 lanes x {SM_MAX_MHZ:.0f} MHz (no FMA on this path)",
+                         "ops_per_launch": ops_per_launch,
+                         "work": {"spheres_examined": int(counts[0]), "box_pass": int(counts[1]),
+                                  "points_scanned": int(counts[2]), "depth": L},
+                         "l1_bytes_per_launch": bytes_per_launch,
+                         "l1_frac": bytes_per_launch / (ms / 1e3) / (sms * 128 * SM_MAX_MHZ * 1e6)},
+            "e2e": {"value": world * C * SPHERES / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": C * SPHERES * 12 + SPHERES * 4, "d2h_bytes_per_step": C,
+                    "flags_equal_device_path": e2e_ok},
+            "edges": {"edges": 4096, "configs": int(ns.sum()), "persistent_graph_ms": edge_ms,
+                      "edges_per_s_persistent": 4096 / (edge_ms / 1e3), "per_edge_launch_ms": per_edge_ms,
+                      "edges_per_s_per_edge": 4096 / (per_edge_ms / 1e3), "valid_fraction": float(valid2.float().mean()),
+                      "equal_results": edges_equal, "launch_cfg": ecfg},
+            "host": host,
+            "gpu_launches": args.steps,
+            "clocks": clk,
+        }
+        if args.all:
+            out["extra"] = extra_workloads(capt, torch, dev, stream, pts, arm, args)
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(pts, arm, 2048)
+        print(json.dumps(out), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+def extra_workloads(capt, torch, dev, stream, pts, arm, args):
+    res = {}
+    # clearance forward and forward + backward (16,384 trajectories x 32 waypoints x 60 spheres)
+    ctree = capt.capt_build(pts, 0.0, R_MAX)
+    capt.capt_upload(ctree, dev.index)
+    T, Wn = 16384, 32
+    q = W.random_trajectories(T, Wn, 1003)
+    c = torch.from_numpy(W.fk_centers(arm, q.reshape(-1, 7)).reshape(T, Wn, SPHERES, 3)).to(dev)
+    r = torch.from_numpy(arm.sphere_radius.copy()).to(dev)
+    g = torch.ones(T, device=dev)
+    cost, d, am = capt.capt_clearance_fwd(ctree, c, r, 0.01)
+    fwd_ms = time_events(torch, lambda: capt.capt_clearance_fwd(ctree, c, r, 0.01, cost, d, am), 10, stream)
+    grad = torch.empty_like(c)
+    bwd_ms = time_events(torch, lambda: capt.capt_clearance_bwd(ctree, c, r, d, am, g, 0.01, grad), 10, stream)
+    m = T * Wn * SPHERES
+    res["clearance"] = {"spheres": m, "fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "fwd_spheres_per_s": m / (fwd_ms / 1e3),
+                        "fwd_bwd_spheres_per_s": m / ((fwd_ms + bwd_ms) / 1e3),
+                        "bwd_hbm_GBps": m * (12 + 4 + 4 + 12 + 12) / (bwd_ms / 1e3) / 1e9}
+    # uniform 2k cloud, 100,000 spheres
+    pu = W.uniform_cloud(2000, 1000)
+    cu, ru = W.cube_queries(100_000, 1000)
+    tu = capt.capt_build(pu, 0.01, 0.08)
+    capt.capt_upload(tu, dev.index)
+    dc, dr = torch.from_numpy(cu).to(dev), torch.from_numpy(ru).to(dev)
+    fl = torch.empty(100_000, dtype=torch.uint8, device=dev)
+    ms = time_events(torch, lambda: capt.capt_query_spheres(tu, dc, dr, fl), 20, stream)
+    res["uniform2k"] = {"spheres": 100_000, "ms": ms, "sphere_queries_per_s": 1e5 / (ms / 1e3)}
+    # room: 200,000 points, 4,194,304 spheres
+    pr = W.room_cloud(1004)
+    t0 = time.perf_counter()
+    tr = capt.capt_build(pr, 0.02, 0.10)
+    bms = (time.perf_counter() - t0) * 1e3
+    capt.capt_upload(tr, dev.index)
+    st = capt.capt_stats(tr)
+    cr, rr = W.room_queries(1 << 22, 1004)
+    dc, dr = torch.from_numpy(cr).to(dev), torch.from_numpy(rr).to(dev)
+    fl = torch.empty(1 << 22, dtype=torch.uint8, device=dev)
+    ms = time_events(torch, lambda: capt.capt_query_spheres(tr, dc, dr, fl), 10, stream)
+    res["room200k"] = {"spheres": 1 << 22, "ms": ms, "sphere_queries_per_s": (1 << 22) / (ms / 1e3),
+                       "build_ms": bms, "tree_device_bytes": int(st["device_bytes"]),
+                       "total_afforded": int(st["total_afforded"]), "max_set": int(st["max_set"])}
+    return res
+
+
+if __name__ == "__main__":
+    main()

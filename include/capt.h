@@ -1,0 +1,283 @@
+/*
+ * capt.h - C ABI of the GB300 collision-affording point tree (CAPT) library.
+ *
+ * The CAPT (Ramsey, Kingston, Thomason, Kavraki, 2024) answers "does a sphere of
+ * radius r in [r_min, r_max] centred at x touch any point of a cloud?" exactly
+ * (Lemma 1, Sec. V-B) with a fixed-length descent of an Eytzinger-ordered split
+ * sequence T to a leaf cell (Alg. 3, Sec. IV-D), a test against that leaf's
+ * bounding box A_i, and a scan of the leaf's affordance set P_i.
+ *
+ * Conventions for every entry point:
+ *  - Every call returns a capt_status (0 = CAPT_OK, negative = error) and never throws.
+ *    capt_last_error() gives a message for the calling thread's last error.
+ *  - "host" pointers are CPU memory; "device" pointers are CUDA device memory on the
+ *    device the tree was uploaded to (for example a torch tensor's data_ptr()).
+ *  - Inputs are caller-owned and never retained after the call returns (for device
+ *    inputs: after the work queued on the stream has finished).  Outputs go to
+ *    caller-owned buffers.  The tree owns its own copies of everything.
+ *  - Device calls are asynchronous and stream-ordered on `stream` (a cudaStream_t; NULL
+ *    is the legacy default stream).  Errors found while queueing are returned; errors
+ *    found by a kernel (a bounded wait that gave up) are latched in the tree's device
+ *    status word, read by capt_device_status().
+ *  - Queries assume r_min <= r <= r_max (Lemma 1's hypothesis).  Outside that range
+ *    the flag is unspecified (it is still computed, never faults).  Non-finite
+ *    centres give unspecified flags and never fault.
+ *  - All floating-point work on the query path is FP32 with every operation rounded
+ *    separately (no fused multiply-add): the flag of a sphere is exactly the FP32
+ *    brute-force predicate ((x0-p0)^2 + (x1-p1)^2) + (x2-p2)^2 <= fl(r*r).
+ */
+#ifndef CAPT_H
+#define CAPT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum capt_status {
+    CAPT_OK = 0,
+    CAPT_E_ARG = -1,        /* null pointer, bad size or bad enum value */
+    CAPT_E_RANGE = -2,      /* r_min > r_max, negative or non-finite radius bound */
+    CAPT_E_NONFINITE = -3,  /* NaN or infinity in an input point cloud */
+    CAPT_E_NOMEM = -4,      /* host or device allocation failed */
+    CAPT_E_CUDA = -5,       /* a CUDA runtime call failed (see capt_last_error) */
+    CAPT_E_TIMEOUT = -6,    /* a bounded device wait gave up (from capt_device_status) */
+    CAPT_E_BOUNDS = -7,     /* a device-side index check failed (debug builds) */
+    CAPT_E_STATE = -8       /* tree not uploaded, used on another device, or pruned
+                               tree given to the clearance calls */
+} capt_status;
+
+/* Opaque tree: host arrays plus, after capt_upload, its device layout. */
+typedef struct capt_tree capt_tree;
+
+typedef struct capt_tree_stats {
+    uint64_t n_points;        /* real points n */
+    uint64_t n_leaves;        /* N = 2^L >= max(n, 1), pads at +inf fill N - n leaves */
+    uint32_t depth;           /* L, the fixed descent length */
+    uint32_t max_set;         /* largest affordance set |P_i| */
+    uint64_t total_afforded;  /* sum over leaves of |P_i| */
+    uint64_t total_blocks;    /* 4-point blocks in the device point buffer */
+    uint64_t pruned_leaves;   /* leaves that kept {t} only (r_min condition, Alg. 1) */
+    uint64_t empty_leaves;    /* leaves with |P_i| = 0 */
+    uint64_t device_bytes;    /* bytes of the device layout (0 before upload) */
+    double build_ms;          /* wall time of capt_build */
+    float r_min, r_max;
+    int32_t device;           /* CUDA ordinal after upload, else -1 */
+    int32_t build_threads;
+} capt_tree_stats;
+
+/* ---------------------------------------------------------------------------------
+ * Host side (no GPU needed)
+ * --------------------------------------------------------------------------------- */
+
+/* Build a CAPT from n points (Alg. 1, Sec. IV-A/B).
+ * points: host float[n][3] (x, y, z), copied.  n = 0 is allowed (every query misses).
+ * r_min, r_max: the query radius range; 0 <= r_min <= r_max, both finite.  r_min > 0
+ *   enables the prune of Alg. 1 (a leaf whose whole cell is within r_min of its
+ *   representative stores that point only); r_min = 0 disables it, which the clearance
+ *   calls require.
+ * Splits cycle x, y, z; each split is the median by (coordinate, point index); a
+ * point is afforded by a cell iff its FP64 distance to the closed cell is at most
+ * r_max (1 + 1e-5); sets are stored in ascending point index.
+ * Errors: CAPT_E_ARG (out == NULL, points == NULL with n > 0, n >= 2^31),
+ *         CAPT_E_RANGE, CAPT_E_NONFINITE, CAPT_E_NOMEM. */
+int capt_build(const float* points, size_t n, float r_min, float r_max, capt_tree** out);
+
+/* capt_build with an explicit number of host threads (0 = hardware concurrency,
+ * 1 = single-threaded).  The result does not depend on the thread count. */
+int capt_build_threads(const float* points, size_t n, float r_min, float r_max, int n_threads,
+                       capt_tree** out);
+
+/* Space-filling-curve filter (Alg. 2, Sec. IV-C).  For each of the 6 axis
+ * permutations (xyz, xzy, yxz, yzx, zxy, zyx) the surviving points are ordered along
+ * a Z-order curve (21 bits per axis over the input's bounding box, the permutation's
+ * first axis most significant, ties by point index) and a point is kept iff its FP32
+ * squared distance to the last kept point exceeds fl(min_spacing^2).
+ * points: host float[n][3]; kept_idx: host uint32[n] (caller-owned) receives the kept
+ * indices in the last pass's curve order; *n_out their count.
+ * Errors: CAPT_E_ARG, CAPT_E_RANGE (min_spacing < 0 or NaN), CAPT_E_NONFINITE, CAPT_E_NOMEM. */
+int sfc_filter(const float* points, size_t n, float min_spacing, uint32_t* kept_idx, size_t* n_out);
+
+/* Statistics of a tree (host memory).  Errors: CAPT_E_ARG. */
+int capt_stats(const capt_tree* t, capt_tree_stats* out);
+
+/* Copy the host arrays of the tree (any output may be NULL):
+ * T: float[N-1] split values in Eytzinger order; set_begin: uint64[N+1] offsets;
+ * set_idx: uint32[total_afforded] point indices; aabb: float[N][6] (lo xyz, hi xyz;
+ * +inf/-inf for an empty set).  Errors: CAPT_E_ARG. */
+int capt_export(const capt_tree* t, float* T, uint64_t* set_begin, uint32_t* set_idx, float* aabb);
+
+/* Free host and device memory of the tree and any plan-independent scratch.  NULL-safe.
+ * The caller must make sure no queued work still uses the tree. */
+void capt_free(capt_tree* t);
+
+/* Message for the last non-OK status returned on the calling thread ("" if none). */
+const char* capt_last_error(void);
+
+/* ---------------------------------------------------------------------------------
+ * Device side
+ * --------------------------------------------------------------------------------- */
+
+/* Copy the tree to device `device` (stream-ordered on `stream`; the host arrays stay).
+ * Device layout (all 256-byte aligned):
+ *   T      float[N-1 rounded up to 4]  split values (Eytzinger)
+ *   leaves 32-byte records {lo.xyz, first block, hi.xyz, count} per leaf
+ *   blocks float4[3 * total_blocks]: each set starts at a block of 4 points stored as
+ *          {x0..x3}{y0..y3}{z0..z3}; unused slots hold +inf
+ *   ids    uint32[4 * total_blocks] point index per slot (0xffffffff in unused slots)
+ *   cloud  float[n][3] the input points (for the clearance gradient)
+ * Calling it again re-uploads.  Errors: CAPT_E_ARG, CAPT_E_CUDA, CAPT_E_NOMEM. */
+int capt_upload(capt_tree* t, int device, void* stream);
+
+/* One flag per sphere (Alg. 3).  d_centers: device float[m][3]; d_radii: device
+ * float[m]; d_flags: device uint8[m] receives 1 = collides, 0 = free.  m = 0 is a
+ * no-op.  Errors: CAPT_E_ARG, CAPT_E_STATE, CAPT_E_CUDA. */
+int capt_query_spheres(const capt_tree* t, const float* d_centers, const float* d_radii, size_t m,
+                       uint8_t* d_flags, void* stream);
+
+/* One flag per configuration of S spheres: 1 iff any sphere collides (Sec. IV-D; a
+ * configuration stops being checked at its first colliding sphere).
+ * d_centers: device float[C][S][3]; d_radii: device float[S] (sphere s of every
+ * configuration has radius d_radii[s]); d_flags: device uint8[C].  1 <= S <= 64.
+ * Errors: CAPT_E_ARG, CAPT_E_STATE, CAPT_E_CUDA. */
+int capt_query_configs(const capt_tree* t, const float* d_centers, const float* d_radii, size_t C, int S,
+                       uint8_t* d_flags, void* stream);
+
+/* capt_query_configs from HOST memory: h_centers float[C][S][3] and h_radii float[S]
+ * are copied to the device in chunks that overlap with the queries of the previous
+ * chunk; the flags come back to h_flags uint8[C].  The call returns when h_flags is
+ * complete (it synchronises).  Page-locked host buffers give the copy/compute overlap;
+ * pageable ones work but copy synchronously.  The first call allocates two chunk
+ * buffers on the device, kept by the tree.  Errors as capt_query_configs, CAPT_E_NOMEM. */
+int capt_query_configs_host(capt_tree* t, const float* h_centers, const float* h_radii, size_t C, int S,
+                            uint8_t* h_flags, void* stream);
+
+/* Algorithmic work of capt_query_configs as the sequential Alg. 3 defines it, summed
+ * over the C configurations (for roofline accounting): d_counts device uint64[3]
+ * receives += [spheres examined (up to and including each configuration's first hit),
+ * spheres whose box test passed, affordance points scanned (up to and including the
+ * first hit in stored order)].  The caller zeroes d_counts.  Errors as capt_query_configs. */
+int capt_count_config_work(const capt_tree* t, const float* d_centers, const float* d_radii, size_t C, int S,
+                           uint64_t* d_counts, void* stream);
+
+/* Leaf index i - (N - 1) reached by the descent of Alg. 3 for each centre.
+ * d_centers device float[m][3]; d_leaves device uint32[m].  Diagnostics. */
+int capt_query_leaves(const capt_tree* t, const float* d_centers, size_t m, uint32_t* d_leaves, void* stream);
+
+/* Read and clear the device status word (synchronises `stream`): CAPT_OK, or the
+ * latched CAPT_E_TIMEOUT / CAPT_E_BOUNDS.  Errors: CAPT_E_ARG, CAPT_E_STATE, CAPT_E_CUDA. */
+int capt_device_status(const capt_tree* t, void* stream);
+
+/* ---------------------------------------------------------------------------------
+ * Launch configuration and autotuning
+ * --------------------------------------------------------------------------------- */
+
+enum { CAPT_STAGE_GLOBAL = 0, /* T read through L1/L2 */
+       CAPT_STAGE_SMEM = 1    /* the top levels of T copied to shared memory by a bulk
+                                 asynchronous (TMA) copy at block start */ };
+enum { CAPT_KERNEL_SPHERES = 0, CAPT_KERNEL_CONFIGS = 1, CAPT_KERNEL_EDGES = 2, CAPT_KERNEL_CLEARANCE = 3 };
+
+typedef struct capt_launch_cfg {
+    int32_t warps_per_block;   /* 1..16 */
+    int32_t spheres_per_lane;  /* sphere slots per lane: 1, 2 or 4 (configurations and
+                                  edges: 2 or 4, whole configurations per warp pass) */
+    int32_t staging;           /* CAPT_STAGE_* */
+    int32_t chunk;             /* edges: configurations per work item (1..1024) */
+} capt_launch_cfg;
+
+/* Set / get the launch configuration used for `kernel` on this tree.
+ * Errors: CAPT_E_ARG (unsupported value). */
+int capt_set_launch_cfg(capt_tree* t, int kernel, const capt_launch_cfg* cfg);
+int capt_get_launch_cfg(const capt_tree* t, int kernel, capt_launch_cfg* cfg);
+
+/* Time every supported configuration of the configuration-query kernel on these
+ * inputs (CUDA events on `stream`), keep the fastest on the tree and return it.
+ * d_flags is overwritten.  best_ms may be NULL.  Synchronises `stream`. */
+int capt_autotune_configs(capt_tree* t, const float* d_centers, const float* d_radii, size_t C, int S,
+                          uint8_t* d_flags, void* stream, capt_launch_cfg* best, float* best_ms);
+
+/* ---------------------------------------------------------------------------------
+ * Batched edge validation
+ * --------------------------------------------------------------------------------- */
+
+#define CAPT_MAX_JOINTS 16
+#define CAPT_MAX_SPHERES 64
+
+/* A serial arm made of spheres.  Joint j rotates its frame about local axis axis[j]
+ * (0 = x, 1 = y, 2 = z) by q_j, then the frame origin moves by link[j] expressed in
+ * the rotated frame.  Sphere s belongs to link sphere_link[s]: its centre is the
+ * origin of that link (before the link's translation) plus R * sphere_offset[s], with
+ * R the rotation after joint sphere_link[s].  All FP32; sin and cos are the library's
+ * own Cody-Waite-reduced Taylor polynomials, so results do not depend on libm. */
+typedef struct capt_arm {
+    int32_t n_joints;                          /* 1..CAPT_MAX_JOINTS */
+    int32_t n_spheres;                         /* 1..CAPT_MAX_SPHERES */
+    float base[3];
+    int32_t axis[CAPT_MAX_JOINTS];
+    float link[CAPT_MAX_JOINTS][3];
+    int32_t sphere_link[CAPT_MAX_SPHERES];
+    float sphere_offset[CAPT_MAX_SPHERES][3];
+    float sphere_radius[CAPT_MAX_SPHERES];
+} capt_arm;
+
+enum { CAPT_EDGES_PERSISTENT = 0, /* one persistent launch over (edge, chunk) work items */
+       CAPT_EDGES_PER_EDGE = 1    /* one launch per edge (baseline) */ };
+
+/* Validate E straight joint-space edges: edge e holds the n_e configurations
+ * q_k = q_a + (k / (n_e - 1)) (q_b - q_a), k = 0..n_e-1 (q_a alone when n_e = 1), and
+ * is valid iff none of them collides (Sec. IV-D early termination; an edge stops being
+ * checked once one configuration collides).  n_e <= 0 means no configuration: valid.
+ * d_qa, d_qb: device float[E][n_joints]; d_nsteps: device int32[E];
+ * d_valid: device uint8[E] receives 1 = valid, 0 = collides.
+ * arm: host pointer, copied.  mode: CAPT_EDGES_*.  CAPT_EDGES_PER_EDGE reads d_nsteps
+ * back to the host (it synchronises `stream` once).  Uses scratch owned by the tree.
+ * Errors: CAPT_E_ARG, CAPT_E_STATE, CAPT_E_CUDA, CAPT_E_NOMEM. */
+int capt_validate_edges(capt_tree* t, const capt_arm* arm, const float* d_qa, const float* d_qb,
+                        const int32_t* d_nsteps, size_t E, uint8_t* d_valid, int mode, void* stream);
+
+/* A captured CUDA graph of the persistent edge validator for fixed buffers: one
+ * capt_edge_plan_launch replays {work-counter reset, per-edge prefix of work items,
+ * persistent kernel} with a single cudaGraphLaunch.  cfg = NULL autotunes the
+ * launch configuration (warps per block, spheres per lane, staging, chunk) on the given
+ * inputs first, which runs the validator several times on `stream`.  The plan owns
+ * its scratch; buffers must outlive it.  Errors as capt_validate_edges. */
+typedef struct capt_edge_plan capt_edge_plan;
+int capt_edge_plan_create(capt_tree* t, const capt_arm* arm, const float* d_qa, const float* d_qb,
+                          const int32_t* d_nsteps, size_t E, uint8_t* d_valid, const capt_launch_cfg* cfg,
+                          void* stream, capt_edge_plan** out);
+int capt_edge_plan_launch(capt_edge_plan* p, void* stream);
+/* The plan's launch configuration and, when it was autotuned, the best time (else 0). */
+int capt_edge_plan_info(const capt_edge_plan* p, capt_launch_cfg* cfg, float* tuned_ms);
+void capt_edge_plan_free(capt_edge_plan* p);
+
+/* ---------------------------------------------------------------------------------
+ * Differentiable clearance (tree built with r_min = 0)
+ * --------------------------------------------------------------------------------- */
+
+/* Forward: for T trajectories x W waypoints x S spheres,
+ *   d = min(||c - p*||, r_max) with p* the nearest cloud point: exact whenever the
+ *       nearest point is within r_max, because every such point is in the leaf's set
+ *       (Lemma 1, case 1); the distance is sqrt of the FP32 squared distance;
+ *   cost_t = sum over its W*S spheres of max(0, r_s + margin - d)^2.
+ * d_centers device float[T][W][S][3]; d_radii device float[S]; d_cost device
+ * float[T]; d_dist device float[T*W*S]; d_argmin device int32[T*W*S] receives the
+ * index of p* (lowest index among FP32 ties), or -1 where d = r_max.  1 <= S <= 64,
+ * 1 <= W.  The cost sums in a fixed order (bitwise reproducible).
+ * Errors: CAPT_E_ARG, CAPT_E_STATE (r_min > 0 or not uploaded), CAPT_E_CUDA. */
+int capt_clearance_fwd(const capt_tree* t, const float* d_centers, const float* d_radii, size_t T, int W, int S,
+                       float margin, float* d_cost, float* d_dist, int32_t* d_argmin, void* stream);
+
+/* Backward: d_grad_centers[t,w,s,:] = g_t * (-2 h) * (c - p*) / d with
+ * h = max(0, r_s + margin - d), when h > 0, d < r_max and d > 0; else 0.
+ * d_grad_cost device float[T] (g).  Other arguments as in the forward, whose d_dist and
+ * d_argmin it reads.  Errors as capt_clearance_fwd. */
+int capt_clearance_bwd(const capt_tree* t, const float* d_centers, const float* d_radii, const float* d_dist,
+                       const int32_t* d_argmin, const float* d_grad_cost, size_t T, int W, int S, float margin,
+                       float* d_grad_centers, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CAPT_H */

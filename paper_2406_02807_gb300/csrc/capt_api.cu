@@ -1,0 +1,661 @@
+// C ABI of the CAPT library: argument checking, tree lifecycle, upload, dispatch to
+// the kernels, the host-buffer pipeline, the autotuner and CUDA-graph edge plans.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/capt.h"
+#include "capt_internal.h"
+#include "kernels.h"
+
+using capt::DevArgs;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(CAPT_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(call, what)                        \
+    do {                                            \
+        cudaError_t _e = (call);                    \
+        if (_e != cudaSuccess) return cuda_fail(_e, what); \
+    } while (0)
+
+// Restores the caller's current device when it goes out of scope.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (dev >= 0 && dev != prev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool valid_cfg(int kernel, const capt_launch_cfg& c) {
+    if (c.warps_per_block < 1 || c.warps_per_block > 16) return false;
+    if (c.staging != CAPT_STAGE_GLOBAL && c.staging != CAPT_STAGE_SMEM) return false;
+    if (kernel == CAPT_KERNEL_SPHERES) return c.spheres_per_lane == 1 || c.spheres_per_lane == 2 || c.spheres_per_lane == 4;
+    if (kernel == CAPT_KERNEL_CONFIGS || kernel == CAPT_KERNEL_EDGES)
+        return (c.spheres_per_lane == 2 || c.spheres_per_lane == 4) && (kernel != CAPT_KERNEL_EDGES || (c.chunk >= 1 && c.chunk <= 1024));
+    if (kernel == CAPT_KERNEL_CLEARANCE) return true;
+    return false;
+}
+
+}  // namespace
+
+struct capt_tree {
+    capt::HostTree h;
+    int device = -1;
+    void* d_T = nullptr;
+    void* d_leaves = nullptr;
+    void* d_blocks = nullptr;
+    void* d_ids = nullptr;
+    void* d_cloud = nullptr;
+    int* d_status = nullptr;
+    uint64_t total_blocks = 0;
+    size_t dev_bytes = 0;
+    capt_launch_cfg cfg[4];
+    // host-buffer pipeline
+    float* d_pipe_c[2] = {nullptr, nullptr};
+    uint8_t* d_pipe_f[2] = {nullptr, nullptr};
+    size_t pipe_cap = 0;   // floats per centre buffer
+    cudaStream_t pipe_stream = nullptr;
+    cudaEvent_t pipe_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // edge validation scratch (persistent mode without a plan)
+    uint32_t* d_edge_scratch = nullptr;
+    size_t edge_scratch_cap = 0;
+    std::mutex mu;
+
+    capt_tree() {
+        cfg[CAPT_KERNEL_SPHERES] = {8, 2, CAPT_STAGE_SMEM, 0};
+        cfg[CAPT_KERNEL_CONFIGS] = {8, 2, CAPT_STAGE_SMEM, 0};
+        cfg[CAPT_KERNEL_EDGES] = {8, 2, CAPT_STAGE_SMEM, 32};
+        cfg[CAPT_KERNEL_CLEARANCE] = {8, 2, CAPT_STAGE_SMEM, 0};
+    }
+
+    DevArgs args() const {
+        DevArgs a;
+        a.T = static_cast<const float*>(d_T);
+        a.leaves = static_cast<const capt::LeafRec*>(d_leaves);
+        a.blocks = static_cast<const float*>(d_blocks);
+        a.ids = static_cast<const uint32_t*>(d_ids);
+        a.cloud = static_cast<const float*>(d_cloud);
+        a.status = d_status;
+        a.N = (uint32_t)h.N;
+        a.L = h.L;
+        a.r_min = h.r_min;
+        a.r_max = h.r_max;
+        return a;
+    }
+
+    void free_device() {
+        if (device < 0) return;
+        DeviceGuard g(device);
+        for (void* p : {d_T, d_leaves, d_blocks, d_ids, d_cloud, (void*)d_status, (void*)d_pipe_c[0], (void*)d_pipe_c[1],
+                        (void*)d_pipe_f[0], (void*)d_pipe_f[1], (void*)d_edge_scratch})
+            if (p) cudaFree(p);
+        for (auto& e : pipe_ev)
+            if (e) cudaEventDestroy(e);
+        if (pipe_stream) cudaStreamDestroy(pipe_stream);
+        d_T = d_leaves = d_blocks = d_ids = d_cloud = nullptr;
+        d_status = nullptr;
+        d_pipe_c[0] = d_pipe_c[1] = nullptr;
+        d_pipe_f[0] = d_pipe_f[1] = nullptr;
+        d_edge_scratch = nullptr;
+        for (auto& e : pipe_ev) e = nullptr;
+        pipe_stream = nullptr;
+        pipe_cap = 0;
+        edge_scratch_cap = 0;
+        dev_bytes = 0;
+        device = -1;
+    }
+};
+
+namespace {
+
+// The tree must be uploaded and the caller's current device must be the tree's.
+int check_ready(const capt_tree* t) {
+    if (!t) return fail(CAPT_E_ARG, "tree is NULL");
+    if (t->device < 0) return fail(CAPT_E_STATE, "tree is not uploaded (call capt_upload)");
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != t->device)
+        return fail(CAPT_E_STATE, "current CUDA device differs from the tree's device");
+    return CAPT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* capt_last_error(void) { return g_err.c_str(); }
+
+int capt_build_threads(const float* points, size_t n, float r_min, float r_max, int n_threads, capt_tree** out) {
+    if (!out) return fail(CAPT_E_ARG, "out is NULL");
+    *out = nullptr;
+    capt_tree* t = nullptr;
+    try {
+        t = new capt_tree();
+    } catch (...) {
+        return fail(CAPT_E_NOMEM, "host allocation failed");
+    }
+    std::string err;
+    int rc = capt::build_host_tree(points, n, r_min, r_max, n_threads, t->h, err);
+    if (rc != CAPT_OK) {
+        delete t;
+        return fail(rc, err);
+    }
+    *out = t;
+    return CAPT_OK;
+}
+
+int capt_build(const float* points, size_t n, float r_min, float r_max, capt_tree** out) {
+    return capt_build_threads(points, n, r_min, r_max, 0, out);
+}
+
+int sfc_filter(const float* points, size_t n, float min_spacing, uint32_t* kept_idx, size_t* n_out) {
+    std::string err;
+    int rc = capt::host_sfc_filter(points, n, min_spacing, kept_idx, n_out, err);
+    return rc == CAPT_OK ? rc : fail(rc, err);
+}
+
+int capt_stats(const capt_tree* t, capt_tree_stats* s) {
+    if (!t || !s) return fail(CAPT_E_ARG, "NULL argument");
+    std::memset(s, 0, sizeof(*s));
+    const auto& h = t->h;
+    s->n_points = h.n;
+    s->n_leaves = h.N;
+    s->depth = (uint32_t)h.L;
+    s->total_afforded = h.set_idx.size();
+    uint64_t blocks = 0, mx = 0, pr = 0, em = 0;
+    for (size_t l = 0; l < h.N; l++) {
+        uint64_t c = h.set_begin[l + 1] - h.set_begin[l];
+        blocks += (c + 3) / 4;
+        mx = std::max(mx, c);
+        pr += h.pruned[l];
+        em += c == 0;
+    }
+    s->total_blocks = blocks;
+    s->max_set = (uint32_t)mx;
+    s->pruned_leaves = pr;
+    s->empty_leaves = em;
+    s->device_bytes = t->dev_bytes;
+    s->build_ms = h.build_ms;
+    s->r_min = h.r_min;
+    s->r_max = h.r_max;
+    s->device = t->device;
+    s->build_threads = h.build_threads;
+    return CAPT_OK;
+}
+
+int capt_export(const capt_tree* t, float* T, uint64_t* set_begin, uint32_t* set_idx, float* aabb) {
+    if (!t) return fail(CAPT_E_ARG, "tree is NULL");
+    const auto& h = t->h;
+    if (T && !h.T.empty()) std::memcpy(T, h.T.data(), h.T.size() * sizeof(float));
+    if (set_begin) std::memcpy(set_begin, h.set_begin.data(), h.set_begin.size() * sizeof(uint64_t));
+    if (set_idx && !h.set_idx.empty()) std::memcpy(set_idx, h.set_idx.data(), h.set_idx.size() * sizeof(uint32_t));
+    if (aabb) std::memcpy(aabb, h.aabb.data(), h.aabb.size() * sizeof(float));
+    return CAPT_OK;
+}
+
+void capt_free(capt_tree* t) {
+    if (!t) return;
+    t->free_device();
+    delete t;
+}
+
+int capt_upload(capt_tree* t, int device, void* stream) {
+    if (!t) return fail(CAPT_E_ARG, "tree is NULL");
+    int ndev = 0;
+    CUDA_TRY(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(CAPT_E_ARG, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(t->mu);
+    t->free_device();
+    DeviceGuard g(device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    capt::Layout lay;
+    try {
+        capt::flatten(t->h, lay);
+    } catch (const std::bad_alloc&) {
+        return fail(CAPT_E_NOMEM, "host allocation failed while flattening");
+    }
+    const auto& h = t->h;
+    const size_t nT = std::max<size_t>(4, ((h.T.size() + 3) / 4) * 4);
+    const size_t sz_T = nT * sizeof(float);
+    const size_t sz_leaves = lay.leaves.size() * sizeof(capt::LeafRec);
+    const size_t sz_blocks = lay.blocks.size() * sizeof(float);
+    const size_t sz_ids = lay.ids.size() * sizeof(uint32_t);
+    const size_t sz_cloud = std::max<size_t>(1, h.pts.size()) * sizeof(float);
+    t->device = device;   // from here on free_device() releases what was allocated
+    auto alloc = [&](void** p, size_t bytes, const char* what) -> int {
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            t->free_device();
+            return fail(e == cudaErrorMemoryAllocation ? CAPT_E_NOMEM : CAPT_E_CUDA,
+                        std::string("cudaMalloc ") + what + ": " + cudaGetErrorString(e));
+        }
+        return CAPT_OK;
+    };
+    int rc;
+    if ((rc = alloc(&t->d_T, sz_T, "T")) || (rc = alloc(&t->d_leaves, sz_leaves, "leaves")) ||
+        (rc = alloc(&t->d_blocks, sz_blocks, "blocks")) || (rc = alloc(&t->d_ids, sz_ids, "ids")) ||
+        (rc = alloc(&t->d_cloud, sz_cloud, "cloud")) || (rc = alloc((void**)&t->d_status, 256, "status")))
+        return rc;
+    std::vector<float> Tpad(nT, INFINITY);
+    std::copy(h.T.begin(), h.T.end(), Tpad.begin());
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t->d_T, Tpad.data(), sz_T, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t->d_leaves, lay.leaves.data(), sz_leaves, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t->d_blocks, lay.blocks.data(), sz_blocks, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t->d_ids, lay.ids.data(), sz_ids, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !h.pts.empty())
+        e = cudaMemcpyAsync(t->d_cloud, h.pts.data(), h.pts.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(t->d_status, 0, 256, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // the staging vectors die here
+    if (e != cudaSuccess) {
+        t->free_device();
+        return cuda_fail(e, "upload");
+    }
+    t->total_blocks = lay.total_blocks;
+    t->dev_bytes = sz_T + sz_leaves + sz_blocks + sz_ids + sz_cloud + 256;
+    return CAPT_OK;
+}
+
+int capt_query_spheres(const capt_tree* t, const float* d_centers, const float* d_radii, size_t m, uint8_t* d_flags,
+                       void* stream) {
+    int rc = check_ready(t);
+    if (rc) return rc;
+    if (m == 0) return CAPT_OK;
+    if (!d_centers || !d_radii || !d_flags) return fail(CAPT_E_ARG, "NULL device pointer");
+    std::string err;
+    rc = capt::launch_query(t->args(), capt::kModeSpheres, d_centers, d_radii, m, 1, d_flags,
+                            t->cfg[CAPT_KERNEL_SPHERES], static_cast<cudaStream_t>(stream), err);
+    return rc ? fail(rc, err) : CAPT_OK;
+}
+
+int capt_query_configs(const capt_tree* t, const float* d_centers, const float* d_radii, size_t C, int S,
+                       uint8_t* d_flags, void* stream) {
+    int rc = check_ready(t);
+    if (rc) return rc;
+    if (S < 1 || S > CAPT_MAX_SPHERES) return fail(CAPT_E_ARG, "S must be in [1, 64]");
+    if (C == 0) return CAPT_OK;
+    if (!d_centers || !d_radii || !d_flags) return fail(CAPT_E_ARG, "NULL device pointer");
+    std::string err;
+    rc = capt::launch_query(t->args(), capt::kModeConfigs, d_centers, d_radii, C, S, d_flags,
+                            t->cfg[CAPT_KERNEL_CONFIGS], static_cast<cudaStream_t>(stream), err);
+    return rc ? fail(rc, err) : CAPT_OK;
+}
+
+int capt_query_configs_host(capt_tree* t, const float* h_centers, const float* h_radii, size_t C, int S,
+                            uint8_t* h_flags, void* stream) {
+    int rc = check_ready(t);
+    if (rc) return rc;
+    if (S < 1 || S > CAPT_MAX_SPHERES) return fail(CAPT_E_ARG, "S must be in [1, 64]");
+    if (C == 0) return CAPT_OK;
+    if (!h_centers || !h_radii || !h_flags) return fail(CAPT_E_ARG, "NULL host pointer");
+    std::lock_guard<std::mutex> lk(t->mu);
+    cudaStream_t user = static_cast<cudaStream_t>(stream);
+    // chunk: 64 Ki configurations (about 47 MB of centres for S = 60)
+    const size_t chunk = std::min<size_t>(C, 65536);
+    const size_t cfloats = chunk * (size_t)S * 3;
+    if (t->pipe_cap < cfloats + 64) {
+        for (int i = 0; i < 2; i++) {
+            if (t->d_pipe_c[i]) cudaFree(t->d_pipe_c[i]);
+            if (t->d_pipe_f[i]) cudaFree(t->d_pipe_f[i]);
+            t->d_pipe_c[i] = nullptr;
+            t->d_pipe_f[i] = nullptr;
+        }
+        t->pipe_cap = 0;
+        for (int i = 0; i < 2; i++) {
+            if (cudaMalloc((void**)&t->d_pipe_c[i], (cfloats + 64) * sizeof(float)) != cudaSuccess ||
+                cudaMalloc((void**)&t->d_pipe_f[i], chunk + 256) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(CAPT_E_NOMEM, "cudaMalloc of the host-pipeline buffers failed");
+            }
+        }
+        t->pipe_cap = cfloats + 64;
+        if (!t->pipe_stream) CUDA_TRY(cudaStreamCreateWithFlags(&t->pipe_stream, cudaStreamNonBlocking), "stream");
+        for (auto& e : t->pipe_ev)
+            if (!e) CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+    }
+    // radii live in the tail of buffer 0's slack (S <= 64 floats)
+    float* d_r = t->d_pipe_c[0] + cfloats;
+    cudaStream_t cp = t->pipe_stream;
+    // the copies start after the caller's queued work
+    CUDA_TRY(cudaEventRecord(t->pipe_ev[2], user), "event record");
+    CUDA_TRY(cudaStreamWaitEvent(cp, t->pipe_ev[2], 0), "wait");
+    CUDA_TRY(cudaMemcpyAsync(d_r, h_radii, (size_t)S * sizeof(float), cudaMemcpyHostToDevice, cp), "radii H2D");
+    const size_t nchunks = (C + chunk - 1) / chunk;
+    std::string err;
+    for (size_t k = 0; k < nchunks; k++) {
+        const int b = (int)(k & 1);
+        const size_t c0 = k * chunk, cn = std::min(chunk, C - c0);
+        if (k >= 2) CUDA_TRY(cudaStreamWaitEvent(cp, t->pipe_ev[b], 0), "wait compute");   // buffer b free again
+        CUDA_TRY(cudaMemcpyAsync(t->d_pipe_c[b], h_centers + c0 * (size_t)S * 3, cn * (size_t)S * 3 * sizeof(float),
+                                 cudaMemcpyHostToDevice, cp),
+                 "centres H2D");
+        CUDA_TRY(cudaEventRecord(t->pipe_ev[3], cp), "event record");
+        CUDA_TRY(cudaStreamWaitEvent(user, t->pipe_ev[3], 0), "wait copy");
+        rc = capt::launch_query(t->args(), capt::kModeConfigs, t->d_pipe_c[b], d_r, cn, S, t->d_pipe_f[b],
+                                t->cfg[CAPT_KERNEL_CONFIGS], user, err);
+        if (rc) return fail(rc, err);
+        CUDA_TRY(cudaMemcpyAsync(h_flags + c0, t->d_pipe_f[b], cn, cudaMemcpyDeviceToHost, user), "flags D2H");
+        CUDA_TRY(cudaEventRecord(t->pipe_ev[b], user), "event record");
+    }
+    CUDA_TRY(cudaStreamSynchronize(user), "synchronize");
+    return CAPT_OK;
+}
+
+int capt_count_config_work(const capt_tree* t, const float* d_centers, const float* d_radii, size_t C, int S,
+                           uint64_t* d_counts, void* stream) {
+    int rc = check_ready(t);
+    if (rc) return rc;
+    if (S < 1 || S > CAPT_MAX_SPHERES) return fail(CAPT_E_ARG, "S must be in [1, 64]");
+    if (C == 0) return CAPT_OK;
+    if (!d_centers || !d_radii || !d_counts) return fail(CAPT_E_ARG, "NULL device pointer");
+    std::string err;
+    rc = capt::launch_count_configs(t->args(), d_centers, d_radii, C, S, d_counts, static_cast<cudaStream_t>(stream), err);
+    return rc ? fail(rc, err) : CAPT_OK;
+}
+
+int capt_query_leaves(const capt_tree* t, const float* d_centers, size_t m, uint32_t* d_leaves, void* stream) {
+    int rc = check_ready(t);
+    if (rc) return rc;
+    if (m == 0) return CAPT_OK;
+    if (!d_centers || !d_leaves) return fail(CAPT_E_ARG, "NULL device pointer");
+    std::string err;
+    rc = capt::launch_leaves(t->args(), d_centers, m, d_leaves, static_cast<cudaStream_t>(stream), err);
+    return rc ? fail(rc, err) : CAPT_OK;
+}
+
+int capt_device_status(const capt_tree* t, void* stream) {
+    int rc = check_ready(t);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int word = 0;
+    CUDA_TRY(cudaMemcpyAsync(&word, t->d_status, sizeof(int), cudaMemcpyDeviceToHost, st), "status D2H");
+    CUDA_TRY(cudaMemsetAsync(t->d_status, 0, sizeof(int), st), "status clear");
+    CUDA_TRY(cudaStreamSynchronize(st), "synchronize");
+    if (word & 1) return fail(CAPT_E_TIMEOUT, "a bounded device wait gave up");
+    if (word & 2) return fail(CAPT_E_BOUNDS, "a device-side index check failed");
+    return CAPT_OK;
+}
+
+int capt_set_launch_cfg(capt_tree* t, int kernel, const capt_launch_cfg* cfg) {
+    if (!t || !cfg || kernel < 0 || kernel > 3) return fail(CAPT_E_ARG, "bad argument");
+    if (!valid_cfg(kernel, *cfg)) return fail(CAPT_E_ARG, "unsupported launch configuration");
+    t->cfg[kernel] = *cfg;
+    return CAPT_OK;
+}
+
+int capt_get_launch_cfg(const capt_tree* t, int kernel, capt_launch_cfg* cfg) {
+    if (!t || !cfg || kernel < 0 || kernel > 3) return fail(CAPT_E_ARG, "bad argument");
+    *cfg = t->cfg[kernel];
+    return CAPT_OK;
+}
+
+int capt_autotune_configs(capt_tree* t, const float* d_centers, const float* d_radii, size_t C, int S,
+                          uint8_t* d_flags, void* stream, capt_launch_cfg* best, float* best_ms) {
+    int rc = check_ready(t);
+    if (rc) return rc;
+    if (S < 1 || S > CAPT_MAX_SPHERES || C == 0) return fail(CAPT_E_ARG, "need C > 0 and S in [1, 64]");
+    if (!d_centers || !d_radii || !d_flags) return fail(CAPT_E_ARG, "NULL device pointer");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0), "event");
+    CUDA_TRY(cudaEventCreate(&e1), "event");
+    float best_t = INFINITY;
+    capt_launch_cfg best_c = t->cfg[CAPT_KERNEL_CONFIGS];
+    std::string err;
+    for (int warps : {4, 8, 16})
+        for (int spl : {2, 4})
+            for (int stage : {CAPT_STAGE_GLOBAL, CAPT_STAGE_SMEM}) {
+                capt_launch_cfg c = {warps, spl, stage, 0};
+                float tt = INFINITY;
+                for (int rep = 0; rep < 3; rep++) {
+                    cudaEventRecord(e0, st);
+                    rc = capt::launch_query(t->args(), capt::kModeConfigs, d_centers, d_radii, C, S, d_flags, c, st, err);
+                    cudaEventRecord(e1, st);
+                    if (rc) break;
+                    if (cudaEventSynchronize(e1) != cudaSuccess) { rc = CAPT_E_CUDA; break; }
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0) tt = std::min(tt, ms);
+                }
+                if (rc) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return fail(rc, err.empty() ? "autotune failed" : err);
+                }
+                if (tt < best_t) { best_t = tt; best_c = c; }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    t->cfg[CAPT_KERNEL_CONFIGS] = best_c;
+    if (best) *best = best_c;
+    if (best_ms) *best_ms = best_t;
+    return CAPT_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------
+// Edges and clearance entry points
+// ------------------------------------------------------------------------------------
+namespace {
+
+int check_arm(const capt_arm* arm) {
+    if (!arm) return fail(CAPT_E_ARG, "arm is NULL");
+    if (arm->n_joints < 1 || arm->n_joints > CAPT_MAX_JOINTS) return fail(CAPT_E_ARG, "n_joints must be in [1, 16]");
+    if (arm->n_spheres < 1 || arm->n_spheres > CAPT_MAX_SPHERES) return fail(CAPT_E_ARG, "n_spheres must be in [1, 64]");
+    for (int j = 0; j < arm->n_joints; j++)
+        if (arm->axis[j] < 0 || arm->axis[j] > 2) return fail(CAPT_E_ARG, "joint axis must be 0, 1 or 2");
+    for (int s = 0; s < arm->n_spheres; s++)
+        if (arm->sphere_link[s] < 0 || arm->sphere_link[s] >= arm->n_joints)
+            return fail(CAPT_E_ARG, "sphere_link out of range");
+    return CAPT_OK;
+}
+
+}  // namespace
+
+struct capt_edge_plan {
+    capt_tree* tree = nullptr;
+    int device = -1;
+    uint32_t* d_scratch = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    capt_launch_cfg cfg{};
+    float tuned_ms = 0.f;
+};
+
+extern "C" {
+
+int capt_validate_edges(capt_tree* t, const capt_arm* arm, const float* d_qa, const float* d_qb,
+                        const int32_t* d_nsteps, size_t E, uint8_t* d_valid, int mode, void* stream) {
+    int rc = check_ready(t);
+    if (rc) return rc;
+    if ((rc = check_arm(arm))) return rc;
+    if (mode != CAPT_EDGES_PERSISTENT && mode != CAPT_EDGES_PER_EDGE) return fail(CAPT_E_ARG, "unknown mode");
+    if (E == 0) return CAPT_OK;
+    if (!d_qa || !d_qb || !d_nsteps || !d_valid) return fail(CAPT_E_ARG, "NULL device pointer");
+    if (E >= (size_t(1) << 31)) return fail(CAPT_E_ARG, "too many edges");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::string err;
+    if (mode == CAPT_EDGES_PER_EDGE) {
+        std::vector<int32_t> ns(E);
+        CUDA_TRY(cudaMemcpyAsync(ns.data(), d_nsteps, E * sizeof(int32_t), cudaMemcpyDeviceToHost, st), "nsteps D2H");
+        CUDA_TRY(cudaStreamSynchronize(st), "synchronize");
+        rc = capt::launch_edges_per_edge(t->args(), *arm, d_qa, d_qb, ns.data(), E, d_valid, t->cfg[CAPT_KERNEL_EDGES],
+                                         st, err);
+        return rc ? fail(rc, err) : CAPT_OK;
+    }
+    std::lock_guard<std::mutex> lk(t->mu);
+    const size_t words = capt::edge_scratch_words(E);
+    if (t->edge_scratch_cap < words) {
+        if (t->d_edge_scratch) cudaFree(t->d_edge_scratch);
+        t->d_edge_scratch = nullptr;
+        t->edge_scratch_cap = 0;
+        if (cudaMalloc((void**)&t->d_edge_scratch, words * sizeof(uint32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(CAPT_E_NOMEM, "cudaMalloc of the edge scratch failed");
+        }
+        t->edge_scratch_cap = words;
+    }
+    rc = capt::launch_edges_persistent(t->args(), *arm, d_qa, d_qb, d_nsteps, E, d_valid, t->d_edge_scratch,
+                                       t->cfg[CAPT_KERNEL_EDGES], st, err);
+    return rc ? fail(rc, err) : CAPT_OK;
+}
+
+void capt_edge_plan_free(capt_edge_plan* p) {
+    if (!p) return;
+    DeviceGuard g(p->device);
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->d_scratch) cudaFree(p->d_scratch);
+    delete p;
+}
+
+int capt_edge_plan_create(capt_tree* t, const capt_arm* arm, const float* d_qa, const float* d_qb,
+                          const int32_t* d_nsteps, size_t E, uint8_t* d_valid, const capt_launch_cfg* cfg,
+                          void* stream, capt_edge_plan** out) {
+    if (!out) return fail(CAPT_E_ARG, "out is NULL");
+    *out = nullptr;
+    int rc = check_ready(t);
+    if (rc) return rc;
+    if ((rc = check_arm(arm))) return rc;
+    if (E == 0 || !d_qa || !d_qb || !d_nsteps || !d_valid) return fail(CAPT_E_ARG, "need E > 0 and device buffers");
+    if (E >= (size_t(1) << 31)) return fail(CAPT_E_ARG, "too many edges");
+    if (cfg && !valid_cfg(CAPT_KERNEL_EDGES, *cfg)) return fail(CAPT_E_ARG, "unsupported launch configuration");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    capt_edge_plan* p = new (std::nothrow) capt_edge_plan();
+    if (!p) return fail(CAPT_E_NOMEM, "host allocation failed");
+    p->tree = t;
+    p->device = t->device;
+    const size_t words = capt::edge_scratch_words(E);
+    if (cudaMalloc((void**)&p->d_scratch, words * sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return fail(CAPT_E_NOMEM, "cudaMalloc of the plan scratch failed");
+    }
+    std::string err;
+    const DevArgs a = t->args();
+    if (cfg) {
+        p->cfg = *cfg;
+    } else {
+        // autotune: warps per block x spheres per lane x staging x chunk
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best = INFINITY;
+        capt_launch_cfg bc = t->cfg[CAPT_KERNEL_EDGES];
+        for (int warps : {4, 8, 16})
+            for (int spl : {2, 4})
+                for (int stage : {CAPT_STAGE_GLOBAL, CAPT_STAGE_SMEM})
+                    for (int chunk : {8, 32}) {
+                        capt_launch_cfg c = {warps, spl, stage, chunk};
+                        float tt = INFINITY;
+                        for (int rep = 0; rep < 3 && !rc; rep++) {
+                            cudaEventRecord(e0, st);
+                            rc = capt::launch_edges_persistent(a, *arm, d_qa, d_qb, d_nsteps, E, d_valid, p->d_scratch,
+                                                               c, st, err);
+                            cudaEventRecord(e1, st);
+                            if (!rc && cudaEventSynchronize(e1) != cudaSuccess) { rc = CAPT_E_CUDA; err = "autotune sync"; }
+                            float ms = 0;
+                            cudaEventElapsedTime(&ms, e0, e1);
+                            if (rep > 0) tt = std::min(tt, ms);
+                        }
+                        if (rc) break;
+                        if (tt < best) { best = tt; bc = c; }
+                    }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rc) {
+            capt_edge_plan_free(p);
+            return fail(rc, err);
+        }
+        p->cfg = bc;
+        p->tuned_ms = best;
+    }
+    // capture {reset, prefix, persistent kernel} into a graph on a private stream
+    cudaStream_t cap = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        rc = capt::launch_edges_persistent(a, *arm, d_qa, d_qb, d_nsteps, E, d_valid, p->d_scratch, p->cfg, cap, err);
+        cudaError_t e2 = cudaStreamEndCapture(cap, &p->graph);
+        if (!rc && e2 != cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess && !rc) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+    if (cap) cudaStreamDestroy(cap);
+    if (e != cudaSuccess || rc) {
+        capt_edge_plan_free(p);
+        return rc ? fail(rc, err) : cuda_fail(e, "edge plan capture");
+    }
+    *out = p;
+    return CAPT_OK;
+}
+
+int capt_edge_plan_launch(capt_edge_plan* p, void* stream) {
+    if (!p || !p->exec) return fail(CAPT_E_ARG, "plan is NULL");
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != p->device)
+        return fail(CAPT_E_STATE, "current CUDA device differs from the plan's device");
+    CUDA_TRY(cudaGraphLaunch(p->exec, static_cast<cudaStream_t>(stream)), "cudaGraphLaunch");
+    return CAPT_OK;
+}
+
+int capt_edge_plan_info(const capt_edge_plan* p, capt_launch_cfg* cfg, float* tuned_ms) {
+    if (!p) return fail(CAPT_E_ARG, "plan is NULL");
+    if (cfg) *cfg = p->cfg;
+    if (tuned_ms) *tuned_ms = p->tuned_ms;
+    return CAPT_OK;
+}
+
+int capt_clearance_fwd(const capt_tree* t, const float* d_centers, const float* d_radii, size_t T, int W, int S,
+                       float margin, float* d_cost, float* d_dist, int32_t* d_argmin, void* stream) {
+    int rc = check_ready(t);
+    if (rc) return rc;
+    if (t->h.r_min != 0.f) return fail(CAPT_E_STATE, "clearance needs a tree built with r_min = 0 (no prune)");
+    if (S < 1 || S > CAPT_MAX_SPHERES || W < 1) return fail(CAPT_E_ARG, "need 1 <= S <= 64 and W >= 1");
+    if (!std::isfinite(margin)) return fail(CAPT_E_ARG, "margin must be finite");
+    if (T == 0) return CAPT_OK;
+    if (!d_centers || !d_radii || !d_cost || !d_dist || !d_argmin) return fail(CAPT_E_ARG, "NULL device pointer");
+    std::string err;
+    rc = capt::launch_clearance_fwd(t->args(), d_centers, d_radii, T, W, S, margin, d_cost, d_dist, d_argmin,
+                                    t->cfg[CAPT_KERNEL_CLEARANCE], static_cast<cudaStream_t>(stream), err);
+    return rc ? fail(rc, err) : CAPT_OK;
+}
+
+int capt_clearance_bwd(const capt_tree* t, const float* d_centers, const float* d_radii, const float* d_dist,
+                       const int32_t* d_argmin, const float* d_grad_cost, size_t T, int W, int S, float margin,
+                       float* d_grad_centers, void* stream) {
+    int rc = check_ready(t);
+    if (rc) return rc;
+    if (t->h.r_min != 0.f) return fail(CAPT_E_STATE, "clearance needs a tree built with r_min = 0 (no prune)");
+    if (S < 1 || S > CAPT_MAX_SPHERES || W < 1) return fail(CAPT_E_ARG, "need 1 <= S <= 64 and W >= 1");
+    if (T == 0) return CAPT_OK;
+    if (!d_centers || !d_radii || !d_dist || !d_argmin || !d_grad_cost || !d_grad_centers)
+        return fail(CAPT_E_ARG, "NULL device pointer");
+    std::string err;
+    rc = capt::launch_clearance_bwd(t->args(), d_centers, d_radii, d_dist, d_argmin, d_grad_cost, T, W, S, margin,
+                                    d_grad_centers, static_cast<cudaStream_t>(stream), err);
+    return rc ? fail(rc, err) : CAPT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,158 @@
+// Device helpers shared by the CAPT kernels (sm_103a).
+//
+// Every floating-point expression on the query path uses the explicitly rounded
+// intrinsics (__fadd_rn, __fsub_rn, __fmul_rn): nvcc never fuses them into an FMA, so
+// a kernel computes exactly the FP32 predicate ((x0-p0)^2 + (x1-p1)^2) + (x2-p2)^2 <=
+// fl(r*r) that defines a collision.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "capt_internal.h"
+
+namespace capt {
+
+// Device status bits (latched by kernels, read by capt_device_status).
+constexpr int kStatusTimeout = 1;
+constexpr int kStatusBounds = 2;
+
+// Largest prefix of T staged into shared memory: the first 13 levels (8191 floats).
+constexpr int kStageLevels = 13;
+constexpr int kStageMaxFloats = (1 << kStageLevels) - 1;
+
+// Bytes of T staged into shared memory for a tree of depth L (multiple of 16), and the
+// same rounded up to 128 (the offset of what follows in dynamic shared memory).
+__host__ __device__ constexpr uint32_t stage_bytes(int L) {
+    return L <= 0 ? 0u : ((((1u << (L < kStageLevels ? L : kStageLevels)) - 1u) * 4u + 15u) & ~15u);
+}
+__host__ __device__ constexpr uint32_t stage_offset(int L) { return (stage_bytes(L) + 127u) & ~127u; }
+
+__device__ __forceinline__ float sq_dist(float x, float y, float z, float px, float py, float pz) {
+    float dx = __fsub_rn(x, px);
+    float dy = __fsub_rn(y, py);
+    float dz = __fsub_rn(z, pz);
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+// Squared distance from (x, y, z) to the box [lo, hi] (clamped per axis, same order).
+__device__ __forceinline__ float box_dist2(float x, float y, float z, const float4& a, const float4& b) {
+    float gx = __fsub_rn(x, fminf(fmaxf(x, a.x), b.x));
+    float gy = __fsub_rn(y, fminf(fmaxf(y, a.y), b.y));
+    float gz = __fsub_rn(z, fminf(fmaxf(z, a.z), b.z));
+    return __fadd_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)), __fmul_rn(gz, gz));
+}
+
+// Fixed-length descent of Alg. 3: i <- 2i + 1 + [x_d > T_i], axes cycling x, y, z.
+// The first `ns` levels read T from shared memory `Ts` (when non-null), the rest
+// through the read-only cache.  Returns the leaf index i - (N - 1).
+__device__ __forceinline__ uint32_t descend(float x, float y, float z, const float* __restrict__ Tg,
+                                            const float* Ts, int ns, int L) {
+    uint32_t i = 0;
+    int ax = 0;
+    int lvl = 0;
+    if (Ts) {
+        for (; lvl < ns; lvl++) {
+            float v = ax == 0 ? x : (ax == 1 ? y : z);
+            float t = Ts[i];
+            i = 2 * i + 1 + (v > t ? 1u : 0u);
+            ax = ax == 2 ? 0 : ax + 1;
+        }
+    }
+    for (; lvl < L; lvl++) {
+        float v = ax == 0 ? x : (ax == 1 ? y : z);
+        float t = __ldg(Tg + i);
+        i = 2 * i + 1 + (v > t ? 1u : 0u);
+        ax = ax == 2 ? 0 : ax + 1;
+    }
+    return i - ((1u << L) - 1u);
+}
+
+__device__ __forceinline__ void load_leaf(const LeafRec* leaves, uint32_t leaf, float4& a, float4& b) {
+    const float4* p = reinterpret_cast<const float4*>(leaves + leaf);
+    a = __ldg(p);
+    b = __ldg(p + 1);
+}
+
+// ------------------------------------------------------------------------------------
+// Staging of the top levels of T into shared memory with the bulk asynchronous copy
+// engine (cp.async.bulk, completion counted on an mbarrier).  One elected thread
+// issues the copies; every thread waits with a bounded spin.  When the wait gives up
+// the block latches kStatusTimeout and reads T from global memory instead.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Returns true when the staged copy is complete and readable by the whole block.
+// `bytes` must be a multiple of 16; src and dst 16-byte aligned.
+__device__ __forceinline__ bool stage_to_smem(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                              int* status) {
+    const uint32_t b = smem_u32(bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t state;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+                     : "=l"(state)
+                     : "r"(b), "r"(bytes)
+                     : "memory");
+        (void)state;
+        const uint32_t d = smem_u32(dst);
+        const char* s = static_cast<const char*>(src);
+        for (uint32_t off = 0; off < bytes; off += 16384u) {
+            uint32_t sz = bytes - off < 16384u ? bytes - off : 16384u;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    d + off),
+                "l"(s + off), "r"(sz), "r"(b)
+                : "memory");
+        }
+    }
+    // bounded wait: about 2^22 polls (far beyond the microseconds a 32 KB copy takes)
+    bool done = false;
+    for (uint32_t it = 0; it < (1u << 22); it++) {
+        if (mbar_try_wait(b, 0)) { done = true; break; }
+    }
+    int all_done = __syncthreads_and(done ? 1 : 0);
+    if (!all_done) {
+        if (threadIdx.x == 0) atomicOr(status, kStatusTimeout);
+        // wait (bounded again) for the copy still in flight before the block may exit
+        for (uint32_t it = 0; it < (1u << 22); it++)
+            if (mbar_try_wait(b, 0)) break;
+        __syncthreads();
+        return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+// Inclusive warp prefix sum.
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+    const uint32_t lane = lane_id();
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= (uint32_t)o) v += u;
+    }
+    return v;
+}
+
+}  // namespace capt

@@ -1,0 +1,45 @@
+// Host-side launchers of the CAPT kernels (internal; each returns a capt_status).
+#pragma once
+
+#include <cuda_runtime_api.h>
+
+#include <string>
+
+#include "capt_internal.h"
+
+namespace capt {
+
+enum QueryMode { kModeSpheres = 0, kModeConfigs = 1 };
+
+// Persistent query kernel: flags per sphere (mode 0) or per configuration (mode 1).
+int launch_query(const DevArgs& t, int mode, const float* centers, const float* radii, uint64_t n_items, int S,
+                 uint8_t* out, const capt_launch_cfg& cfg, cudaStream_t st, std::string& err);
+
+// Sequential Alg. 3 work counters for configuration queries.
+int launch_count_configs(const DevArgs& t, const float* centers, const float* radii, uint64_t C, int S,
+                         uint64_t* counts, cudaStream_t st, std::string& err);
+
+int launch_leaves(const DevArgs& t, const float* centers, uint64_t m, uint32_t* leaves, cudaStream_t st,
+                  std::string& err);
+
+// Clearance forward / backward.
+int launch_clearance_fwd(const DevArgs& t, const float* centers, const float* radii, uint64_t T, int W, int S,
+                         float margin, float* cost, float* dist, int32_t* argmin, const capt_launch_cfg& cfg,
+                         cudaStream_t st, std::string& err);
+int launch_clearance_bwd(const DevArgs& t, const float* centers, const float* radii, const float* dist,
+                         const int32_t* argmin, const float* grad_cost, uint64_t T, int W, int S, float margin,
+                         float* grad, cudaStream_t st, std::string& err);
+
+// Edge validation: scratch holds (E + 1) uint32 work-item offsets plus one counter.
+size_t edge_scratch_words(size_t E);
+int launch_edges_persistent(const DevArgs& t, const capt_arm& arm, const float* qa, const float* qb,
+                            const int32_t* ns, uint64_t E, uint8_t* valid, uint32_t* scratch,
+                            const capt_launch_cfg& cfg, cudaStream_t st, std::string& err);
+int launch_edges_per_edge(const DevArgs& t, const capt_arm& arm, const float* qa, const float* qb,
+                          const int32_t* h_ns, uint64_t E, uint8_t* valid, const capt_launch_cfg& cfg,
+                          cudaStream_t st, std::string& err);
+
+// Number of SMs of the current device (cached per device).
+int sm_count();
+
+}  // namespace capt

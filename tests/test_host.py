@@ -1,0 +1,119 @@
+"""Host side of the product library against the oracle (no GPU): the optimised C++
+builder must produce the oracle's plain Alg. 1 tree (same T, same sets, same boxes),
+the C++ filter the oracle's plain Alg. 2 output, and the C ABI must export every
+symbol include/capt.h declares and reject bad arguments without touching a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _sets(sb, si, N):
+    return [si[int(sb[l]):int(sb[l + 1])] for l in range(N)]
+
+
+def _compare_trees(orc, capt, pts, r_min, r_max, threads=0):
+    ref = orc.PlainCAPT(pts, r_min, r_max)
+    t = capt.capt_build_threads(pts, r_min, r_max, threads)
+    st = capt.capt_stats(t)
+    assert st["n_leaves"] == ref.N and st["depth"] == ref.L
+    assert st["total_afforded"] == ref.total and st["max_set"] == ref.max_set
+    assert st["pruned_leaves"] == ref.n_pruned
+    a, b = capt.capt_export(t), ref.export()
+    np.testing.assert_array_equal(a["T"], b["T"])
+    np.testing.assert_array_equal(a["set_begin"].astype(np.int64), b["set_begin"])
+    np.testing.assert_array_equal(a["set_idx"], b["set_idx"])
+    np.testing.assert_array_equal(a["aabb"], b["aabb"])
+    return t, st
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 5, 17, 64, 100, 1000])
+def test_builder_equals_plain_capt_uniform(orc, capt_lib, n):
+    pts = W.uniform_cloud(n, 300 + n)
+    _compare_trees(orc, capt_lib, pts, 0.01, 0.08)
+    _compare_trees(orc, capt_lib, pts, 0.0, 0.2)
+
+
+def test_builder_equals_plain_capt_grid_duplicates(orc, capt_lib):
+    rng = np.random.default_rng(9)
+    pts = (rng.integers(0, 5, (300, 3)) * 0.125).astype(np.float32)   # many ties and plane points
+    _compare_trees(orc, capt_lib, pts, 0.02, 0.3)
+    _compare_trees(orc, capt_lib, pts, 0.0, 0.125)
+
+
+def test_builder_dense_prunes_like_oracle(orc, capt_lib):
+    pts = W.uniform_cloud(1500, 77) * np.float32(0.08)
+    _, st = _compare_trees(orc, capt_lib, pts, 0.02, 0.08)
+    assert st["pruned_leaves"] > 0
+
+
+@pytest.mark.parametrize("threads", [1, 2, 8])
+def test_builder_threads_do_not_change_the_tree(orc, capt_lib, threads):
+    pts, _ = W.tabletop_cloud(1001, n=5000)
+    _compare_trees(orc, capt_lib, pts, 0.02, 0.08, threads)
+
+
+def test_builder_rejects_bad_input(capt_lib):
+    pts = W.uniform_cloud(10, 1)
+    with pytest.raises(capt_lib.CaptError) as e:
+        capt_lib.capt_build(pts, 0.1, 0.05)
+    assert e.value.status == -2
+    bad = pts.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(capt_lib.CaptError) as e:
+        capt_lib.capt_build(bad, 0.0, 0.05)
+    assert e.value.status == -3
+    with pytest.raises(capt_lib.CaptError) as e:
+        capt_lib.capt_build(pts, -0.1, 0.05)
+    assert e.value.status == -2
+
+
+@pytest.mark.parametrize("n,rf", [(0, 0.1), (1, 0.1), (6, 0.4), (3000, 0.01), (30000, 0.01), (20000, 0.0)])
+def test_filter_equals_plain_alg2(orc, capt_lib, n, rf):
+    if n == 6:
+        x = np.array([0.0, 0.3, 0.5, 1.2, 1.25, 2.0], np.float32)
+        pts = np.stack([x, np.zeros_like(x), np.zeros_like(x)], 1)
+    else:
+        pts, _ = W.tabletop_cloud(1001, n=max(n, 1))
+        pts = pts[:n]
+    if rf == 0.0:
+        pts = np.concatenate([pts, pts[::7]])          # exact duplicates
+    a = capt_lib.sfc_filter(pts, rf)
+    b = orc.sfc_filter(pts, rf)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_filter_rejects_nonfinite(capt_lib):
+    pts = W.uniform_cloud(10, 2)
+    pts[4, 0] = np.inf
+    with pytest.raises(capt_lib.CaptError) as e:
+        capt_lib.sfc_filter(pts, 0.1)
+    assert e.value.status == -3
+
+
+def test_header_symbols_are_exported(capt_lib):
+    hdr = open(os.path.join(ROOT, "include", "capt.h")).read()
+    declared = set(re.findall(r"^\s*(?:int|void|const char\*)\s+(\w+)\s*\(", hdr, re.M))
+    assert declared == set(capt_lib.EXPORTED_SYMBOLS)
+    lib = ctypes.CDLL(capt_lib._build.LIB)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_device_calls_reject_unuploaded_tree_without_gpu(capt_lib):
+    """Host-side argument checks run before any CUDA call."""
+    t = capt_lib.capt_build(W.uniform_cloud(50, 3), 0.01, 0.08)
+    L = capt_lib._load()
+    rc = L.capt_query_spheres(t.h, None, None, 10, None, None)
+    assert rc == -8                                    # CAPT_E_STATE: not uploaded
+    assert "not uploaded" in capt_lib.capt_last_error()
+    rc = L.capt_query_spheres(None, None, None, 10, None, None)
+    assert rc == -1
+    st = capt_lib.capt_stats(t)
+    assert st["device"] == -1 and st["device_bytes"] == 0

@@ -360,8 +360,18 @@ def fk_centers(arm: ArmModel, q: np.ndarray, chunk: int = 1 << 16) -> np.ndarray
     return out
 
 
-def random_configs(C: int, seed: int, n_joints: int = 7, lo=-2.8, hi=2.8) -> np.ndarray:
-    return Stream(seed, P_CONFIGS).uniform(lo, hi, C * n_joints).reshape(C, n_joints).astype(np.float32)
+def random_configs(C: int, seed: int, n_joints: int = 7, lo=-2.8, hi=2.8, first: int = 0) -> np.ndarray:
+    """Configurations first .. first + C - 1 of the seed's configuration stream, so that
+    disjoint ranges (one per process) are slices of one global sequence."""
+    st = Stream(seed, P_CONFIGS)
+    st.counter = first * n_joints
+    return st.uniform(lo, hi, C * n_joints).reshape(C, n_joints).astype(np.float32)
+
+
+def tabletop_scene(seed: int = 1001):
+    """The tabletop cloud (30,000 points) and the arm used by every tabletop workload."""
+    pts, layout = tabletop_cloud(seed)
+    return pts, layout, arm_7dof()
 
 
 def random_edges(E: int, seed: int, n_joints: int = 7, lo=-2.8, hi=2.8, step=0.01,
