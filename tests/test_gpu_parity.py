@@ -294,7 +294,7 @@ def test_clearance_forward_against_fp64(tabletop, orc, capt_lib, torch_):
     ocost, od, _ = orc.clearance64(tabletop["pts"], cen, r, 0.08, 0.01, want_grad=False)
     assert np.abs(d - od).max() <= 1e-5
     near = od < 0.08 - 1e-5
-    assert near.mean() > 0.05
+    assert near.sum() > 1000                 # random arm postures: a few percent of spheres near the cloud
     dn, idx, d2 = orc.nearest64(tabletop["pts"], cen.reshape(-1, 3))
     sep = (d2 - dn > 1e-5).reshape(d.shape) & near
     assert np.array_equal(am[sep], idx.reshape(d.shape)[sep])
