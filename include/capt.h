@@ -237,6 +237,26 @@ enum { CAPT_EDGES_PERSISTENT = 0, /* one persistent launch over (edge, chunk) wo
 int capt_validate_edges(capt_tree* t, const capt_arm* arm, const float* d_qa, const float* d_qb,
                         const int32_t* d_nsteps, size_t E, uint8_t* d_valid, int mode, void* stream);
 
+/* The same validation as capt_validate_edges in persistent mode, for callers that
+ * cannot let the library allocate device memory: a planner in a real-time control loop
+ * must not enter the CUDA allocator (cudaMalloc/cudaFree can synchronise the device and
+ * take unbounded time), and an application whose device memory belongs to another
+ * allocator (a caching allocator or a fixed arena) cannot have raw allocations appear
+ * behind its back.  The paper has no counterpart: this is a deployment variant.
+ * Instead of a buffer it allocates, the call uses one fixed scratch array inside the
+ * library (CAPT_STATIC_MAX_EDGES + 64 words, about 256 KB), which every device that
+ * loads the library holds until the process exits.  It calls no allocator.
+ *  - E must be <= CAPT_STATIC_MAX_EDGES, else CAPT_E_ARG.
+ *  - The first call on a device looks the array's device address up (once per device,
+ *    with that device current); make that first call before any stream capture.
+ *  - Every call reuses the same array and re-initialises what must start at zero, so
+ *    calls whose work overlaps on the GPU (other streams, other host threads) race:
+ *    order them on one stream or synchronise between them.
+ * Arguments, results and the other errors as capt_validate_edges. */
+#define CAPT_STATIC_MAX_EDGES 65536
+int capt_validate_edges_static(const capt_tree* t, const capt_arm* arm, const float* d_qa, const float* d_qb,
+                               const int32_t* d_nsteps, size_t E, uint8_t* d_valid, void* stream);
+
 /* A captured CUDA graph of the persistent edge validator for fixed buffers: one
  * capt_edge_plan_launch replays {work-counter reset, per-edge prefix of work items,
  * persistent kernel} with a single cudaGraphLaunch.  cfg = NULL autotunes the

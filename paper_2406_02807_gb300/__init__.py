@@ -22,6 +22,7 @@ __all__ = [
     "capt_get_launch_cfg", "capt_autotune_configs", "capt_validate_edges", "capt_edge_plan_create",
     "capt_edge_plan_launch", "capt_edge_plan_info", "capt_edge_plan_free", "capt_clearance_fwd",
     "capt_clearance_bwd", "capt_free", "capt_last_error", "make_arm", "CaptTree", "EdgePlan",
+    "capt_validate_edges_static", "CAPT_STATIC_MAX_EDGES",
     "STATUS", "CAPT_STAGE_GLOBAL", "CAPT_STAGE_SMEM", "CAPT_KERNEL_SPHERES", "CAPT_KERNEL_CONFIGS",
     "CAPT_KERNEL_EDGES", "CAPT_KERNEL_CLEARANCE", "CAPT_EDGES_PERSISTENT", "CAPT_EDGES_PER_EDGE",
     "EXPORTED_SYMBOLS",
@@ -41,7 +42,9 @@ EXPORTED_SYMBOLS = [
     "capt_query_leaves", "capt_device_status", "capt_set_launch_cfg", "capt_get_launch_cfg",
     "capt_autotune_configs", "capt_validate_edges", "capt_edge_plan_create", "capt_edge_plan_launch",
     "capt_edge_plan_info", "capt_edge_plan_free", "capt_clearance_fwd", "capt_clearance_bwd",
+    "capt_validate_edges_static",
 ]
+CAPT_STATIC_MAX_EDGES = 65536
 
 
 class CaptError(RuntimeError):
@@ -98,6 +101,7 @@ def _load():
         "capt_get_launch_cfg": [P, I, C.POINTER(_LaunchCfg)],
         "capt_autotune_configs": [P, P, P, SZ, I, P, P, C.POINTER(_LaunchCfg), C.POINTER(F)],
         "capt_validate_edges": [P, C.POINTER(_Arm), P, P, P, SZ, P, I, P],
+        "capt_validate_edges_static": [P, C.POINTER(_Arm), P, P, P, SZ, P, P],
         "capt_edge_plan_create": [P, C.POINTER(_Arm), P, P, P, SZ, P, C.POINTER(_LaunchCfg), P, C.POINTER(P)],
         "capt_edge_plan_launch": [P, P],
         "capt_edge_plan_info": [P, C.POINTER(_LaunchCfg), C.POINTER(F)],
@@ -363,6 +367,23 @@ def capt_validate_edges(tree: CaptTree, arm, qa, qb, nsteps, valid=None, mode=CA
     _check(_load().capt_validate_edges(tree.h, C.byref(a), _dev(qa, torch.float32, "qa"), _dev(qb, torch.float32, "qb"),
                                        _dev(nsteps, torch.int32, "nsteps"), E, _dev(valid, torch.uint8, "valid"),
                                        int(mode), _stream(stream)), "capt_validate_edges")
+    return valid
+
+
+def capt_validate_edges_static(tree: CaptTree, arm, qa, qb, nsteps, valid=None, stream=None):
+    """capt_validate_edges without any device allocation by the library (at most
+    CAPT_STATIC_MAX_EDGES edges; calls share one scratch array, so overlapping calls
+    race).  For callers that must not enter the CUDA allocator, such as a planner in a
+    real-time control loop or an application whose device memory another allocator owns."""
+    import torch
+    E = qa.shape[0]
+    if valid is None:
+        valid = torch.empty(E, dtype=torch.uint8, device=qa.device)
+    a = arm if isinstance(arm, _Arm) else make_arm(arm)
+    _check(_load().capt_validate_edges_static(tree.h, C.byref(a), _dev(qa, torch.float32, "qa"),
+                                              _dev(qb, torch.float32, "qb"), _dev(nsteps, torch.int32, "nsteps"), E,
+                                              _dev(valid, torch.uint8, "valid"), _stream(stream)),
+           "capt_validate_edges_static")
     return valid
 
 

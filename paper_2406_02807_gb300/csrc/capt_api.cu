@@ -455,6 +455,20 @@ int capt_autotune_configs(capt_tree* t, const float* d_centers, const float* d_r
 
 }  // extern "C"
 
+// Internal accessors for entry points defined in other translation units.
+int capt_internal_tree_args(const capt_tree* t, capt::DevArgs* out, int* device) {
+    int rc = check_ready(t);
+    if (rc) return rc;
+    *out = t->args();
+    *device = t->device;
+    return CAPT_OK;
+}
+
+const char* capt_internal_set_error(int code, const char* msg) {
+    fail(code, msg ? msg : "");
+    return g_err.c_str();
+}
+
 // ------------------------------------------------------------------------------------
 // Edges and clearance entry points
 // ------------------------------------------------------------------------------------
