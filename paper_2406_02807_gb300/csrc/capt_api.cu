@@ -70,6 +70,8 @@ struct capt_tree {
     int* d_status = nullptr;
     uint64_t total_blocks = 0;
     size_t dev_bytes = 0;
+    uint32_t tail_off = 0, stage_floats = 0;
+    int K = 0, R = 0, Ks = 0, tail_staged = 0;
     capt_launch_cfg cfg[4];
     // host-buffer pipeline
     float* d_pipe_c[2] = {nullptr, nullptr};
@@ -92,6 +94,12 @@ struct capt_tree {
     DevArgs args() const {
         DevArgs a;
         a.T = static_cast<const float*>(d_T);
+        a.tail_off = tail_off;
+        a.K = K;
+        a.R = R;
+        a.Ks = Ks;
+        a.tail_staged = tail_staged;
+        a.stage_floats = stage_floats;
         a.leaves = static_cast<const capt::LeafRec*>(d_leaves);
         a.blocks = static_cast<const float*>(d_blocks);
         a.ids = static_cast<const uint32_t*>(d_ids);
@@ -235,8 +243,13 @@ int capt_upload(capt_tree* t, int device, void* stream) {
         return fail(CAPT_E_NOMEM, "host allocation failed while flattening");
     }
     const auto& h = t->h;
-    const size_t nT = std::max<size_t>(4, ((h.T.size() + 3) / 4) * 4);
-    const size_t sz_T = nT * sizeof(float);
+    capt::BlockedSplits bs;
+    try {
+        capt::blocked_splits(h, bs);
+    } catch (const std::bad_alloc&) {
+        return fail(CAPT_E_NOMEM, "host allocation failed while blocking T");
+    }
+    const size_t sz_T = bs.data.size() * sizeof(float);
     const size_t sz_leaves = lay.leaves.size() * sizeof(capt::LeafRec);
     const size_t sz_blocks = lay.blocks.size() * sizeof(float);
     const size_t sz_ids = lay.ids.size() * sizeof(uint32_t);
@@ -257,10 +270,8 @@ int capt_upload(capt_tree* t, int device, void* stream) {
         (rc = alloc(&t->d_blocks, sz_blocks, "blocks")) || (rc = alloc(&t->d_ids, sz_ids, "ids")) ||
         (rc = alloc(&t->d_cloud, sz_cloud, "cloud")) || (rc = alloc((void**)&t->d_status, 256, "status")))
         return rc;
-    std::vector<float> Tpad(nT, INFINITY);
-    std::copy(h.T.begin(), h.T.end(), Tpad.begin());
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(t->d_T, Tpad.data(), sz_T, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t->d_T, bs.data.data(), sz_T, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(t->d_leaves, lay.leaves.data(), sz_leaves, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(t->d_blocks, lay.blocks.data(), sz_blocks, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(t->d_ids, lay.ids.data(), sz_ids, cudaMemcpyHostToDevice, st);
@@ -273,6 +284,12 @@ int capt_upload(capt_tree* t, int device, void* stream) {
         return cuda_fail(e, "upload");
     }
     t->total_blocks = lay.total_blocks;
+    t->tail_off = bs.tail_off;
+    t->K = bs.K;
+    t->R = bs.R;
+    t->Ks = bs.Ks;
+    t->tail_staged = bs.tail_staged;
+    t->stage_floats = bs.stage_floats;
     t->dev_bytes = sz_T + sz_leaves + sz_blocks + sz_ids + sz_cloud + 256;
     return CAPT_OK;
 }

@@ -42,9 +42,23 @@ struct Layout {
     uint64_t total_blocks = 0;
 };
 
+// Blocked copy of T used by the descent (see blocked_splits).
+struct BlockedSplits {
+    std::vector<float> data;
+    uint32_t tail_off = 0;      // float offset of the tail blocks
+    int K = 0, R = 0;           // full 3-level super-levels, remaining levels (L = 3K + R)
+    uint32_t stage_floats = 0;  // prefix copied to shared memory by the staged kernels
+    int Ks = 0;                 // super-levels inside that prefix
+    int tail_staged = 0;        // 1 if the tail is inside it too
+};
+void blocked_splits(const HostTree& t, BlockedSplits& out);
+
 // Kernel view of an uploaded tree (raw device pointers, passed by value).
 struct DevArgs {
-    const float* T = nullptr;        // N-1 split values, padded to a multiple of 4 floats
+    const float* T = nullptr;        // blocked split array (BlockedSplits::data)
+    uint32_t tail_off = 0;
+    int K = 0, R = 0, Ks = 0, tail_staged = 0;
+    uint32_t stage_floats = 0;
     const LeafRec* leaves = nullptr; // N records
     const float* blocks = nullptr;   // 12 floats per 4-point block (float4 x 3)
     const uint32_t* ids = nullptr;   // 4 per block

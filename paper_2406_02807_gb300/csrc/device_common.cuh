@@ -17,16 +17,12 @@ namespace capt {
 constexpr int kStatusTimeout = 1;
 constexpr int kStatusBounds = 2;
 
-// Largest prefix of T staged into shared memory: the first 13 levels (8191 floats).
-constexpr int kStageLevels = 13;
-constexpr int kStageMaxFloats = (1 << kStageLevels) - 1;
-
-// Bytes of T staged into shared memory for a tree of depth L (multiple of 16), and the
-// same rounded up to 128 (the offset of what follows in dynamic shared memory).
-__host__ __device__ constexpr uint32_t stage_bytes(int L) {
-    return L <= 0 ? 0u : ((((1u << (L < kStageLevels ? L : kStageLevels)) - 1u) * 4u + 15u) & ~15u);
+// Bytes of the blocked split prefix staged into shared memory (a multiple of 16), and
+// the offset of what follows it in dynamic shared memory (rounded up to 128).
+__host__ __device__ __forceinline__ uint32_t stage_bytes(const DevArgs& t) { return t.stage_floats * 4u; }
+__host__ __device__ __forceinline__ uint32_t stage_offset(const DevArgs& t) {
+    return (stage_bytes(t) + 127u) & ~127u;
 }
-__host__ __device__ constexpr uint32_t stage_offset(int L) { return (stage_bytes(L) + 127u) & ~127u; }
 
 __device__ __forceinline__ float sq_dist(float x, float y, float z, float px, float py, float pz) {
     float dx = __fsub_rn(x, px);
@@ -43,30 +39,58 @@ __device__ __forceinline__ float box_dist2(float x, float y, float z, const floa
     return __fadd_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)), __fmul_rn(gz, gz));
 }
 
-// Fixed-length descent of Alg. 3: i <- 2i + 1 + [x_d > T_i], axes cycling x, y, z.
-// The first `ns` levels read T from shared memory `Ts` (when non-null), the rest
-// through the read-only cache.  Returns the leaf index i - (N - 1).
-__device__ __forceinline__ uint32_t descend(float x, float y, float z, const float* __restrict__ Tg,
-                                            const float* Ts, int ns, int L) {
-    uint32_t i = 0;
-    int ax = 0;
-    int lvl = 0;
+// Three levels of the descent on one 8-float block (axes x, y, z in that order):
+// i <- 2i + 1 + [x_d > T_i] three times.  `bits` collects the comparison results, which
+// is the leaf's position once all L levels are done; `u` is the next block.
+__device__ __forceinline__ void step3(float x, float y, float z, const float4& a, const float4& b, uint32_t& u,
+                                      uint32_t& bits) {
+    const uint32_t c0 = x > a.x ? 1u : 0u;
+    const uint32_t c1 = y > (c0 ? a.z : a.y) ? 1u : 0u;
+    const float t2 = c0 ? (c1 ? b.z : b.y) : (c1 ? b.x : a.w);
+    const uint32_t c2 = z > t2 ? 1u : 0u;
+    const uint32_t child = (c0 << 2) | (c1 << 1) | c2;
+    u = 8u * u + 1u + child;
+    bits = (bits << 3) | child;
+}
+
+// Fixed-length descent of Alg. 3 (exactly L = 3K + R comparisons, branch-free), over the
+// blocked split array.  The first t.Ks block levels (and the tail, if t.tail_staged)
+// come from the shared-memory copy `Ts` when it is non-null, the rest through the
+// read-only cache.  Returns the leaf index i - (N - 1).
+__device__ __forceinline__ uint32_t descend(float x, float y, float z, const DevArgs& t, const float* Ts) {
+    uint32_t u = 0, bits = 0;
+    int k = 0;
     if (Ts) {
-        for (; lvl < ns; lvl++) {
-            float v = ax == 0 ? x : (ax == 1 ? y : z);
-            float t = Ts[i];
-            i = 2 * i + 1 + (v > t ? 1u : 0u);
-            ax = ax == 2 ? 0 : ax + 1;
+        for (; k < t.Ks; k++) {
+            const float4 a = *reinterpret_cast<const float4*>(Ts + 8u * u);
+            const float4 b = *reinterpret_cast<const float4*>(Ts + 8u * u + 4u);
+            step3(x, y, z, a, b, u, bits);
         }
     }
-    for (; lvl < L; lvl++) {
-        float v = ax == 0 ? x : (ax == 1 ? y : z);
-        float t = __ldg(Tg + i);
-        i = 2 * i + 1 + (v > t ? 1u : 0u);
-        ax = ax == 2 ? 0 : ax + 1;
+    for (; k < t.K; k++) {
+        const float4* g = reinterpret_cast<const float4*>(t.T + 8ull * u);
+        const float4 a = __ldg(g);
+        const float4 b = __ldg(g + 1);
+        step3(x, y, z, a, b, u, bits);
     }
-    return i - ((1u << L) - 1u);
+    if (t.R) {
+        const size_t o = (size_t)t.tail_off + 4ull * bits;
+        const float4 q = (Ts && t.tail_staged) ? *reinterpret_cast<const float4*>(Ts + o)
+                                               : __ldg(reinterpret_cast<const float4*>(t.T + o));
+        const uint32_t c0 = x > q.x ? 1u : 0u;
+        if (t.R == 2) {
+            const uint32_t c1 = y > (c0 ? q.z : q.y) ? 1u : 0u;
+            bits = (bits << 2) | (c0 << 1) | c1;
+        } else {
+            bits = (bits << 1) | c0;
+        }
+    }
+    return bits;
 }
+
+// Stage the blocked prefix into `smem`; returns the pointer to use, or nullptr when
+// there is nothing to stage or the copy did not complete (then T is read globally).
+__device__ __forceinline__ const float* stage_splits(const DevArgs& t, void* smem, uint64_t* bar);
 
 __device__ __forceinline__ void load_leaf(const LeafRec* leaves, uint32_t leaf, float4& a, float4& b) {
     const float4* p = reinterpret_cast<const float4*>(leaves + leaf);
@@ -108,12 +132,11 @@ __device__ __forceinline__ bool stage_to_smem(void* dst, const void* src, uint32
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        uint64_t state;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
-                     : "=l"(state)
-                     : "r"(b), "r"(bytes)
-                     : "memory");
-        (void)state;
+        asm volatile(
+            "{\n\t.reg .b64 st;\n\t"
+            "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(b),
+            "r"(bytes)
+            : "memory");
         const uint32_t d = smem_u32(dst);
         const char* s = static_cast<const char*>(src);
         for (uint32_t off = 0; off < bytes; off += 16384u) {
@@ -140,6 +163,12 @@ __device__ __forceinline__ bool stage_to_smem(void* dst, const void* src, uint32
         return false;
     }
     return true;
+}
+
+__device__ __forceinline__ const float* stage_splits(const DevArgs& t, void* smem, uint64_t* bar) {
+    const uint32_t bytes = stage_bytes(t);
+    if (bytes == 0) return nullptr;
+    return stage_to_smem(smem, t.T, bytes, bar, t.status) ? reinterpret_cast<const float*>(smem) : nullptr;
 }
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }

@@ -38,15 +38,10 @@ __global__ void __launch_bounds__(512) k_clearance_fwd(DevArgs t, const float* _
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t bar;
     const float* Ts = nullptr;
-    int ns = 0;
     uint32_t off = 0;
     if constexpr (STAGE) {
-        const uint32_t bytes = stage_bytes(t.L);
-        off = stage_offset(t.L);
-        if (bytes > 0 && stage_to_smem(smem_raw, t.T, bytes, &bar, t.status)) {
-            Ts = reinterpret_cast<const float*>(smem_raw);
-            ns = t.L < kStageLevels ? t.L : kStageLevels;
-        }
+        Ts = stage_splits(t, smem_raw, &bar);
+        off = stage_offset(t);
     }
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     ClearScratch* ws = reinterpret_cast<ClearScratch*>(smem_raw + off) + warp;
@@ -78,7 +73,7 @@ __global__ void __launch_bounds__(512) k_clearance_fwd(DevArgs t, const float* _
                     X[h] = __ldg(centers + 3 * sph);
                     Y[h] = __ldg(centers + 3 * sph + 1);
                     Z[h] = __ldg(centers + 3 * sph + 2);
-                    const uint32_t leaf = descend(X[h], Y[h], Z[h], t.T, Ts, ns, t.L);
+                    const uint32_t leaf = descend(X[h], Y[h], Z[h], t, Ts);
                     float4 a, b;
                     load_leaf(t.leaves, leaf, a, b);
                     const uint32_t cnt = __float_as_uint(b.w);
@@ -213,10 +208,10 @@ int launch_clearance_fwd(const DevArgs& t, const float* centers, const float* ra
                          cudaStream_t st, std::string& err) {
     if (T == 0) return CAPT_OK;
     if (W > kMaxWaypoints) { err = "clearance supports at most 4096 waypoints per trajectory"; return CAPT_E_ARG; }
-    const bool stage = cfg.staging == CAPT_STAGE_SMEM && t.L > 0;
+    const bool stage = cfg.staging == CAPT_STAGE_SMEM && t.stage_floats > 0;
     auto fn = stage ? k_clearance_fwd<true> : k_clearance_fwd<false>;
     const int warps = std::max(1, std::min(16, std::min((int)cfg.warps_per_block, W)));
-    const size_t smem = (stage ? stage_offset(t.L) : 0u) + sizeof(ClearScratch) * (size_t)warps +
+    const size_t smem = (stage ? stage_offset(t) : 0u) + sizeof(ClearScratch) * (size_t)warps +
                         sizeof(float) * (size_t)W;
     cudaError_t ce = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (ce != cudaSuccess) { err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }

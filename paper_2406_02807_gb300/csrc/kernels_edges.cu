@@ -139,7 +139,7 @@ struct EdgeScratch {
 // Returns true if any of them collides.
 template <int SPL>
 __device__ bool check_configs(const DevArgs& t, const capt_arm& arm, const LaneSpheres& ls, const float* qa_e,
-                              const float* qb_e, int n_e, int k0, int limit, const float* Ts, int ns,
+                              const float* qb_e, int n_e, int k0, int limit, const float* Ts,
                               EdgeScratch<SPL>* ws) {
     constexpr int CPT = SPL / 2;
     const uint32_t lane = lane_id();
@@ -170,7 +170,7 @@ __device__ bool check_configs(const DevArgs& t, const capt_arm& arm, const LaneS
             Z[k] = pc[2];
             R2[k] = ls.r2[h];
             if (live && ls.f[h] >= 0) {
-                const uint32_t leaf = descend(X[k], Y[k], Z[k], t.T, Ts, ns, t.L);
+                const uint32_t leaf = descend(X[k], Y[k], Z[k], t, Ts);
                 float4 a, b;
                 load_leaf(t.leaves, leaf, a, b);
                 const uint32_t cnt = __float_as_uint(b.w);
@@ -272,15 +272,10 @@ __global__ void __launch_bounds__(512) k_edges_persistent(DevArgs t, const __gri
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t bar;
     const float* Ts = nullptr;
-    int ns_lv = 0;
     uint32_t off = 0;
     if constexpr (STAGE) {
-        const uint32_t bytes = stage_bytes(t.L);
-        off = stage_offset(t.L);
-        if (bytes > 0 && stage_to_smem(smem_raw, t.T, bytes, &bar, t.status)) {
-            Ts = reinterpret_cast<const float*>(smem_raw);
-            ns_lv = t.L < kStageLevels ? t.L : kStageLevels;
-        }
+        Ts = stage_splits(t, smem_raw, &bar);
+        off = stage_offset(t);
     }
     constexpr int CPT = SPL / 2;
     const uint32_t lane = lane_id();
@@ -308,7 +303,7 @@ __global__ void __launch_bounds__(512) k_edges_persistent(DevArgs t, const __gri
         const float* qa_e = qa + (size_t)e * J;
         const float* qb_e = qb + (size_t)e * J;
         for (int k = k_begin; k < k_end; k += CPT) {
-            if (check_configs<SPL>(t, arm, ls, qa_e, qb_e, n_e, k, k_end, Ts, ns_lv, ws)) {
+            if (check_configs<SPL>(t, arm, ls, qa_e, qb_e, n_e, k, k_end, Ts, ws)) {
                 if (lane == 0) valid[e] = 0;
                 break;
             }
@@ -330,7 +325,7 @@ __global__ void __launch_bounds__(512) k_edge_single(DevArgs t, const __grid_con
     const int gw = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
     for (int k = gw * CPT; k < n_e; k += warps * CPT) {
         if (load_volatile_u8(valid_e) == 0) break;
-        if (check_configs<SPL>(t, arm, ls, qa_e, qb_e, n_e, k, n_e, nullptr, 0, ws)) {
+        if (check_configs<SPL>(t, arm, ls, qa_e, qb_e, n_e, k, n_e, nullptr, ws)) {
             if (lane_id() == 0) *valid_e = 0;
             break;
         }
@@ -360,12 +355,12 @@ int launch_edges_persistent(const DevArgs& t, const capt_arm& arm, const float* 
     k_edges_setup<<<1, 1024, 0, st>>>(ns, (uint32_t)E, chunk, scratch, valid);
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) { err = std::string("edge setup launch: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
-    const bool stage = cfg.staging == CAPT_STAGE_SMEM && t.L > 0;
+    const bool stage = cfg.staging == CAPT_STAGE_SMEM && t.stage_floats > 0;
     PersistentKernel fn = pick_persistent(cfg.spheres_per_lane, stage);
     if (!fn) { err = "edges need spheres_per_lane 2 or 4"; return CAPT_E_ARG; }
     const int warps = std::max(1, std::min(16, (int)cfg.warps_per_block));
     const size_t ws = cfg.spheres_per_lane == 2 ? sizeof(EdgeScratch<2>) : sizeof(EdgeScratch<4>);
-    const uint32_t sb = stage ? stage_offset(t.L) : 0u;
+    const uint32_t sb = stage ? stage_offset(t) : 0u;
     const size_t smem = sb + ws * (size_t)warps;
     ce = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (ce != cudaSuccess) { err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }

@@ -25,10 +25,21 @@ namespace capt {
 template <int SPL>
 struct WarpScratch {
     static constexpr int E = 32 * SPL;
-    float cx[E], cy[E], cz[E], r2[E];
-    uint32_t blk[E], start[E], end[E], grp[E];
-    uint32_t ghit[E];
+    float4 c[E];          // centre and r^2 of each entry
+    int32_t boff[E];      // first block of the entry minus its start in the block list
+    uint32_t end[E];      // exclusive end of the entry in the block list
+    uint32_t grp[E];      // group (sphere slot or configuration) of the entry
+    uint32_t ghit[E];     // per group: 1 once it collides
 };
+
+// 4 FP32 sphere tests against one 4-point block (3 x 16-byte loads).
+__device__ __forceinline__ bool block_hit(const float4* __restrict__ blocks, int32_t b, const float4& c) {
+    const float4 px = __ldg(blocks + 3 * (size_t)b);
+    const float4 py = __ldg(blocks + 3 * (size_t)b + 1);
+    const float4 pz = __ldg(blocks + 3 * (size_t)b + 2);
+    return (sq_dist(c.x, c.y, c.z, px.x, py.x, pz.x) <= c.w) | (sq_dist(c.x, c.y, c.z, px.y, py.y, pz.y) <= c.w) |
+           (sq_dist(c.x, c.y, c.z, px.z, py.z, pz.z) <= c.w) | (sq_dist(c.x, c.y, c.z, px.w, py.w, pz.w) <= c.w);
+}
 
 template <int SPL, bool STAGE, int MODE>
 __global__ void __launch_bounds__(512) k_query(DevArgs t, const float* __restrict__ centers,
@@ -37,15 +48,10 @@ __global__ void __launch_bounds__(512) k_query(DevArgs t, const float* __restric
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t bar;
     const float* Ts = nullptr;
-    int ns = 0;
     uint32_t off = 0;
     if constexpr (STAGE) {
-        const uint32_t bytes = stage_bytes(t.L);
-        off = (bytes + 127u) & ~127u;
-        if (bytes > 0 && stage_to_smem(smem_raw, t.T, bytes, &bar, t.status)) {
-            Ts = reinterpret_cast<const float*>(smem_raw);
-            ns = t.L < kStageLevels ? t.L : kStageLevels;
-        }
+        Ts = stage_splits(t, smem_raw, &bar);
+        off = stage_offset(t);
     }
     const uint32_t lane = lane_id();
     const uint32_t warp = threadIdx.x >> 5;
@@ -56,12 +62,15 @@ __global__ void __launch_bounds__(512) k_query(DevArgs t, const float* __restric
     const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     const uint32_t lt_mask = (1u << lane) - 1u;
     const uint32_t span = 32u * (uint32_t)rows;
+    // one configuration per tile: its first hit ends the tile, no per-group bookkeeping
+    const bool single = MODE == kModeConfigs && cpt == 1;
 
     for (uint64_t tile = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp; tile < n_tiles; tile += nwarps) {
         // ---- 1. descent and box test per slot ----
         bool act[SPL];
-        uint32_t nb[SPL], fb[SPL], grp[SPL];
-        float X[SPL], Y[SPL], Z[SPL], R2[SPL];
+        uint32_t nb[SPL], fb[SPL];
+        float4 C[SPL];
+        bool any = false;
 #pragma unroll
         for (int k = 0; k < SPL; k++) {
             const uint32_t j = (uint32_t)k * 32u + lane;
@@ -71,51 +80,63 @@ __global__ void __launch_bounds__(512) k_query(DevArgs t, const float* __restric
             if constexpr (MODE == kModeSpheres) {
                 sph = tile * per_tile + j;
                 valid = sph < n_items;
-                grp[k] = j;
                 r = valid ? __ldg(radii + sph) : 0.f;
             } else {
                 const uint32_t g = j / span, s = j - g * span;
                 const uint64_t cfg = tile * per_tile + g;
                 valid = g < (uint32_t)cpt && s < (uint32_t)S && cfg < n_items;
                 sph = cfg * (uint64_t)S + s;
-                grp[k] = g;
                 r = valid ? __ldg(radii + s) : 0.f;
             }
             act[k] = false;
             nb[k] = 0;
             fb[k] = 0;
-            X[k] = Y[k] = Z[k] = 0.f;
-            R2[k] = __fmul_rn(r, r);
+            C[k] = make_float4(0.f, 0.f, 0.f, __fmul_rn(r, r));
             if (valid) {
-                X[k] = __ldg(centers + 3 * sph);
-                Y[k] = __ldg(centers + 3 * sph + 1);
-                Z[k] = __ldg(centers + 3 * sph + 2);
-                const uint32_t leaf = descend(X[k], Y[k], Z[k], t.T, Ts, ns, t.L);
+                C[k].x = __ldg(centers + 3 * sph);
+                C[k].y = __ldg(centers + 3 * sph + 1);
+                C[k].z = __ldg(centers + 3 * sph + 2);
+                const uint32_t leaf = descend(C[k].x, C[k].y, C[k].z, t, Ts);
                 float4 a, b;
                 load_leaf(t.leaves, leaf, a, b);
                 const uint32_t cnt = __float_as_uint(b.w);
-                act[k] = cnt > 0 && box_dist2(X[k], Y[k], Z[k], a, b) <= R2[k];
+                act[k] = cnt > 0 && box_dist2(C[k].x, C[k].y, C[k].z, a, b) <= C[k].w;
                 nb[k] = act[k] ? (cnt + 3u) >> 2 : 0u;
                 fb[k] = __float_as_uint(a.w);
             }
+            any |= act[k];
         }
-        // ---- 2. compaction into the warp's entry list ----
-        for (uint32_t g = lane; g < (uint32_t)(32 * SPL); g += 32) ws->ghit[g] = 0;
+        if (!__any_sync(0xffffffffu, any)) {
+            // no sphere of the tile reaches a point's box: every flag is 0
+            if constexpr (MODE == kModeSpheres) {
+#pragma unroll
+                for (int k = 0; k < SPL; k++) {
+                    const uint64_t sph = tile * per_tile + (uint64_t)k * 32u + lane;
+                    if (sph < n_items) out[sph] = 0;
+                }
+            } else {
+                const uint64_t cfg = tile * per_tile + lane;
+                if (lane < (uint32_t)cpt && cfg < n_items) out[cfg] = 0;
+            }
+            continue;
+        }
+        // ---- 2. compaction into the warp's entry list (slot order) ----
+        if (!single)
+            for (uint32_t g = lane; g < (uint32_t)(32 * SPL); g += 32) ws->ghit[g] = 0;
         uint32_t total = 0, n_ent = 0;
 #pragma unroll
         for (int k = 0; k < SPL; k++) {
             const uint32_t mask = __ballot_sync(0xffffffffu, act[k]);
+            if (mask == 0) continue;
             const uint32_t incl = warp_incl_scan(nb[k]);
             if (act[k]) {
                 const uint32_t pos = n_ent + __popc(mask & lt_mask);
-                ws->cx[pos] = X[k];
-                ws->cy[pos] = Y[k];
-                ws->cz[pos] = Z[k];
-                ws->r2[pos] = R2[k];
-                ws->blk[pos] = fb[k];
-                ws->start[pos] = total + incl - nb[k];
+                const uint32_t start = total + incl - nb[k];
+                ws->c[pos] = C[k];
+                ws->boff[pos] = (int32_t)fb[k] - (int32_t)start;
                 ws->end[pos] = total + incl;
-                ws->grp[pos] = grp[k];
+                if constexpr (MODE == kModeSpheres) ws->grp[pos] = (uint32_t)k * 32u + lane;
+                else ws->grp[pos] = ((uint32_t)k * 32u + lane) / span;
             }
             total += __shfl_sync(0xffffffffu, incl, 31);
             n_ent += __popc(mask);
@@ -123,22 +144,25 @@ __global__ void __launch_bounds__(512) k_query(DevArgs t, const float* __restric
         __syncwarp();
         // ---- 3. load-balanced scan over all live blocks ----
         uint32_t e = 0;
+        bool tile_hit = false;
         for (uint32_t base = 0; base < total; base += 32) {
             const uint32_t p = base + lane;
             bool h = false;
             if (p < total) {
                 while (ws->end[e] <= p) e++;
-                const uint32_t g = ws->grp[e];
-                if (!ws->ghit[g]) {
-                    const uint32_t b = ws->blk[e] + (p - ws->start[e]);
-                    const float4 px = __ldg(blocks + 3 * (size_t)b);
-                    const float4 py = __ldg(blocks + 3 * (size_t)b + 1);
-                    const float4 pz = __ldg(blocks + 3 * (size_t)b + 2);
-                    const float x = ws->cx[e], y = ws->cy[e], z = ws->cz[e], rr = ws->r2[e];
-                    h = (sq_dist(x, y, z, px.x, py.x, pz.x) <= rr) | (sq_dist(x, y, z, px.y, py.y, pz.y) <= rr) |
-                        (sq_dist(x, y, z, px.z, py.z, pz.z) <= rr) | (sq_dist(x, y, z, px.w, py.w, pz.w) <= rr);
-                    if (h) ws->ghit[g] = 1;
+                if (single) {
+                    h = block_hit(blocks, ws->boff[e] + (int32_t)p, ws->c[e]);
+                } else {
+                    const uint32_t g = ws->grp[e];
+                    if (!ws->ghit[g]) {
+                        h = block_hit(blocks, ws->boff[e] + (int32_t)p, ws->c[e]);
+                        if (h) ws->ghit[g] = 1;
+                    }
                 }
+            }
+            if (single) {
+                if (__any_sync(0xffffffffu, h)) { tile_hit = true; break; }
+                continue;
             }
             __syncwarp();
             if (__any_sync(0xffffffffu, h)) {
@@ -158,10 +182,8 @@ __global__ void __launch_bounds__(512) k_query(DevArgs t, const float* __restric
                 if (sph < n_items) out[sph] = act[k] ? (uint8_t)ws->ghit[k * 32 + lane] : (uint8_t)0;
             }
         } else {
-            if (lane < (uint32_t)cpt) {
-                const uint64_t cfg = tile * per_tile + lane;
-                if (cfg < n_items) out[cfg] = (uint8_t)ws->ghit[lane];
-            }
+            const uint64_t cfg = tile * per_tile + lane;
+            if (lane < (uint32_t)cpt && cfg < n_items) out[cfg] = single ? (uint8_t)tile_hit : (uint8_t)ws->ghit[lane];
         }
         __syncwarp();
     }
@@ -178,7 +200,7 @@ __global__ void k_count_configs(DevArgs t, const float* __restrict__ centers, co
         for (int s = 0; s < S; s++) {
             const float* x = centers + 3 * (c * (uint64_t)S + s);
             const float r = radii[s], r2 = __fmul_rn(r, r);
-            const uint32_t leaf = descend(x[0], x[1], x[2], t.T, nullptr, 0, t.L);
+            const uint32_t leaf = descend(x[0], x[1], x[2], t, nullptr);
             float4 a, b;
             load_leaf(t.leaves, leaf, a, b);
             nsph++;
@@ -210,7 +232,7 @@ __global__ void k_count_configs(DevArgs t, const float* __restrict__ centers, co
 
 __global__ void k_leaves(DevArgs t, const float* __restrict__ centers, uint64_t m, uint32_t* __restrict__ leaves) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m) leaves[i] = descend(centers[3 * i], centers[3 * i + 1], centers[3 * i + 2], t.T, nullptr, 0, t.L);
+    if (i < m) leaves[i] = descend(centers[3 * i], centers[3 * i + 1], centers[3 * i + 2], t, nullptr);
 }
 
 // ------------------------------------------------------------------------------------
@@ -286,11 +308,11 @@ int launch_query(const DevArgs& t, int mode, const float* centers, const float* 
         if (spl > 4) { err = "configurations of more than 64 spheres need more slots than a warp holds"; return CAPT_E_ARG; }
         cpt = spl / rows;
     }
-    const bool stage = cfg.staging == CAPT_STAGE_SMEM && t.L > 0;
+    const bool stage = cfg.staging == CAPT_STAGE_SMEM && t.stage_floats > 0;
     QueryKernel fn = mode == kModeSpheres ? pick_query<kModeSpheres>(spl, stage) : pick_query<kModeConfigs>(spl, stage);
     if (!fn) { err = "unsupported spheres_per_lane"; return CAPT_E_ARG; }
     const int warps = std::max(1, std::min(16, (int)cfg.warps_per_block));
-    const size_t smem = (stage ? ((stage_bytes(t.L) + 127u) & ~127u) : 0u) + scratch_bytes(spl) * (size_t)warps;
+    const size_t smem = (stage ? stage_offset(t) : 0u) + scratch_bytes(spl) * (size_t)warps;
     cudaError_t ce = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (ce != cudaSuccess) { err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
     const int occ = std::max(1, occupancy((const void*)fn, warps * 32, smem));
