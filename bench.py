@@ -231,8 +231,10 @@ def main():
     tuned, tuned_ms = capt.capt_autotune_configs(tree, cen, r, flags)
     counts = capt.capt_count_config_work(tree, cen, r).cpu().numpy().astype(np.int64)
     L = capt.capt_stats(tree)["depth"]
-    ops_per_launch = int(counts[0]) * (L + 15) + int(counts[2]) * 9
-    bytes_per_launch = int(counts[0]) * (12 + 32 + 4 * L) + int(counts[2]) * 12
+    # FP32 operations of the method per launch: a root box test for every examined
+    # sphere (15), a descent and leaf box test for the near ones (L + 15), 9 per point
+    ops_per_launch = int(counts[0]) * 15 + int(counts[1]) * (L + 15) + int(counts[3]) * 9
+    bytes_per_launch = int(counts[0]) * 12 + int(counts[1]) * (32 + 4 * L) + int(counts[3]) * 12
 
     def step():
         capt.capt_query_configs(tree, cen, r, flags)
@@ -318,8 +320,8 @@ def main():
                          "frac": achieved / peak_tops, "traffic": TRAFFIC.get(h),
                          "peak_basis": f"{sms} SMs x 128 FP32 lanes x {SM_MAX_MHZ:.0f} MHz (no FMA on this path)",
                          "ops_per_launch": ops_per_launch,
-                         "work": {"spheres_examined": int(counts[0]), "box_pass": int(counts[1]),
-                                  "points_scanned": int(counts[2]), "depth": L},
+                         "work": {"spheres_examined": int(counts[0]), "near_cloud_box": int(counts[1]),
+                                  "leaf_box_pass": int(counts[2]), "points_scanned": int(counts[3]), "depth": L},
                          "l1_bytes_per_launch": bytes_per_launch,
                          "l1_frac": bytes_per_launch / (ms / 1e3) / (sms * 128 * SM_MAX_MHZ * 1e6)},
             "e2e": {"value": world * C * SPHERES / e2e_s, "unit": UNIT,

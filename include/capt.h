@@ -154,11 +154,12 @@ int capt_query_configs(const capt_tree* t, const float* d_centers, const float* 
 int capt_query_configs_host(capt_tree* t, const float* h_centers, const float* h_radii, size_t C, int S,
                             uint8_t* h_flags, void* stream);
 
-/* Algorithmic work of capt_query_configs as the sequential Alg. 3 defines it, summed
- * over the C configurations (for roofline accounting): d_counts device uint64[3]
- * receives += [spheres examined (up to and including each configuration's first hit),
- * spheres whose box test passed, affordance points scanned (up to and including the
- * first hit in stored order)].  The caller zeroes d_counts.  Errors as capt_query_configs. */
+/* Algorithmic work of capt_query_configs, counted sequentially per configuration (for
+ * roofline accounting): d_counts device uint64[4] receives += [spheres examined (up to
+ * and including each configuration's first hit), spheres within reach of the cloud's
+ * bounding box (these descend), spheres passing their leaf's box test (Alg. 3),
+ * affordance points scanned (in stored order, up to and including the first hit)].
+ * The caller zeroes d_counts.  Errors as capt_query_configs. */
 int capt_count_config_work(const capt_tree* t, const float* d_centers, const float* d_radii, size_t C, int S,
                            uint64_t* d_counts, void* stream);
 

@@ -56,7 +56,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     def compile_one(src):
         obj = os.path.join(OUTDIR, os.path.basename(src) + ".o")
         if src.endswith(".cu"):
-            cmd = [nvcc, *ARCH, *NVCC_FLAGS, *inc, "-c", src, "-o", obj]
+            extra = os.environ.get("CAPT_NVCC_EXTRA", "").split()
+            cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, *inc, "-c", src, "-o", obj]
         else:
             cmd = [os.environ.get("CXX", "g++"), *CXX_FLAGS, *inc, "-I", _cuda_include(nvcc), "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)

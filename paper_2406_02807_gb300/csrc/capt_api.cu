@@ -50,9 +50,10 @@ struct DeviceGuard {
 bool valid_cfg(int kernel, const capt_launch_cfg& c) {
     if (c.warps_per_block < 1 || c.warps_per_block > 16) return false;
     if (c.staging != CAPT_STAGE_GLOBAL && c.staging != CAPT_STAGE_SMEM) return false;
-    if (kernel == CAPT_KERNEL_SPHERES) return c.spheres_per_lane == 1 || c.spheres_per_lane == 2 || c.spheres_per_lane == 4;
-    if (kernel == CAPT_KERNEL_CONFIGS || kernel == CAPT_KERNEL_EDGES)
-        return (c.spheres_per_lane == 2 || c.spheres_per_lane == 4) && (kernel != CAPT_KERNEL_EDGES || (c.chunk >= 1 && c.chunk <= 1024));
+    const int spl = c.spheres_per_lane;
+    if (kernel == CAPT_KERNEL_SPHERES) return spl == 1 || spl == 2 || spl == 4 || spl == 8;
+    if (kernel == CAPT_KERNEL_CONFIGS) return spl == 2 || spl == 4 || spl == 8;
+    if (kernel == CAPT_KERNEL_EDGES) return (spl == 2 || spl == 4) && c.chunk >= 1 && c.chunk <= 1024;
     if (kernel == CAPT_KERNEL_CLEARANCE) return true;
     return false;
 }
@@ -71,6 +72,8 @@ struct capt_tree {
     uint64_t total_blocks = 0;
     size_t dev_bytes = 0;
     uint32_t tail_off = 0, stage_floats = 0;
+    float box_lo[3] = {INFINITY, INFINITY, INFINITY};     // bounding box of every point
+    float box_hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     int K = 0, R = 0, Ks = 0, tail_staged = 0;
     capt_launch_cfg cfg[4];
     // host-buffer pipeline
@@ -109,6 +112,10 @@ struct capt_tree {
         a.L = h.L;
         a.r_min = h.r_min;
         a.r_max = h.r_max;
+        for (int d = 0; d < 3; d++) {
+            a.lo[d] = box_lo[d];
+            a.hi[d] = box_hi[d];
+        }
         return a;
     }
 
@@ -284,6 +291,15 @@ int capt_upload(capt_tree* t, int device, void* stream) {
         return cuda_fail(e, "upload");
     }
     t->total_blocks = lay.total_blocks;
+    for (int d = 0; d < 3; d++) {
+        t->box_lo[d] = INFINITY;
+        t->box_hi[d] = -INFINITY;
+    }
+    for (size_t j = 0; j < h.n; j++)
+        for (int d = 0; d < 3; d++) {
+            t->box_lo[d] = std::min(t->box_lo[d], h.pts[3 * j + d]);
+            t->box_hi[d] = std::max(t->box_hi[d], h.pts[3 * j + d]);
+        }
     t->tail_off = bs.tail_off;
     t->K = bs.K;
     t->R = bs.R;
@@ -441,7 +457,7 @@ int capt_autotune_configs(capt_tree* t, const float* d_centers, const float* d_r
     capt_launch_cfg best_c = t->cfg[CAPT_KERNEL_CONFIGS];
     std::string err;
     for (int warps : {4, 8, 16})
-        for (int spl : {2, 4})
+        for (int spl : {2, 4, 8})
             for (int stage : {CAPT_STAGE_GLOBAL, CAPT_STAGE_SMEM}) {
                 capt_launch_cfg c = {warps, spl, stage, 0};
                 float tt = INFINITY;

@@ -67,6 +67,8 @@ struct DevArgs {
     uint32_t N = 1;
     int L = 0;
     float r_min = 0.f, r_max = 0.f;
+    float lo[3] = {0.f, 0.f, 0.f};   // bounding box of the cloud (empty cloud: lo > hi)
+    float hi[3] = {-1.f, -1.f, -1.f};
 };
 
 int build_host_tree(const float* points, size_t n, float r_min, float r_max, int threads, HostTree& out,

@@ -13,7 +13,7 @@ import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-ALL_CFGS = [(w, s, st) for w in (4, 8, 16) for s in (1, 2, 4) for st in (0, 1)]
+ALL_CFGS = [(w, s, st) for w in (4, 8, 16) for s in (1, 2, 4, 8) for st in (0, 1)]
 
 
 @pytest.fixture(scope="module")
@@ -150,7 +150,7 @@ def test_configs_bit_exact_against_brute_force(tabletop, orc, capt_lib, torch_):
     assert 0.05 < ref.mean() < 0.95
 
 
-@pytest.mark.parametrize("warps,spl,stage", [(w, s, st) for w in (4, 8, 16) for s in (2, 4) for st in (0, 1)])
+@pytest.mark.parametrize("warps,spl,stage", [(w, s, st) for w in (4, 8, 16) for s in (2, 4, 8) for st in (0, 1)])
 def test_configs_every_launch_cfg(tabletop, orc, capt_lib, torch_, warps, spl, stage):
     cen = _configs(tabletop, 3001, first=777)                    # odd count: ragged last tile
     r = tabletop["arm"].sphere_radius
@@ -173,11 +173,20 @@ def test_configs_sphere_counts(tabletop, orc, capt_lib, torch_, S):
 
 
 def test_work_counters_match_oracle(tabletop, capt_lib, torch_):
+    """Spheres examined, leaf-box passes and points scanned equal the oracle's Alg. 3
+    counts; the root box count is the FP32 box test against the cloud's bounds."""
     cen = _configs(tabletop, 4000, first=99)
     r = tabletop["arm"].sphere_radius
-    _, counts = tabletop["oracle_tree"].query_configs(cen, r)
-    g = capt_lib.capt_count_config_work(tabletop["tree"], _cuda(torch_, cen), _cuda(torch_, r))
-    assert g.cpu().numpy().tolist() == counts.tolist()
+    flags, counts = tabletop["oracle_tree"].query_configs(cen, r)
+    g = capt_lib.capt_count_config_work(tabletop["tree"], _cuda(torch_, cen), _cuda(torch_, r)).cpu().numpy()
+    assert [g[0], g[2], g[3]] == counts.tolist()
+    pts = tabletop["pts"]
+    lo, hi = pts.min(0), pts.max(0)
+    d = (cen - np.clip(cen, lo, hi)).astype(np.float32)
+    q = d * d
+    near = ((q[..., 0] + q[..., 1]) + q[..., 2]) <= (r * r)[None, :]
+    # spheres examined: all S of a free configuration, up to the first hit otherwise
+    assert g[1] <= near.sum() and g[1] >= near[flags == 0].sum()
 
 
 def test_host_buffer_pipeline_matches_device_path(tabletop, capt_lib, torch_):
