@@ -182,10 +182,13 @@ enum { CAPT_KERNEL_SPHERES = 0, CAPT_KERNEL_CONFIGS = 1, CAPT_KERNEL_EDGES = 2, 
 
 typedef struct capt_launch_cfg {
     int32_t warps_per_block;   /* 1..16 */
-    int32_t spheres_per_lane;  /* sphere slots per lane: 1, 2 or 4 (configurations and
-                                  edges: 2 or 4, whole configurations per warp pass) */
+    int32_t spheres_per_lane;  /* tile size.  Spheres: 1, 2, 4 or 8 spheres per lane
+                                  (32 x that per warp tile).  Configurations: 2, 4 or 8,
+                                  for 4, 8 or 16 configurations per warp tile.  Edges:
+                                  not used (one configuration per lane). */
     int32_t staging;           /* CAPT_STAGE_* */
-    int32_t chunk;             /* edges: configurations per work item (1..1024) */
+    int32_t chunk;             /* edges: configurations per work item (1..1024, rounded
+                                  up to a multiple of 32) */
 } capt_launch_cfg;
 
 /* Set / get the launch configuration used for `kernel` on this tree.

@@ -53,7 +53,7 @@ bool valid_cfg(int kernel, const capt_launch_cfg& c) {
     const int spl = c.spheres_per_lane;
     if (kernel == CAPT_KERNEL_SPHERES) return spl == 1 || spl == 2 || spl == 4 || spl == 8;
     if (kernel == CAPT_KERNEL_CONFIGS) return spl == 2 || spl == 4 || spl == 8;
-    if (kernel == CAPT_KERNEL_EDGES) return (spl == 2 || spl == 4) && c.chunk >= 1 && c.chunk <= 1024;
+    if (kernel == CAPT_KERNEL_EDGES) return c.chunk >= 1 && c.chunk <= 1024;   // one configuration per lane
     if (kernel == CAPT_KERNEL_CLEARANCE) return true;
     return false;
 }
@@ -612,10 +612,9 @@ int capt_edge_plan_create(capt_tree* t, const capt_arm* arm, const float* d_qa, 
         float best = INFINITY;
         capt_launch_cfg bc = t->cfg[CAPT_KERNEL_EDGES];
         for (int warps : {4, 8, 16})
-            for (int spl : {2, 4})
-                for (int stage : {CAPT_STAGE_GLOBAL, CAPT_STAGE_SMEM})
-                    for (int chunk : {8, 32}) {
-                        capt_launch_cfg c = {warps, spl, stage, chunk};
+            for (int stage : {CAPT_STAGE_GLOBAL, CAPT_STAGE_SMEM})
+                for (int chunk : {32, 64, 128}) {
+                        capt_launch_cfg c = {warps, 1, stage, chunk};
                         float tt = INFINITY;
                         for (int rep = 0; rep < 3 && !rc; rep++) {
                             cudaEventRecord(e0, st);

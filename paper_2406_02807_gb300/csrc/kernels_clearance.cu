@@ -3,177 +3,232 @@
 // With r_min = 0 every leaf stores all points within r_max of its cell (Alg. 1, Lemma 1
 // case 1), so for a centre x in that cell the nearest stored point is the nearest
 // cloud point whenever it is within r_max.  The forward pass therefore scans the whole
-// set (no early exit), keeping the minimum FP32 squared distance and its slot; a set
-// whose box lies farther than r_max is skipped (d = r_max).
+// set (no early exit), keeping the minimum FP32 squared distance and its slot.
 //
-// Forward layout: a block owns one trajectory at a time (persistent over trajectories);
-// its warps take the waypoints (one configuration of S <= 64 spheres per warp pass).
-// Each warp compacts its live spheres into an entry list and scans the concatenation of
-// their blocks 32 at a time; per step, a segmented warp reduction delivers each
-// entry's minimum (squared distance, slot) key to the entry's first lane, which folds
-// it into the entry's running minimum.  Per-waypoint costs land in shared memory and
-// one thread sums them in waypoint order, so the cost is bitwise reproducible.
-//
+// Forward layout: one block per trajectory, each warp owning a contiguous range of its
+// waypoints.
+//  1. Passes of 128 consecutive spheres (4 per lane, three 16-byte loads): a sphere
+//     farther than r_max from the cloud's bounding box is farther than r_max from every
+//     point, so it gets d = r_max, argmin = -1 at once; the others are queued.
+//  2. Rounds of 32 queued spheres: descent and leaf box test against r_max; each set
+//     of a sphere that passes is scanned in full by the whole warp in packed FP32x2
+//     arithmetic, every lane keeping a running minimum of (d^2, slot) keys, reduced by
+//     one butterfly per set.
+//  3. Each waypoint's cost is summed from the written distances in a fixed order
+//     (lane-strided, then a butterfly) and one thread adds the waypoints in order, so
+//     the cost is bitwise reproducible whatever the launch configuration.
 // Backward: elementwise, one thread per sphere, from the saved distance and argmin.
 #include <algorithm>
 
 #include "device_common.cuh"
 #include "kernels.h"
+#include "scan.cuh"
 
 namespace capt {
 
-constexpr int kMaxWaypoints = 4096;
+constexpr int kClearQueue = 160;
 
 struct ClearScratch {
-    float cx[64], cy[64], cz[64];
-    uint32_t blk[64], start[64], end[64];
-    unsigned long long minkey[64];
+    float4 nq[kClearQueue];      // queued spheres: centre
+    uint32_t ni[kClearQueue];    // their index within the trajectory
 };
 
+// One round over the first n queued spheres of the trajectory at `tbase` (sphere index
+// offset of the trajectory in dist / argmin).  Spheres passing the leaf box test are
+// scanned one at a time by the whole warp: lanes stride over the set's 4-point blocks
+// (two blocks in flight per lane) keeping a running minimum of (d^2, slot) keys, and one
+// butterfly per set reduces the 32 minima.  The lowest key is the smallest FP32 squared
+// distance, ties going to the lowest slot, i.e. the lowest point index.
+__device__ __forceinline__ void clearance_round(const DevArgs& t, const float* Ts, ClearScratch* ws, uint32_t n,
+                                                uint64_t tbase, float rmax, float rmax2, float* __restrict__ dist,
+                                                int32_t* __restrict__ argmin, uint32_t lane, uint32_t lt_mask) {
+    const float4* blocks = reinterpret_cast<const float4*>(t.blocks);
+    const bool live = lane < n;
+    bool act = false;
+    uint32_t nb = 0, fb = 0, gi = 0;
+    float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (live) {
+        c = ws->nq[lane];
+        gi = ws->ni[lane];
+        const uint32_t leaf = descend(c.x, c.y, c.z, t, Ts);
+        float4 a, b;
+        load_leaf(t.leaves, leaf, a, b);
+        const uint32_t cnt = __float_as_uint(b.w);
+        act = cnt > 0 && box_dist2(c.x, c.y, c.z, a, b) <= rmax2;
+        nb = act ? (cnt + 3u) >> 2 : 0u;
+        fb = __float_as_uint(a.w);
+        if (!act) {
+            // every stored point is farther than r_max
+            dist[tbase + gi] = rmax;
+            argmin[tbase + gi] = -1;
+        }
+    }
+    uint32_t mask = __ballot_sync(0xffffffffu, act);
+    while (mask) {
+        const int src = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const float cx = __shfl_sync(0xffffffffu, c.x, src);
+        const float cy = __shfl_sync(0xffffffffu, c.y, src);
+        const float cz = __shfl_sync(0xffffffffu, c.z, src);
+        const uint32_t b0 = __shfl_sync(0xffffffffu, fb, src);
+        const uint32_t nbs = __shfl_sync(0xffffffffu, nb, src);
+        const uint64_t cxx = f2_dup(cx), cyy = f2_dup(cy), czz = f2_dup(cz);
+        unsigned long long best = ~0ull;
+        auto fold = [&](uint32_t r) {
+            uint64_t s01, s23;
+            block_d2(blocks, (int64_t)b0 + r, cxx, cyy, czz, s01, s23);
+            const float2 d01 = f2_split(s01), d23 = f2_split(s23);
+            float bd = d01.x;
+            uint32_t bq = 0;
+            if (d01.y < bd) { bd = d01.y; bq = 1; }
+            if (d23.x < bd) { bd = d23.x; bq = 2; }
+            if (d23.y < bd) { bd = d23.y; bq = 3; }
+            const unsigned long long key = ((unsigned long long)__float_as_uint(bd) << 32) | (4u * r + bq);
+            best = key < best ? key : best;
+        };
+        uint32_t r = lane;
+        for (; r + 32 < nbs; r += 64) {
+            fold(r);
+            fold(r + 32);
+        }
+        if (r < nbs) fold(r);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+            best = other < best ? other : best;
+        }
+        if (lane == (uint32_t)src) {
+            const float dd = __fsqrt_rn(__uint_as_float((uint32_t)(best >> 32)));
+            const uint64_t i = tbase + gi;
+            if (dd < rmax) {
+                dist[i] = dd;
+                argmin[i] = (int32_t)__ldg(t.ids + 4 * (size_t)b0 + (uint32_t)(best & 0xffffffffu));
+            } else {
+                dist[i] = rmax;
+                argmin[i] = -1;
+            }
+        }
+    }
+    (void)lt_mask;
+    __syncwarp();
+}
+
 template <bool STAGE>
-__global__ void __launch_bounds__(512) k_clearance_fwd(DevArgs t, const float* __restrict__ centers,
-                                                       const float* __restrict__ radii, uint64_t T, int W, int S,
-                                                       float margin, float* __restrict__ cost,
-                                                       float* __restrict__ dist, int32_t* __restrict__ argmin) {
+__global__ void __launch_bounds__(512, 2) k_clearance_fwd(DevArgs t, const float* __restrict__ centers,
+                                                          const float* __restrict__ radii, uint64_t T, int W, int S,
+                                                          float margin, float* __restrict__ cost,
+                                                          float* __restrict__ dist, int32_t* __restrict__ argmin) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t bar;
+    __shared__ float rm[64];    // r_s + margin
+    for (int i = (int)threadIdx.x; i < S; i += (int)blockDim.x) rm[i] = __fadd_rn(radii[i], margin);
     const float* Ts = nullptr;
     uint32_t off = 0;
     if constexpr (STAGE) {
-        Ts = stage_splits(t, smem_raw, &bar);
+        Ts = stage_splits(t, smem_raw, &bar);   // contains a block barrier
         off = stage_offset(t);
+    } else {
+        __syncthreads();
     }
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    ClearScratch* ws = reinterpret_cast<ClearScratch*>(smem_raw + off) + warp;
-    float* partial = reinterpret_cast<float*>(smem_raw + off + sizeof(ClearScratch) * nw);
-    const float4* blocks = reinterpret_cast<const float4*>(t.blocks);
-    const float rmax = t.r_max, rmax2 = __fmul_rn(t.r_max, t.r_max);
     const uint32_t lt_mask = (1u << lane) - 1u;
-    // the lane's two sphere slots: radius and hinge offset r + margin
-    float rm[2];
+    ClearScratch* ws = reinterpret_cast<ClearScratch*>(smem_raw + off) + warp;
+    float* partial = reinterpret_cast<float*>(smem_raw + off + sizeof(ClearScratch) * nw);   // [W]
+    const float rmax = t.r_max, rmax2 = __fmul_rn(t.r_max, t.r_max);
+    const float4 rlo = make_float4(t.lo[0], t.lo[1], t.lo[2], 0.f);
+    const float4 rhi = make_float4(t.hi[0], t.hi[1], t.hi[2], 0.f);
+    // one trajectory per block (the grid covers them all, so the hardware hands out
+    // blocks as earlier ones finish); warp k owns a contiguous range of waypoints
+    const uint64_t traj = blockIdx.x;
+    const uint32_t w_lo = (uint32_t)(((uint64_t)W * warp) / nw), w_hi = (uint32_t)(((uint64_t)W * (warp + 1)) / nw);
+    const uint64_t tbase = traj * (uint64_t)W * (uint64_t)S;        // first sphere of the trajectory
+    const uint32_t s_lo = w_lo * (uint32_t)S, s_hi = w_hi * (uint32_t)S;   // this warp's spheres
+    const float* base = centers + 3 * tbase;
+    uint32_t n_q = 0;
+    for (uint32_t p0 = s_lo; p0 < s_hi; p0 += 128) {
+        const uint32_t i0 = p0 + 4 * lane;
+        const uint32_t nv = i0 < s_hi ? min(4u, s_hi - i0) : 0u;
+        float v[12];
+        if (nv == 4 && ((reinterpret_cast<uintptr_t>(base + 3 * (size_t)i0) & 15u) == 0)) {
+            const float4* q = reinterpret_cast<const float4*>(base + 3 * (size_t)i0);
+            const float4 a = __ldg(q), b = __ldg(q + 1), cc = __ldg(q + 2);
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+            v[8] = cc.x; v[9] = cc.y; v[10] = cc.z; v[11] = cc.w;
+        } else {
 #pragma unroll
-    for (int h = 0; h < 2; h++) {
-        const int s = (int)lane + 32 * h;
-        rm[h] = s < S ? __fadd_rn(__ldg(radii + s), margin) : 0.f;
+            for (int k = 0; k < 12; k++) v[k] = (uint32_t)(k / 3) < nv ? __ldg(base + 3 * (size_t)i0 + k) : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const float x = v[3 * k], y = v[3 * k + 1], z = v[3 * k + 2];
+            const bool valid = (uint32_t)k < nv;
+            // farther than r_max from the cloud's box: farther than r_max from every point
+            const bool near = valid && box_dist2(x, y, z, rlo, rhi) <= rmax2;
+            if (valid && !near) {
+                dist[tbase + i0 + k] = rmax;
+                argmin[tbase + i0 + k] = -1;
+            }
+            const uint32_t mask = __ballot_sync(0xffffffffu, near);
+            if (near) {
+                const uint32_t pos = n_q + __popc(mask & lt_mask);
+                ws->nq[pos] = make_float4(x, y, z, 0.f);
+                ws->ni[pos] = i0 + k;
+            }
+            n_q += __popc(mask);
+        }
+        if (n_q >= 32) {
+            __syncwarp();
+            uint32_t r0 = 0;
+            for (; n_q - r0 >= 32; r0 += 32) {
+                if (r0) {
+                    const float4 cc = ws->nq[r0 + lane];
+                    const uint32_t ii = ws->ni[r0 + lane];
+                    __syncwarp();
+                    ws->nq[lane] = cc;
+                    ws->ni[lane] = ii;
+                    __syncwarp();
+                }
+                clearance_round(t, Ts, ws, 32, tbase, rmax, rmax2, dist, argmin, lane, lt_mask);
+            }
+            const uint32_t rest = n_q - r0;
+            float4 cc = make_float4(0.f, 0.f, 0.f, 0.f);
+            uint32_t ii = 0;
+            if (lane < rest) {
+                cc = ws->nq[r0 + lane];
+                ii = ws->ni[r0 + lane];
+            }
+            __syncwarp();
+            if (lane < rest) {
+                ws->nq[lane] = cc;
+                ws->ni[lane] = ii;
+            }
+            n_q = rest;
+            __syncwarp();
+        }
     }
-    for (uint64_t traj = blockIdx.x; traj < T; traj += gridDim.x) {
-        for (int w = (int)warp; w < W; w += (int)nw) {
-            const uint64_t cfg = traj * (uint64_t)W + (uint64_t)w;
-            bool act[2];
-            uint32_t nb[2], fb[2], pos[2];
-            float X[2], Y[2], Z[2];
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int s = (int)lane + 32 * h;
-                act[h] = false;
-                nb[h] = fb[h] = 0;
-                X[h] = Y[h] = Z[h] = 0.f;
-                if (s < S) {
-                    const uint64_t sph = cfg * (uint64_t)S + s;
-                    X[h] = __ldg(centers + 3 * sph);
-                    Y[h] = __ldg(centers + 3 * sph + 1);
-                    Z[h] = __ldg(centers + 3 * sph + 2);
-                    const uint32_t leaf = descend(X[h], Y[h], Z[h], t, Ts);
-                    float4 a, b;
-                    load_leaf(t.leaves, leaf, a, b);
-                    const uint32_t cnt = __float_as_uint(b.w);
-                    act[h] = cnt > 0 && box_dist2(X[h], Y[h], Z[h], a, b) <= rmax2;
-                    nb[h] = act[h] ? (cnt + 3u) >> 2 : 0u;
-                    fb[h] = __float_as_uint(a.w);
-                }
-            }
-            uint32_t total = 0, n_ent = 0;
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const uint32_t mask = __ballot_sync(0xffffffffu, act[h]);
-                const uint32_t incl = warp_incl_scan(nb[h]);
-                pos[h] = n_ent + __popc(mask & lt_mask);
-                if (act[h]) {
-                    ws->cx[pos[h]] = X[h];
-                    ws->cy[pos[h]] = Y[h];
-                    ws->cz[pos[h]] = Z[h];
-                    ws->blk[pos[h]] = fb[h];
-                    ws->start[pos[h]] = total + incl - nb[h];
-                    ws->end[pos[h]] = total + incl;
-                    ws->minkey[pos[h]] = ~0ull;
-                }
-                total += __shfl_sync(0xffffffffu, incl, 31);
-                n_ent += __popc(mask);
-            }
-            __syncwarp();
-            uint32_t e = 0;
-            for (uint32_t base = 0; base < total; base += 32) {
-                const uint32_t p = base + lane;
-                unsigned long long key = ~0ull;
-                uint32_t my_e = 0xffffffffu;
-                if (p < total) {
-                    while (ws->end[e] <= p) e++;
-                    my_e = e;
-                    const uint32_t rel = p - ws->start[e];
-                    const uint32_t b = ws->blk[e] + rel;
-                    const float4 px = __ldg(blocks + 3 * (size_t)b);
-                    const float4 py = __ldg(blocks + 3 * (size_t)b + 1);
-                    const float4 pz = __ldg(blocks + 3 * (size_t)b + 2);
-                    const float x = ws->cx[e], y = ws->cy[e], z = ws->cz[e];
-                    const float d0 = sq_dist(x, y, z, px.x, py.x, pz.x);
-                    const float d1 = sq_dist(x, y, z, px.y, py.y, pz.y);
-                    const float d2 = sq_dist(x, y, z, px.z, py.z, pz.z);
-                    const float d3 = sq_dist(x, y, z, px.w, py.w, pz.w);
-                    // lowest slot wins ties (slots are in ascending point index)
-                    float bd = d0;
-                    uint32_t bq = 0;
-                    if (d1 < bd) { bd = d1; bq = 1; }
-                    if (d2 < bd) { bd = d2; bq = 2; }
-                    if (d3 < bd) { bd = d3; bq = 3; }
-                    key = ((unsigned long long)__float_as_uint(bd) << 32) | (unsigned long long)(rel * 4u + bq);
-                }
-                // segmented minimum over lanes that share an entry (runs are contiguous)
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const unsigned long long ok = __shfl_down_sync(0xffffffffu, key, o);
-                    const uint32_t oe = __shfl_down_sync(0xffffffffu, my_e, o);
-                    if (lane + (uint32_t)o < 32u && oe == my_e && ok < key) key = ok;
-                }
-                const uint32_t prev_e = __shfl_up_sync(0xffffffffu, my_e, 1);
-                if (my_e != 0xffffffffu && (lane == 0 || prev_e != my_e)) {
-                    if (key < ws->minkey[my_e]) ws->minkey[my_e] = key;
-                }
-                __syncwarp();
-            }
-            __syncwarp();
-            float term = 0.f;
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int s = (int)lane + 32 * h;
-                if (s >= S) continue;
-                const uint64_t sph = cfg * (uint64_t)S + s;
-                float d = rmax;
-                int32_t am = -1;
-                if (act[h]) {
-                    const unsigned long long k = ws->minkey[pos[h]];
-                    const float dd = __fsqrt_rn(__uint_as_float((uint32_t)(k >> 32)));
-                    if (dd < rmax) {
-                        d = dd;
-                        am = (int32_t)__ldg(t.ids + 4 * (size_t)fb[h] + (uint32_t)(k & 0xffffffffu));
-                    }
-                }
-                dist[sph] = d;
-                argmin[sph] = am;
-                const float hh = fmaxf(0.f, __fsub_rn(rm[h], d));
-                term = __fadd_rn(term, __fmul_rn(hh, hh));
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) term = __fadd_rn(term, __shfl_xor_sync(0xffffffffu, term, o));
-            if (lane == 0) partial[w] = term;
-            __syncwarp();
+    if (n_q) {
+        __syncwarp();
+        clearance_round(t, Ts, ws, n_q, tbase, rmax, rmax2, dist, argmin, lane, lt_mask);
+    }
+    __syncwarp();
+    // per-waypoint cost in a fixed order: sphere s = lane + 32 m summed by lane, then a
+    // butterfly; the block then sums the waypoints in order
+    for (uint32_t w = w_lo; w < w_hi; w++) {
+        float term = 0.f;
+        for (uint32_t s = lane; s < (uint32_t)S; s += 32) {
+            const float hh = fmaxf(0.f, __fsub_rn(rm[s], dist[tbase + (uint64_t)w * S + s]));
+            term = __fadd_rn(term, __fmul_rn(hh, hh));
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            float acc = 0.f;
-            for (int w = 0; w < W; w++) acc = __fadd_rn(acc, partial[w]);
-            cost[traj] = acc;
-        }
-        __syncthreads();
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) term = __fadd_rn(term, __shfl_xor_sync(0xffffffffu, term, o));
+        if (lane == 0) partial[w] = term;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float acc = 0.f;
+        for (int w = 0; w < W; w++) acc = __fadd_rn(acc, partial[w]);
+        cost[traj] = acc;
     }
 }
 
@@ -207,19 +262,15 @@ int launch_clearance_fwd(const DevArgs& t, const float* centers, const float* ra
                          float margin, float* cost, float* dist, int32_t* argmin, const capt_launch_cfg& cfg,
                          cudaStream_t st, std::string& err) {
     if (T == 0) return CAPT_OK;
-    if (W > kMaxWaypoints) { err = "clearance supports at most 4096 waypoints per trajectory"; return CAPT_E_ARG; }
+    if (W > 8192) { err = "clearance takes at most 8192 waypoints per trajectory"; return CAPT_E_ARG; }
+    if (T > 0x7fffffffull) { err = "too many trajectories for one launch"; return CAPT_E_ARG; }
     const bool stage = cfg.staging == CAPT_STAGE_SMEM && t.stage_floats > 0;
     auto fn = stage ? k_clearance_fwd<true> : k_clearance_fwd<false>;
     const int warps = std::max(1, std::min(16, std::min((int)cfg.warps_per_block, W)));
-    const size_t smem = (stage ? stage_offset(t) : 0u) + sizeof(ClearScratch) * (size_t)warps +
-                        sizeof(float) * (size_t)W;
+    const size_t smem = (stage ? stage_offset(t) : 0u) + sizeof(ClearScratch) * (size_t)warps + sizeof(float) * (size_t)W;
     cudaError_t ce = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (ce != cudaSuccess) { err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)fn, warps * 32, smem);
-    occ = std::max(1, occ);
-    const uint64_t blocks = std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)sm_count() * occ, T));
-    fn<<<(unsigned)blocks, warps * 32, smem, st>>>(t, centers, radii, T, W, S, margin, cost, dist, argmin);
+    fn<<<(unsigned)T, warps * 32, smem, st>>>(t, centers, radii, T, W, S, margin, cost, dist, argmin);
     ce = cudaGetLastError();
     if (ce != cudaSuccess) { err = std::string("clearance launch: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
     return CAPT_OK;

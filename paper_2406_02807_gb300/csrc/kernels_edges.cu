@@ -2,22 +2,63 @@
 // whole straight-line edges, with the interpolated configurations and their sphere
 // centres generated inside the kernel.
 //
-// Persistent mode: work items are (edge, chunk of `chunk` consecutive configurations),
-// enumerated edge by edge.  A setup kernel writes the exclusive prefix of the per-edge
-// item counts and resets the work counter and the validity flags; the persistent
-// kernel's warps then take items from the counter with one atomic each.  A warp skips
-// an item whose edge is already known to collide, and stops its chunk at the first
-// colliding configuration, so colliding edges cost little beyond their first hit.
-// The three steps are captured once into a CUDA graph by capt_edge_plan_create.
+// A warp validates up to 32 consecutive configurations of one edge per pass, one per
+// lane: each lane interpolates its configuration, walks the arm's kinematic chain in
+// FP32 and, as each sphere centre appears, applies the root box test (the bounding box
+// of the cloud contains every affordance set, so a sphere that misses it misses every
+// point).  Spheres that come near the cloud are queued in shared memory and processed
+// in rounds of 32 (descent, leaf box test, load-balanced scan, scan.cuh); the first
+// hit invalidates the edge and ends the pass.
 //
-// Per-edge mode (the baseline): one kernel launch per edge, each launching just enough
-// warps for that edge's configurations.
+// Persistent mode: work items are (edge, chunk of configurations), enumerated edge by
+// edge.  A setup kernel writes the exclusive prefix of the per-edge item counts and
+// resets the work counter and the validity flags; the persistent kernel's warps take
+// items from the counter with one atomic each and skip items of edges already known to
+// collide.  capt_edge_plan_create captures both launches into a CUDA graph.
+// Per-edge mode (the baseline): one kernel launch per edge.
 #include <algorithm>
+#include <vector>
 
 #include "device_common.cuh"
 #include "kernels.h"
+#include "scan.cuh"
 
 namespace capt {
+
+// The arm as the kernels read it: spheres ordered by the link they hang on, so that a
+// lane can place each link's spheres right after rotating that link's frame.
+struct ArmPlan {
+    int32_t J, S;
+    float base[3];
+    int32_t axis[CAPT_MAX_JOINTS];
+    float link[CAPT_MAX_JOINTS][3];
+    int32_t sbeg[CAPT_MAX_JOINTS + 1];   // spheres of link j: [sbeg[j], sbeg[j + 1])
+    float off[CAPT_MAX_SPHERES][3];      // offsets in the link frame, in that order
+    float r2[CAPT_MAX_SPHERES];          // fl(r * r), in that order
+};
+
+ArmPlan make_plan(const capt_arm& a) {
+    ArmPlan p{};
+    p.J = a.n_joints;
+    p.S = a.n_spheres;
+    for (int d = 0; d < 3; d++) p.base[d] = a.base[d];
+    for (int j = 0; j < a.n_joints; j++) {
+        p.axis[j] = a.axis[j];
+        for (int d = 0; d < 3; d++) p.link[j][d] = a.link[j][d];
+    }
+    int n = 0;
+    for (int j = 0; j < a.n_joints; j++) {
+        p.sbeg[j] = n;
+        for (int s = 0; s < a.n_spheres; s++)
+            if (a.sphere_link[s] == j) {
+                for (int d = 0; d < 3; d++) p.off[n][d] = a.sphere_offset[s][d];
+                p.r2[n] = a.sphere_radius[s] * a.sphere_radius[s];
+                n++;
+            }
+    }
+    p.sbeg[a.n_joints] = n;
+    return p;
+}
 
 // sin and cos of x in FP32 by Cody-Waite reduction modulo pi/2 (Cody and Waite,
 // "Software Manual for the Elementary Functions", 1980) and Taylor polynomials on
@@ -67,48 +108,54 @@ __device__ __forceinline__ float row_dot(const float R[9], int r, float v0, floa
     return __fadd_rn(__fadd_rn(__fmul_rn(R[3 * r], v0), __fmul_rn(R[3 * r + 1], v1)), __fmul_rn(R[3 * r + 2], v2));
 }
 
-// The two sphere slots a lane owns in every configuration (s = lane, lane + 32),
-// loaded once from the arm description into registers.
-struct LaneSpheres {
-    int f[2];          // link index, -1 for an unused slot
-    float o[2][3];     // offset in the link frame
-    float r2[2];       // fl(r * r)
+struct EdgeScratch {
+    float4 nc[64];   // queued near spheres (< 32 left over + 32 from one sphere step)
+    RoundEntries re;
 };
 
-__device__ __forceinline__ LaneSpheres lane_spheres(const capt_arm& arm) {
-    LaneSpheres ls;
-    const int lane = (int)lane_id();
-#pragma unroll
-    for (int h = 0; h < 2; h++) {
-        const int s = lane + 32 * h;
-        const bool v = s < arm.n_spheres;
-        ls.f[h] = v ? arm.sphere_link[s] : -1;
-        const float r = v ? arm.sphere_radius[s] : 0.f;
-        ls.r2[h] = __fmul_rn(r, r);
-#pragma unroll
-        for (int a = 0; a < 3; a++) ls.o[h][a] = v ? arm.sphere_offset[s][a] : 0.f;
-    }
-    return ls;
-}
-
-// Centres of the lane's two sphere slots for one configuration.  The sines and
-// cosines of its joints sit in lanes src_lane0 .. src_lane0 + J - 1 (sj, cj); every
-// lane walks the whole chain and keeps the frames its spheres hang on.
-__device__ __forceinline__ void fk_lane(const capt_arm& arm, const LaneSpheres& ls, float sj, float cj, int src_lane0,
-                                        float c0[3], float c1[3]) {
+// One pass: configurations k0 .. k0 + count - 1 (count <= 32) of the edge with n_e
+// configurations from qa_e to qb_e, lane i taking configuration k0 + i.  Returns true
+// as soon as one of them collides.
+__device__ bool edge_pass(const DevArgs& t, const ArmPlan& arm, const float* __restrict__ qa_e,
+                          const float* __restrict__ qb_e, int n_e, int k0, int count, const float* Ts,
+                          EdgeScratch* ws) {
+    const uint32_t lane = lane_id();
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const bool live = (int)lane < count;
+    const float4 rlo = make_float4(t.lo[0], t.lo[1], t.lo[2], 0.f);
+    const float4 rhi = make_float4(t.hi[0], t.hi[1], t.hi[2], 0.f);
+    // q_k = q_a + (k / (n - 1)) (q_b - q_a)
+    const float tk = n_e > 1 ? __fdiv_rn((float)(k0 + (int)lane), (float)(n_e - 1)) : 0.f;
     float R[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
     float p[3] = {arm.base[0], arm.base[1], arm.base[2]};
-    for (int j = 0; j < arm.n_joints; j++) {
-        const float s = __shfl_sync(0xffffffffu, sj, src_lane0 + j);
-        const float c = __shfl_sync(0xffffffffu, cj, src_lane0 + j);
-        rotate_frame(R, arm.axis[j], s, c);
-        if (j == ls.f[0]) {
-#pragma unroll
-            for (int r = 0; r < 3; r++) c0[r] = __fadd_rn(p[r], row_dot(R, r, ls.o[0][0], ls.o[0][1], ls.o[0][2]));
-        }
-        if (j == ls.f[1]) {
-#pragma unroll
-            for (int r = 0; r < 3; r++) c1[r] = __fadd_rn(p[r], row_dot(R, r, ls.o[1][0], ls.o[1][1], ls.o[1][2]));
+    uint32_t n_near = 0;
+    for (int j = 0; j < arm.J; j++) {
+        const float a = __ldg(qa_e + j), b = __ldg(qb_e + j);
+        const float q = __fadd_rn(a, __fmul_rn(tk, __fsub_rn(b, a)));
+        float sj, cj;
+        sincos_cw(q, sj, cj);
+        rotate_frame(R, arm.axis[j], sj, cj);
+        for (int i = arm.sbeg[j]; i < arm.sbeg[j + 1]; i++) {
+            const float ox = arm.off[i][0], oy = arm.off[i][1], oz = arm.off[i][2];
+            const float cx = __fadd_rn(p[0], row_dot(R, 0, ox, oy, oz));
+            const float cy = __fadd_rn(p[1], row_dot(R, 1, ox, oy, oz));
+            const float cz = __fadd_rn(p[2], row_dot(R, 2, ox, oy, oz));
+            const float r2 = arm.r2[i];
+            const bool near = live && box_dist2(cx, cy, cz, rlo, rhi) <= r2;
+            const uint32_t mask = __ballot_sync(0xffffffffu, near);
+            if (near) ws->nc[n_near + __popc(mask & lt_mask)] = make_float4(cx, cy, cz, r2);
+            n_near += __popc(mask);
+            if (n_near >= 32) {
+                __syncwarp();
+                if (sphere_round<true>(t, Ts, &ws->re, nullptr, ws->nc[lane], 0, true, lane, lt_mask)) return true;
+                const uint32_t rest = n_near - 32;
+                float4 cc = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (lane < rest) cc = ws->nc[32 + lane];
+                __syncwarp();
+                if (lane < rest) ws->nc[lane] = cc;
+                __syncwarp();
+                n_near = rest;
+            }
         }
         const float l0 = arm.link[j][0], l1 = arm.link[j][1], l2 = arm.link[j][2];
         const float tx = row_dot(R, 0, l0, l1, l2);
@@ -118,107 +165,11 @@ __device__ __forceinline__ void fk_lane(const capt_arm& arm, const LaneSpheres& 
         p[1] = __fadd_rn(p[1], ty);
         p[2] = __fadd_rn(p[2], tz);
     }
-}
-
-// q_k = q_a + (k / (n - 1)) (q_b - q_a), component j.
-__device__ __forceinline__ float interp_joint(const float* qa, const float* qb, int j, int k, int n) {
-    const float t = n > 1 ? __fdiv_rn((float)k, (float)(n - 1)) : 0.f;
-    const float a = __ldg(qa + j), b = __ldg(qb + j);
-    return __fadd_rn(a, __fmul_rn(t, __fsub_rn(b, a)));
-}
-
-template <int SPL>
-struct EdgeScratch {
-    static constexpr int E = 32 * SPL;
-    float cx[E], cy[E], cz[E], r2[E];
-    uint32_t blk[E], start[E], end[E];
-};
-
-// Check the SPL / 2 consecutive configurations k0, k0 + 1, .. of edge (qa_e, qb_e, n_e)
-// that are below `limit` as one warp tile (64 slots per configuration; S <= 64).
-// Returns true if any of them collides.
-template <int SPL>
-__device__ bool check_configs(const DevArgs& t, const capt_arm& arm, const LaneSpheres& ls, const float* qa_e,
-                              const float* qb_e, int n_e, int k0, int limit, const float* Ts,
-                              EdgeScratch<SPL>* ws) {
-    constexpr int CPT = SPL / 2;
-    const uint32_t lane = lane_id();
-    const uint32_t lt_mask = (1u << lane) - 1u;
-    const int J = arm.n_joints;
-    // lane (c * 16 + j) computes sin/cos of joint j of configuration k0 + c
-    float sj = 0.f, cj = 1.f;
-    {
-        const int c = (int)(lane >> 4), j = (int)(lane & 15u);
-        if (c < CPT && j < J && k0 + c < limit) sincos_cw(interp_joint(qa_e, qb_e, j, k0 + c, n_e), sj, cj);
-    }
-    bool act[SPL];
-    uint32_t nb[SPL], fb[SPL];
-    float X[SPL], Y[SPL], Z[SPL], R2[SPL];
-#pragma unroll
-    for (int c = 0; c < CPT; c++) {
-        float p0[3] = {0.f, 0.f, 0.f}, p1[3] = {0.f, 0.f, 0.f};
-        const bool live = k0 + c < limit;
-        fk_lane(arm, ls, sj, cj, c * 16, p0, p1);
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const int k = 2 * c + h;
-            const float* pc = h == 0 ? p0 : p1;
-            act[k] = false;
-            nb[k] = fb[k] = 0;
-            X[k] = pc[0];
-            Y[k] = pc[1];
-            Z[k] = pc[2];
-            R2[k] = ls.r2[h];
-            if (live && ls.f[h] >= 0) {
-                const uint32_t leaf = descend(X[k], Y[k], Z[k], t, Ts);
-                float4 a, b;
-                load_leaf(t.leaves, leaf, a, b);
-                const uint32_t cnt = __float_as_uint(b.w);
-                act[k] = cnt > 0 && box_dist2(X[k], Y[k], Z[k], a, b) <= R2[k];
-                nb[k] = act[k] ? (cnt + 3u) >> 2 : 0u;
-                fb[k] = __float_as_uint(a.w);
-            }
-        }
-    }
-    uint32_t total = 0, n_ent = 0;
-#pragma unroll
-    for (int k = 0; k < SPL; k++) {
-        const uint32_t mask = __ballot_sync(0xffffffffu, act[k]);
-        const uint32_t incl = warp_incl_scan(nb[k]);
-        if (act[k]) {
-            const uint32_t pos = n_ent + __popc(mask & lt_mask);
-            ws->cx[pos] = X[k];
-            ws->cy[pos] = Y[k];
-            ws->cz[pos] = Z[k];
-            ws->r2[pos] = R2[k];
-            ws->blk[pos] = fb[k];
-            ws->start[pos] = total + incl - nb[k];
-            ws->end[pos] = total + incl;
-        }
-        total += __shfl_sync(0xffffffffu, incl, 31);
-        n_ent += __popc(mask);
-    }
+    if (n_near == 0) return false;
     __syncwarp();
-    const float4* blocks = reinterpret_cast<const float4*>(t.blocks);
-    bool hit = false;
-    uint32_t e = 0;
-    for (uint32_t base = 0; base < total; base += 32) {
-        const uint32_t p = base + lane;
-        bool h = false;
-        if (p < total) {
-            while (ws->end[e] <= p) e++;
-            const uint32_t b = ws->blk[e] + (p - ws->start[e]);
-            const float4 px = __ldg(blocks + 3 * (size_t)b);
-            const float4 py = __ldg(blocks + 3 * (size_t)b + 1);
-            const float4 pz = __ldg(blocks + 3 * (size_t)b + 2);
-            const float x = ws->cx[e], y = ws->cy[e], z = ws->cz[e], rr = ws->r2[e];
-            h = (sq_dist(x, y, z, px.x, py.x, pz.x) <= rr) | (sq_dist(x, y, z, px.y, py.y, pz.y) <= rr) |
-                (sq_dist(x, y, z, px.z, py.z, pz.z) <= rr) | (sq_dist(x, y, z, px.w, py.w, pz.w) <= rr);
-        }
-        if (__any_sync(0xffffffffu, h)) { hit = true; break; }
-    }
-    __syncwarp();
-    return hit;
+    const bool in_queue = lane < n_near;
+    const float4 c = in_queue ? ws->nc[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+    return sphere_round<true>(t, Ts, &ws->re, nullptr, c, 0, in_queue, lane, lt_mask);
 }
 
 __device__ __forceinline__ uint8_t load_volatile_u8(const uint8_t* p) {
@@ -263,12 +214,11 @@ __global__ void k_edges_setup(const int32_t* __restrict__ ns, uint32_t E, uint32
     }
 }
 
-template <int SPL, bool STAGE>
-__global__ void __launch_bounds__(512) k_edges_persistent(DevArgs t, const __grid_constant__ capt_arm arm,
-                                                          const float* __restrict__ qa,
-                                                          const float* __restrict__ qb, const int32_t* __restrict__ ns,
-                                                          uint32_t E, uint32_t chunk, uint32_t* scratch,
-                                                          uint8_t* valid) {
+template <bool STAGE>
+__global__ void __launch_bounds__(512, 2) k_edges_persistent(DevArgs t, const __grid_constant__ ArmPlan arm,
+                                                             const float* __restrict__ qa, const float* __restrict__ qb,
+                                                             const int32_t* __restrict__ ns, uint32_t E, uint32_t chunk,
+                                                             uint32_t* scratch, uint8_t* valid) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t bar;
     const float* Ts = nullptr;
@@ -277,13 +227,11 @@ __global__ void __launch_bounds__(512) k_edges_persistent(DevArgs t, const __gri
         Ts = stage_splits(t, smem_raw, &bar);
         off = stage_offset(t);
     }
-    constexpr int CPT = SPL / 2;
     const uint32_t lane = lane_id();
-    EdgeScratch<SPL>* ws = reinterpret_cast<EdgeScratch<SPL>*>(smem_raw + off) + (threadIdx.x >> 5);
+    EdgeScratch* ws = reinterpret_cast<EdgeScratch*>(smem_raw + off) + (threadIdx.x >> 5);
     const uint32_t total_items = scratch[E];
     uint32_t* counter = scratch + E + 1;
-    const int J = arm.n_joints;
-    const LaneSpheres ls = lane_spheres(arm);
+    const int J = arm.J;
     while (true) {
         uint32_t item = 0;
         if (lane == 0) item = atomicAdd(counter, 1u);
@@ -293,7 +241,8 @@ __global__ void __launch_bounds__(512) k_edges_persistent(DevArgs t, const __gri
         uint32_t lo = 0, hi = E;
         while (hi - lo > 1) {
             const uint32_t mid = (lo + hi) >> 1;
-            if (__ldg(scratch + mid) <= item) lo = mid; else hi = mid;
+            if (__ldg(scratch + mid) <= item) lo = mid;
+            else hi = mid;
         }
         const uint32_t e = lo;
         if (load_volatile_u8(valid + e) == 0) continue;
@@ -302,8 +251,8 @@ __global__ void __launch_bounds__(512) k_edges_persistent(DevArgs t, const __gri
         const int k_end = min(n_e, k_begin + (int)chunk);
         const float* qa_e = qa + (size_t)e * J;
         const float* qb_e = qb + (size_t)e * J;
-        for (int k = k_begin; k < k_end; k += CPT) {
-            if (check_configs<SPL>(t, arm, ls, qa_e, qb_e, n_e, k, k_end, Ts, ws)) {
+        for (int k = k_begin; k < k_end; k += 32) {
+            if (edge_pass(t, arm, qa_e, qb_e, n_e, k, min(32, k_end - k), Ts, ws)) {
                 if (lane == 0) valid[e] = 0;
                 break;
             }
@@ -313,19 +262,16 @@ __global__ void __launch_bounds__(512) k_edges_persistent(DevArgs t, const __gri
 }
 
 // One edge per launch (the per-edge baseline): warps stride over its configurations.
-template <int SPL>
-__global__ void __launch_bounds__(512) k_edge_single(DevArgs t, const __grid_constant__ capt_arm arm,
-                                                     const float* __restrict__ qa_e, const float* __restrict__ qb_e,
-                                                     int n_e, uint8_t* valid_e) {
+__global__ void __launch_bounds__(512, 2) k_edge_single(DevArgs t, const __grid_constant__ ArmPlan arm,
+                                                        const float* __restrict__ qa_e, const float* __restrict__ qb_e,
+                                                        int n_e, uint8_t* valid_e) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    constexpr int CPT = SPL / 2;
-    const LaneSpheres ls = lane_spheres(arm);
-    EdgeScratch<SPL>* ws = reinterpret_cast<EdgeScratch<SPL>*>(smem_raw) + (threadIdx.x >> 5);
+    EdgeScratch* ws = reinterpret_cast<EdgeScratch*>(smem_raw) + (threadIdx.x >> 5);
     const int warps = (int)(gridDim.x * (blockDim.x >> 5));
     const int gw = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
-    for (int k = gw * CPT; k < n_e; k += warps * CPT) {
+    for (int k = gw * 32; k < n_e; k += warps * 32) {
         if (load_volatile_u8(valid_e) == 0) break;
-        if (check_configs<SPL>(t, arm, ls, qa_e, qb_e, n_e, k, n_e, nullptr, ws)) {
+        if (edge_pass(t, arm, qa_e, qb_e, n_e, k, min(32, n_e - k), nullptr, ws)) {
             if (lane_id() == 0) *valid_e = 0;
             break;
         }
@@ -336,13 +282,10 @@ size_t edge_scratch_words(size_t E) { return E + 2 + 62; }
 
 namespace {
 
-using PersistentKernel = void (*)(DevArgs, const capt_arm, const float*, const float*, const int32_t*, uint32_t,
-                                  uint32_t, uint32_t*, uint8_t*);
-
-PersistentKernel pick_persistent(int spl, bool stage) {
-    if (spl == 2) return stage ? k_edges_persistent<2, true> : k_edges_persistent<2, false>;
-    if (spl == 4) return stage ? k_edges_persistent<4, true> : k_edges_persistent<4, false>;
-    return nullptr;
+// configurations per work item: a multiple of 32 (one per lane per pass)
+uint32_t item_chunk(const capt_launch_cfg& cfg) {
+    const int c = std::max(1, std::min(1024, (int)cfg.chunk));
+    return (uint32_t)(((c + 31) / 32) * 32);
 }
 
 }  // namespace
@@ -351,23 +294,21 @@ int launch_edges_persistent(const DevArgs& t, const capt_arm& arm, const float* 
                             const int32_t* ns, uint64_t E, uint8_t* valid, uint32_t* scratch,
                             const capt_launch_cfg& cfg, cudaStream_t st, std::string& err) {
     if (E == 0) return CAPT_OK;
-    const uint32_t chunk = (uint32_t)std::max(1, std::min(1024, (int)cfg.chunk));
+    const uint32_t chunk = item_chunk(cfg);
     k_edges_setup<<<1, 1024, 0, st>>>(ns, (uint32_t)E, chunk, scratch, valid);
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) { err = std::string("edge setup launch: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
     const bool stage = cfg.staging == CAPT_STAGE_SMEM && t.stage_floats > 0;
-    PersistentKernel fn = pick_persistent(cfg.spheres_per_lane, stage);
-    if (!fn) { err = "edges need spheres_per_lane 2 or 4"; return CAPT_E_ARG; }
+    auto fn = stage ? k_edges_persistent<true> : k_edges_persistent<false>;
     const int warps = std::max(1, std::min(16, (int)cfg.warps_per_block));
-    const size_t ws = cfg.spheres_per_lane == 2 ? sizeof(EdgeScratch<2>) : sizeof(EdgeScratch<4>);
-    const uint32_t sb = stage ? stage_offset(t) : 0u;
-    const size_t smem = sb + ws * (size_t)warps;
+    const size_t smem = (stage ? stage_offset(t) : 0u) + sizeof(EdgeScratch) * (size_t)warps;
     ce = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (ce != cudaSuccess) { err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)fn, warps * 32, smem);
     occ = std::max(1, occ);
-    fn<<<(unsigned)(sm_count() * occ), warps * 32, smem, st>>>(t, arm, qa, qb, ns, (uint32_t)E, chunk, scratch, valid);
+    const ArmPlan plan = make_plan(arm);
+    fn<<<(unsigned)(sm_count() * occ), warps * 32, smem, st>>>(t, plan, qa, qb, ns, (uint32_t)E, chunk, scratch, valid);
     ce = cudaGetLastError();
     if (ce != cudaSuccess) { err = std::string("edge launch: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
     return CAPT_OK;
@@ -378,20 +319,18 @@ int launch_edges_per_edge(const DevArgs& t, const capt_arm& arm, const float* qa
                           cudaStream_t st, std::string& err) {
     cudaError_t ce = cudaMemsetAsync(valid, 1, E, st);
     if (ce != cudaSuccess) { err = std::string("memset: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
-    const int spl = cfg.spheres_per_lane == 4 ? 4 : 2;
-    const int cpt = spl / 2;
     const int warps = std::max(1, std::min(16, (int)cfg.warps_per_block));
-    const size_t smem = (spl == 2 ? sizeof(EdgeScratch<2>) : sizeof(EdgeScratch<4>)) * (size_t)warps;
-    auto fn = spl == 2 ? k_edge_single<2> : k_edge_single<4>;
-    ce = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = sizeof(EdgeScratch) * (size_t)warps;
+    ce = cudaFuncSetAttribute((const void*)k_edge_single, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (ce != cudaSuccess) { err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
+    const ArmPlan plan = make_plan(arm);
     const int J = arm.n_joints;
     for (uint64_t e = 0; e < E; e++) {
         const int n = h_ns[e];
         if (n <= 0) continue;
-        const int warps_needed = (n + cpt - 1) / cpt;
+        const int warps_needed = (n + 31) / 32;
         const int blocks = (warps_needed + warps - 1) / warps;
-        fn<<<blocks, warps * 32, smem, st>>>(t, arm, qa + e * J, qb + e * J, n, valid + e);
+        k_edge_single<<<blocks, warps * 32, smem, st>>>(t, plan, qa + e * J, qb + e * J, n, valid + e);
     }
     ce = cudaGetLastError();
     if (ce != cudaSuccess) { err = std::string("per-edge launch: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }

@@ -1,0 +1,148 @@
+// The affordance scan shared by the query, edge and clearance kernels.
+//
+// A "round" takes up to 32 queued spheres (centre and r^2, one per lane): each lane
+// descends the tree, loads its leaf record and applies the leaf box test of Alg. 3;
+// the spheres that pass become entries whose affordance sets are concatenated, and the
+// warp walks the concatenated 4-point blocks 32 at a time, every lane testing one
+// block (three 16-byte loads, four FP32 distance tests in packed FP32x2 arithmetic).
+#pragma once
+
+#include "device_common.cuh"
+
+namespace capt {
+
+// Packed FP32x2 arithmetic: two IEEE-rounded FP32 operations per instruction; the
+// element results are bitwise those of the scalar __fsub_rn / __fmul_rn / __fadd_rn.
+__device__ __forceinline__ uint64_t f2_dup(float a) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ float2 f2_split(uint64_t v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+
+// Squared distances from a centre (each coordinate duplicated) to the four points of
+// block b: ((p_x - c_x)^2 + (p_y - c_y)^2) + (p_z - c_z)^2 per point, each operation
+// rounded; p - c is the exact negation of c - p, so the squares are those of the
+// defining expression.  Returns the pairs (points 0,1) and (points 2,3).
+__device__ __forceinline__ void block_d2(const float4* __restrict__ blocks, int64_t b, uint64_t cxx, uint64_t cyy,
+                                         uint64_t czz, uint64_t& s01, uint64_t& s23) {
+    const ulonglong2 px = __ldg(reinterpret_cast<const ulonglong2*>(blocks + 3 * b));
+    const ulonglong2 py = __ldg(reinterpret_cast<const ulonglong2*>(blocks + 3 * b + 1));
+    const ulonglong2 pz = __ldg(reinterpret_cast<const ulonglong2*>(blocks + 3 * b + 2));
+    const uint64_t x01 = f2_sub(px.x, cxx), x23 = f2_sub(px.y, cxx);
+    const uint64_t y01 = f2_sub(py.x, cyy), y23 = f2_sub(py.y, cyy);
+    const uint64_t z01 = f2_sub(pz.x, czz), z23 = f2_sub(pz.y, czz);
+    s01 = f2_add(f2_add(f2_mul(x01, x01), f2_mul(y01, y01)), f2_mul(z01, z01));
+    s23 = f2_add(f2_add(f2_mul(x23, x23), f2_mul(y23, y23)), f2_mul(z23, z23));
+}
+
+// Does any of the four points of block b lie within r2 of the centre?
+__device__ __forceinline__ bool block_hit2(const float4* __restrict__ blocks, int64_t b, uint64_t cxx, uint64_t cyy,
+                                           uint64_t czz, float r2) {
+    uint64_t s01, s23;
+    block_d2(blocks, b, cxx, cyy, czz, s01, s23);
+    const float2 a = f2_split(s01), c = f2_split(s23);
+    return (a.x <= r2) | (a.y <= r2) | (c.x <= r2) | (c.y <= r2);
+}
+
+// Per-warp storage of one round's entries.
+struct RoundEntries {
+    float4 c[32];      // centre and r^2
+    int32_t boff[32];  // first block of the entry minus its start in the concatenated list
+    uint32_t end[32];  // exclusive end of the entry in the concatenated list
+    uint32_t grp[32];  // group of the entry (configuration of the tile)
+};
+
+// One round over the spheres (c, g) held by lanes < n.  Groups already marked in
+// ghit are skipped; a hit marks its group.  With SINGLE there is one group and the
+// first hit ends the round (return value: whether a hit was found).
+template <bool SINGLE>
+__device__ __forceinline__ bool sphere_round(const DevArgs& t, const float* Ts, RoundEntries* re, uint32_t* ghit,
+                                             float4 c, uint32_t g, bool live, uint32_t lane, uint32_t lt_mask) {
+    const float4* blocks = reinterpret_cast<const float4*>(t.blocks);
+    bool act = false;
+    uint32_t nb = 0, fb = 0;
+    if (live && (SINGLE || !ghit[g])) {
+        const uint32_t leaf = descend(c.x, c.y, c.z, t, Ts);
+        float4 a, b;
+        load_leaf(t.leaves, leaf, a, b);
+        const uint32_t cnt = __float_as_uint(b.w);
+        act = cnt > 0 && box_dist2(c.x, c.y, c.z, a, b) <= c.w;
+        nb = act ? (cnt + 3u) >> 2 : 0u;
+        fb = __float_as_uint(a.w);
+    }
+    const uint32_t mask = __ballot_sync(0xffffffffu, act);
+    if (mask == 0) return false;
+    const uint32_t incl = warp_incl_scan(nb);
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    const uint32_t n_ent = __popc(mask);
+    __syncwarp();
+    if (act) {
+        const uint32_t pos = __popc(mask & lt_mask);
+        re->c[pos] = c;
+        re->boff[pos] = (int32_t)fb - (int32_t)(incl - nb);
+        re->end[pos] = incl;
+        re->grp[pos] = g;
+    }
+    __syncwarp();
+    uint32_t e = 0, e_loaded = 0xffffffffu;
+    uint64_t cxx = 0, cyy = 0, czz = 0;
+    float r2 = 0.f;
+    int32_t boff = 0;
+    uint32_t ge = 0;
+    bool found = false;
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t p = base + lane;
+        bool h = false;
+        if (p < total) {
+            while (re->end[e] <= p) e++;
+            if (e != e_loaded) {
+                const float4 ce = re->c[e];
+                cxx = f2_dup(ce.x);
+                cyy = f2_dup(ce.y);
+                czz = f2_dup(ce.z);
+                r2 = ce.w;
+                boff = re->boff[e];
+                ge = re->grp[e];
+                e_loaded = e;
+            }
+            if (SINGLE || !ghit[ge]) {
+                h = block_hit2(blocks, (int64_t)boff + p, cxx, cyy, czz, r2);
+                if (!SINGLE && h) ghit[ge] = 1;
+            }
+        }
+        if (SINGLE) {
+            if (__any_sync(0xffffffffu, h)) { found = true; break; }
+            continue;
+        }
+        __syncwarp();
+        if (__any_sync(0xffffffffu, h)) {
+            // leave once every entry that still has blocks ahead is resolved
+            const bool open = lane < n_ent && re->end[lane] > base + 32 && !ghit[re->grp[lane]];
+            if (!__any_sync(0xffffffffu, open)) break;
+        }
+    }
+    __syncwarp();
+    return found;
+}
+
+}  // namespace capt

@@ -259,7 +259,7 @@ def test_edge_plan_autotuned(tabletop, edges, capt_lib, torch_):
     torch_.cuda.synchronize()
     assert np.array_equal(valid.cpu().numpy(), edges["ref"])
     cfg, ms = capt_lib.capt_edge_plan_info(plan)
-    assert ms > 0 and cfg["spheres_per_lane"] in (2, 4)
+    assert ms > 0 and cfg["chunk"] in (32, 64, 128)
 
 
 def test_edges_degenerate_counts(tabletop, orc, capt_lib, torch_):
