@@ -124,8 +124,9 @@ const char* capt_last_error(void);
  * Device layout (all 256-byte aligned):
  *   T      float[N-1 rounded up to 4]  split values (Eytzinger)
  *   leaves 32-byte records {lo.xyz, first block, hi.xyz, count} per leaf
- *   blocks float4[3 * total_blocks]: each set starts at a block of 4 points stored as
- *          {x0..x3}{y0..y3}{z0..z3}; unused slots hold +inf
+ *   blocks float4[3 * total_blocks]: each set starts at a block of 4 points; the
+ *          blocks are stored as three planes, all x quads {x0..x3}, then all y quads,
+ *          then all z quads; unused slots hold +inf
  *   ids    uint32[4 * total_blocks] point index per slot (0xffffffff in unused slots)
  *   cloud  float[n][3] the input points (for the clearance gradient)
  * Calling it again re-uploads.  Errors: CAPT_E_ARG, CAPT_E_CUDA, CAPT_E_NOMEM. */

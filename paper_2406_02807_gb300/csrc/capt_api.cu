@@ -105,6 +105,7 @@ struct capt_tree {
         a.stage_floats = stage_floats;
         a.leaves = static_cast<const capt::LeafRec*>(d_leaves);
         a.blocks = static_cast<const float*>(d_blocks);
+        a.plane = total_blocks > 0 ? total_blocks : 1;
         a.ids = static_cast<const uint32_t*>(d_ids);
         a.cloud = static_cast<const float*>(d_cloud);
         a.status = d_status;

@@ -37,7 +37,7 @@ static_assert(sizeof(LeafRec) == 32, "leaf record is one 32-byte sector");
 // Flattened device layout, built on the host then copied.
 struct Layout {
     std::vector<LeafRec> leaves;      // N
-    std::vector<float> blocks;        // 12 floats per block
+    std::vector<float> blocks;        // three planes (x, y, z) of 4 floats per block
     std::vector<uint32_t> ids;        // 4 per block
     uint64_t total_blocks = 0;
 };
@@ -60,7 +60,8 @@ struct DevArgs {
     int K = 0, R = 0, Ks = 0, tail_staged = 0;
     uint32_t stage_floats = 0;
     const LeafRec* leaves = nullptr; // N records
-    const float* blocks = nullptr;   // 12 floats per 4-point block (float4 x 3)
+    const float* blocks = nullptr;   // 4-point blocks in three planes of float4 (x, y, z quads)
+    uint64_t plane = 1;              // blocks per plane (float4 stride between the planes)
     const uint32_t* ids = nullptr;   // 4 per block
     const float* cloud = nullptr;    // [n][3]
     int* status = nullptr;           // latched device status bits

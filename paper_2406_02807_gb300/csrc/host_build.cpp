@@ -268,15 +268,18 @@ void flatten(const HostTree& t, Layout& out) {
         blocks += (cnt + 3) / 4;
     }
     out.total_blocks = blocks;
-    out.blocks.assign(12 * std::max<uint64_t>(blocks, 1), INFINITY);
-    out.ids.assign(4 * std::max<uint64_t>(blocks, 1), 0xffffffffu);
+    // three planes of 4-point quads: all x quads, then all y quads, then all z quads, so
+    // that consecutive blocks read by consecutive lanes are contiguous in each plane
+    const uint64_t plane = std::max<uint64_t>(blocks, 1);
+    out.blocks.assign(12 * plane, INFINITY);
+    out.ids.assign(4 * plane, 0xffffffffu);
     for (size_t l = 0; l < t.N; l++) {
         uint64_t b0 = out.leaves[l].block;
         uint64_t beg = t.set_begin[l], cnt = t.set_begin[l + 1] - beg;
         for (uint64_t j = 0; j < cnt; j++) {
             uint32_t p = t.set_idx[beg + j];
             uint64_t blk = b0 + j / 4, lane = j % 4;
-            for (int e = 0; e < 3; e++) out.blocks[12 * blk + 4 * e + lane] = t.pts[3 * (size_t)p + e];
+            for (int e = 0; e < 3; e++) out.blocks[4 * (e * plane + blk) + lane] = t.pts[3 * (size_t)p + e];
             out.ids[4 * blk + lane] = p;
         }
     }

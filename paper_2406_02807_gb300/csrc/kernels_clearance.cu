@@ -76,7 +76,7 @@ __device__ __forceinline__ void clearance_round(const DevArgs& t, const float* T
         unsigned long long best = ~0ull;
         auto fold = [&](uint32_t r) {
             uint64_t s01, s23;
-            block_d2(blocks, (int64_t)b0 + r, cxx, cyy, czz, s01, s23);
+            block_d2(blocks, t.plane, (int64_t)b0 + r, cxx, cyy, czz, s01, s23);
             const float2 d01 = f2_split(s01), d23 = f2_split(s23);
             float bd = d01.x;
             uint32_t bq = 0;

@@ -49,7 +49,7 @@ __device__ __forceinline__ void bulk_copy(float* dst, const float* src, uint32_t
 }
 
 template <int SPL, bool STAGE>
-__global__ void __launch_bounds__(512, SPL <= 2 ? 3 : 2)
+__global__ void __launch_bounds__(512, 2)
     k_spheres(DevArgs t, const float* __restrict__ centers, const float* __restrict__ radii, uint64_t m,
               uint8_t* __restrict__ out) {
     using WS = SphereScratch<SPL>;
@@ -350,10 +350,10 @@ __global__ void k_count_configs(DevArgs t, const float* __restrict__ centers, co
             const uint32_t b0 = __float_as_uint(a.w);
             bool hit = false;
             for (uint32_t j = 0; j < cnt && !hit; j++) {
-                const float* blk = t.blocks + 12 * (size_t)(b0 + j / 4);
-                const uint32_t q = j & 3u;
+                const float* bx = t.blocks + 4 * (size_t)(b0 + j / 4) + (j & 3u);
+                const size_t pl = 4 * (size_t)t.plane;
                 npts++;
-                hit = sq_dist(x[0], x[1], x[2], blk[q], blk[4 + q], blk[8 + q]) <= r2;
+                hit = sq_dist(x[0], x[1], x[2], bx[0], bx[pl], bx[2 * pl]) <= r2;
             }
             if (hit) break;
         }

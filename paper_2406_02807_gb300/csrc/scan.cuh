@@ -2,12 +2,24 @@
 //
 // A "round" takes up to 32 queued spheres (centre and r^2, one per lane): each lane
 // descends the tree, loads its leaf record and applies the leaf box test of Alg. 3;
-// the spheres that pass become entries whose affordance sets are concatenated, and the
-// warp walks the concatenated 4-point blocks 32 at a time, every lane testing one
-// block (three 16-byte loads, four FP32 distance tests in packed FP32x2 arithmetic).
+// the spheres that pass become entries.  When their sets are large (at least 32 blocks
+// each on average) the warp scans one set at a time, all lanes on its 4-point blocks;
+// otherwise it walks the concatenation of all the sets 32 blocks at a time, so that
+// lanes stay busy on small sets.  Every lane test is three 16-byte loads and four FP32
+// distance tests in packed FP32x2 arithmetic.
+// The blocks are stored as three planes of float4 (x quads, y quads, z quads), so the
+// loads of 32 consecutive blocks by 32 lanes are 512 contiguous bytes per plane.
 #pragma once
 
 #include "device_common.cuh"
+
+// blocks per lane per step of the two scan forms (concatenated / per entry)
+#ifndef CAPT_SCAN_UNROLL
+#define CAPT_SCAN_UNROLL 1
+#endif
+#ifndef CAPT_SCAN_PE_UNROLL
+#define CAPT_SCAN_PE_UNROLL 2
+#endif
 
 namespace capt {
 
@@ -43,11 +55,12 @@ __device__ __forceinline__ float2 f2_split(uint64_t v) {
 // block b: ((p_x - c_x)^2 + (p_y - c_y)^2) + (p_z - c_z)^2 per point, each operation
 // rounded; p - c is the exact negation of c - p, so the squares are those of the
 // defining expression.  Returns the pairs (points 0,1) and (points 2,3).
-__device__ __forceinline__ void block_d2(const float4* __restrict__ blocks, int64_t b, uint64_t cxx, uint64_t cyy,
-                                         uint64_t czz, uint64_t& s01, uint64_t& s23) {
-    const ulonglong2 px = __ldg(reinterpret_cast<const ulonglong2*>(blocks + 3 * b));
-    const ulonglong2 py = __ldg(reinterpret_cast<const ulonglong2*>(blocks + 3 * b + 1));
-    const ulonglong2 pz = __ldg(reinterpret_cast<const ulonglong2*>(blocks + 3 * b + 2));
+// The block's quads live in three planes `plane` float4s apart.
+__device__ __forceinline__ void block_d2(const float4* __restrict__ blocks, uint64_t plane, int64_t b, uint64_t cxx,
+                                         uint64_t cyy, uint64_t czz, uint64_t& s01, uint64_t& s23) {
+    const ulonglong2 px = __ldg(reinterpret_cast<const ulonglong2*>(blocks + b));
+    const ulonglong2 py = __ldg(reinterpret_cast<const ulonglong2*>(blocks + plane + b));
+    const ulonglong2 pz = __ldg(reinterpret_cast<const ulonglong2*>(blocks + 2 * plane + b));
     const uint64_t x01 = f2_sub(px.x, cxx), x23 = f2_sub(px.y, cxx);
     const uint64_t y01 = f2_sub(py.x, cyy), y23 = f2_sub(py.y, cyy);
     const uint64_t z01 = f2_sub(pz.x, czz), z23 = f2_sub(pz.y, czz);
@@ -56,10 +69,10 @@ __device__ __forceinline__ void block_d2(const float4* __restrict__ blocks, int6
 }
 
 // Does any of the four points of block b lie within r2 of the centre?
-__device__ __forceinline__ bool block_hit2(const float4* __restrict__ blocks, int64_t b, uint64_t cxx, uint64_t cyy,
-                                           uint64_t czz, float r2) {
+__device__ __forceinline__ bool block_hit2(const float4* __restrict__ blocks, uint64_t plane, int64_t b, uint64_t cxx,
+                                           uint64_t cyy, uint64_t czz, float r2) {
     uint64_t s01, s23;
-    block_d2(blocks, b, cxx, cyy, czz, s01, s23);
+    block_d2(blocks, plane, b, cxx, cyy, czz, s01, s23);
     const float2 a = f2_split(s01), c = f2_split(s23);
     return (a.x <= r2) | (a.y <= r2) | (c.x <= r2) | (c.y <= r2);
 }
@@ -104,31 +117,95 @@ __device__ __forceinline__ bool sphere_round(const DevArgs& t, const float* Ts, 
         re->grp[pos] = g;
     }
     __syncwarp();
-    uint32_t e = 0, e_loaded = 0xffffffffu;
-    uint64_t cxx = 0, cyy = 0, czz = 0;
-    float r2 = 0.f;
-    int32_t boff = 0;
-    uint32_t ge = 0;
     bool found = false;
-    for (uint32_t base = 0; base < total; base += 32) {
-        const uint32_t p = base + lane;
+    if (total >= 32u * n_ent) {
+    // Large sets: one entry at a time, the whole warp on its blocks (lane l takes blocks
+    // fb + l + 32 k, V per step), so block addresses need no per-lane lookup; a hit
+    // resolves the entry's group.
+    constexpr int V = CAPT_SCAN_PE_UNROLL;
+    for (uint32_t e = 0; e < n_ent; e++) {
+        const uint32_t ge = re->grp[e];
+        if (!SINGLE && ghit[ge]) continue;
+        const float4 ce = re->c[e];
+        const uint32_t b_end = re->end[e];
+        const uint32_t b_beg = e ? re->end[e - 1] : 0u;
+        const int64_t o = (int64_t)re->boff[e];
+        const uint64_t cxx = f2_dup(ce.x), cyy = f2_dup(ce.y), czz = f2_dup(ce.z);
+        bool hit = false;
+        for (uint32_t p = b_beg + lane; __any_sync(0xffffffffu, p < b_end); p += 32 * V) {
+            uint64_t s01[V], s23[V];
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                s01[v] = s23[v] = 0;
+                if (p + 32 * v < b_end) block_d2(blocks, t.plane, o + p + 32 * v, cxx, cyy, czz, s01[v], s23[v]);
+            }
+            bool h = false;
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                if (p + 32 * v < b_end) {
+                    const float2 x = f2_split(s01[v]), y = f2_split(s23[v]);
+                    h |= (x.x <= ce.w) | (x.y <= ce.w) | (y.x <= ce.w) | (y.y <= ce.w);
+                }
+            }
+            if (__any_sync(0xffffffffu, h)) { hit = true; break; }
+        }
+        if (hit) {
+            if (SINGLE) { found = true; break; }
+            if (lane == 0) ghit[ge] = 1;
+            __syncwarp();
+        }
+    }
+    } else {
+    // Small sets: the concatenated blocks of all entries, U per lane per step (32 U per
+    // warp step), lane l taking blocks base + l + 32 u; each lane keeps the fields of the
+    // entries it is in, reloading them only when it moves on.
+    constexpr int U = CAPT_SCAN_UNROLL;
+    uint32_t ei[U], ce[U];
+    float4 cc[U];
+    int32_t oo[U];
+    uint32_t gg[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        ei[u] = 0;
+        ce[u] = 0xffffffffu;
+        cc[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        oo[u] = 0;
+        gg[u] = 0;
+    }
+    for (uint32_t base = 0; base < total; base += 32 * U) {
+        bool live[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const uint32_t p = base + lane + 32u * u;
+            live[u] = p < total;
+            if (live[u]) {
+                if (u > 0 && ei[u] < ei[u - 1]) ei[u] = ei[u - 1];
+                while (re->end[ei[u]] <= p) ei[u]++;
+                if (ei[u] != ce[u]) {
+                    cc[u] = re->c[ei[u]];
+                    oo[u] = re->boff[ei[u]];
+                    gg[u] = re->grp[ei[u]];
+                    ce[u] = ei[u];
+                }
+                live[u] = SINGLE || !ghit[gg[u]];
+            }
+        }
+        uint64_t s01[U], s23[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            s01[u] = s23[u] = 0;
+            if (live[u])
+                block_d2(blocks, t.plane, (int64_t)oo[u] + base + lane + 32u * u, f2_dup(cc[u].x), f2_dup(cc[u].y),
+                         f2_dup(cc[u].z), s01[u], s23[u]);
+        }
         bool h = false;
-        if (p < total) {
-            while (re->end[e] <= p) e++;
-            if (e != e_loaded) {
-                const float4 ce = re->c[e];
-                cxx = f2_dup(ce.x);
-                cyy = f2_dup(ce.y);
-                czz = f2_dup(ce.z);
-                r2 = ce.w;
-                boff = re->boff[e];
-                ge = re->grp[e];
-                e_loaded = e;
-            }
-            if (SINGLE || !ghit[ge]) {
-                h = block_hit2(blocks, (int64_t)boff + p, cxx, cyy, czz, r2);
-                if (!SINGLE && h) ghit[ge] = 1;
-            }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            if (!live[u]) continue;
+            const float2 x = f2_split(s01[u]), y = f2_split(s23[u]);
+            const bool hu = (x.x <= cc[u].w) | (x.y <= cc[u].w) | (y.x <= cc[u].w) | (y.y <= cc[u].w);
+            if (!SINGLE && hu) ghit[gg[u]] = 1;
+            h |= hu;
         }
         if (SINGLE) {
             if (__any_sync(0xffffffffu, h)) { found = true; break; }
@@ -137,9 +214,10 @@ __device__ __forceinline__ bool sphere_round(const DevArgs& t, const float* Ts, 
         __syncwarp();
         if (__any_sync(0xffffffffu, h)) {
             // leave once every entry that still has blocks ahead is resolved
-            const bool open = lane < n_ent && re->end[lane] > base + 32 && !ghit[re->grp[lane]];
+            const bool open = lane < n_ent && re->end[lane] > base + 32 * U && !ghit[re->grp[lane]];
             if (!__any_sync(0xffffffffu, open)) break;
         }
+    }
     }
     __syncwarp();
     return found;
