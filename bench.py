@@ -38,7 +38,7 @@ R_MIN, R_MAX, R_FILTER = 0.02, 0.08, 0.01
 SM_MAX_MHZ = 2070.0
 # DRAM bytes (read + write) per launch of the configuration-query kernel from an ncu
 # capture, keyed by the hash of the kernel source it was taken on (null when stale).
-TRAFFIC = {}
+TRAFFIC = {"258953f80130fda8": 777239552 + 4401920}   # profiles/k_configs_tabletop_1M.md
 
 
 def parse():
@@ -303,7 +303,7 @@ def main():
         sms = props.multi_processor_count
         peak_tops = sms * 128 * SM_MAX_MHZ * 1e6 / 1e12
         achieved = ops_per_launch / (ms / 1e3) / 1e12
-        h = src_hash("kernels_query.cu", "device_common.cuh")
+        h = src_hash("kernels_query.cu", "scan.cuh", "device_common.cuh", "capt_internal.h")
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
