@@ -207,6 +207,7 @@ def main():
         return
     import torch
     import paper_2406_02807_gb300 as capt
+    from paper_2406_02807_gb300.shard import max_over_ranks, weak_slice
     capt.build()
     torch.cuda.set_device(local)
     pg = None
@@ -220,7 +221,8 @@ def main():
     raw, pts, arm, tree, host = tabletop_tree(capt)
     capt.capt_upload(tree, local)
     C = args.configs
-    q = W.random_configs(C, 1001, first=rank * C)
+    first, _ = weak_slice(C, rank)          # this rank's own configurations (weak scaling)
+    q = W.random_configs(C, 1001, first=first)
     cen_host = torch.from_numpy(W.fk_centers(arm, q)).pin_memory()
     del q
     cen = cen_host.to(dev, non_blocking=False)
@@ -251,9 +253,7 @@ def main():
     clk = clocks.stop()
     if pg:
         pg.barrier()
-        tt = torch.tensor([ms], device=dev)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        ms = float(tt.item())
+        ms = max_over_ranks(ms, pg, dev)
     value = world * C * SPHERES / (ms / 1e3)
     collide = float(flags.float().mean().item())
 
@@ -269,9 +269,7 @@ def main():
         capt.capt_query_configs_host(tree, cen_host, r_host, h_flags)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     if pg:
-        tt = torch.tensor([e2e_s], device=dev)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+        e2e_s = max_over_ranks(e2e_s, pg, dev)
     e2e_ok = bool(torch.equal(h_flags, flags.cpu()))
 
     # batched edge validation: persistent graph launch vs one launch per edge
