@@ -146,12 +146,15 @@ int capt_query_spheres(const capt_tree* t, const float* d_centers, const float* 
 int capt_query_configs(const capt_tree* t, const float* d_centers, const float* d_radii, size_t C, int S,
                        uint8_t* d_flags, void* stream);
 
-/* capt_query_configs from HOST memory: h_centers float[C][S][3] and h_radii float[S]
- * are copied to the device in chunks that overlap with the queries of the previous
- * chunk; the flags come back to h_flags uint8[C].  The call returns when h_flags is
- * complete (it synchronises).  Page-locked host buffers give the copy/compute overlap;
- * pageable ones work but copy synchronously.  The first call allocates two chunk
- * buffers on the device, kept by the tree.  Errors as capt_query_configs, CAPT_E_NOMEM. */
+/* capt_query_configs from HOST memory: h_centers float[C][S][3], h_radii float[S],
+ * flags to h_flags uint8[C]; the call returns when h_flags is complete (it
+ * synchronises `stream`).  When h_centers is page-locked (cudaHostAlloc, torch
+ * pin_memory) the kernel reads the centres straight from host memory, each once (on
+ * Grace systems over NVLink-C2C), with no staging copy; flags are written the same way
+ * when h_flags is page-locked.  Pageable centres are copied in 64 Ki-configuration
+ * chunks that overlap with the queries of the previous chunk.  The first call
+ * allocates small device buffers (chunk buffers for pageable input), kept by the tree.
+ * Errors as capt_query_configs, CAPT_E_NOMEM. */
 int capt_query_configs_host(capt_tree* t, const float* h_centers, const float* h_radii, size_t C, int S,
                             uint8_t* h_flags, void* stream);
 

@@ -82,6 +82,8 @@ struct capt_tree {
     size_t pipe_cap = 0;   // floats per centre buffer
     cudaStream_t pipe_stream = nullptr;
     cudaEvent_t pipe_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    uint8_t* d_zc_flags = nullptr;  // flags of the zero-copy path when h_flags is pageable
+    size_t zc_cap = 0;
     // edge validation scratch (persistent mode without a plan)
     uint32_t* d_edge_scratch = nullptr;
     size_t edge_scratch_cap = 0;
@@ -124,7 +126,7 @@ struct capt_tree {
         if (device < 0) return;
         DeviceGuard g(device);
         for (void* p : {d_T, d_leaves, d_blocks, d_ids, d_cloud, (void*)d_status, (void*)d_pipe_c[0], (void*)d_pipe_c[1],
-                        (void*)d_pipe_f[0], (void*)d_pipe_f[1], (void*)d_edge_scratch})
+                        (void*)d_pipe_f[0], (void*)d_pipe_f[1], (void*)d_edge_scratch, (void*)d_zc_flags})
             if (p) cudaFree(p);
         for (auto& e : pipe_ev)
             if (e) cudaEventDestroy(e);
@@ -134,6 +136,8 @@ struct capt_tree {
         d_pipe_c[0] = d_pipe_c[1] = nullptr;
         d_pipe_f[0] = d_pipe_f[1] = nullptr;
         d_edge_scratch = nullptr;
+        d_zc_flags = nullptr;
+        zc_cap = 0;
         for (auto& e : pipe_ev) e = nullptr;
         pipe_stream = nullptr;
         pipe_cap = 0;
@@ -145,6 +149,18 @@ struct capt_tree {
 
 namespace {
 
+// Device address of a page-locked host allocation that the current device can reach,
+// or nullptr for pageable (or device) memory.
+const void* mapped_device_pointer(const void* h) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    return a.devicePointer;
+}
+
 // The tree must be uploaded and the caller's current device must be the tree's.
 int check_ready(const capt_tree* t) {
     if (!t) return fail(CAPT_E_ARG, "tree is NULL");
@@ -153,6 +169,46 @@ int check_ready(const capt_tree* t) {
     if (cudaGetDevice(&cur) != cudaSuccess || cur != t->device)
         return fail(CAPT_E_STATE, "current CUDA device differs from the tree's device");
     return CAPT_OK;
+}
+
+// Two chunk buffers of `chunk` configurations of S spheres (+ slack for the radii),
+// their flag buffers, a copy stream and events, kept by the tree.
+bool ensure_pipe(capt_tree* t, size_t chunk, int S) {
+    const size_t cfloats = chunk * (size_t)S * 3;
+    if (t->pipe_cap >= cfloats + 64) return true;
+    for (int i = 0; i < 2; i++) {
+        if (t->d_pipe_c[i]) cudaFree(t->d_pipe_c[i]);
+        if (t->d_pipe_f[i]) cudaFree(t->d_pipe_f[i]);
+        t->d_pipe_c[i] = nullptr;
+        t->d_pipe_f[i] = nullptr;
+    }
+    t->pipe_cap = 0;
+    for (int i = 0; i < 2; i++) {
+        if (cudaMalloc((void**)&t->d_pipe_c[i], (cfloats + 64) * sizeof(float)) != cudaSuccess ||
+            cudaMalloc((void**)&t->d_pipe_f[i], chunk + 256) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+    }
+    t->pipe_cap = cfloats + 64;
+    if (!t->pipe_stream && cudaStreamCreateWithFlags(&t->pipe_stream, cudaStreamNonBlocking) != cudaSuccess) return false;
+    for (auto& e : t->pipe_ev)
+        if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return false;
+    return true;
+}
+
+// A device flag buffer of at least C bytes (zero-copy path with pageable flags).
+bool ensure_flags(capt_tree* t, size_t C) {
+    if (t->zc_cap >= C) return true;
+    if (t->d_zc_flags) cudaFree(t->d_zc_flags);
+    t->d_zc_flags = nullptr;
+    t->zc_cap = 0;
+    if (cudaMalloc((void**)&t->d_zc_flags, C) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    t->zc_cap = C;
+    return true;
 }
 
 }  // namespace
@@ -345,38 +401,44 @@ int capt_query_configs_host(capt_tree* t, const float* h_centers, const float* h
     if (!h_centers || !h_radii || !h_flags) return fail(CAPT_E_ARG, "NULL host pointer");
     std::lock_guard<std::mutex> lk(t->mu);
     cudaStream_t user = static_cast<cudaStream_t>(stream);
+    std::string err;
+    // Page-locked host memory is mapped into the device's address space: the kernel then
+    // reads every centre once, straight from host memory (over NVLink-C2C on Grace
+    // systems), with no staging copy.  Flags go to page-locked host memory the same way,
+    // else through a small device buffer.
+    const void* dc = mapped_device_pointer(h_centers);
+    if (dc) {
+        if (!ensure_pipe(t, 1, S)) return fail(CAPT_E_NOMEM, "cudaMalloc of the host-pipeline buffers failed");
+        float* d_r = t->d_pipe_c[0];
+        CUDA_TRY(cudaMemcpyAsync(d_r, h_radii, (size_t)S * sizeof(float), cudaMemcpyHostToDevice, user), "radii H2D");
+        void* df = const_cast<void*>(mapped_device_pointer(h_flags));
+        if (df) {
+            rc = capt::launch_query(t->args(), capt::kModeConfigs, static_cast<const float*>(dc), d_r, C, S,
+                                    static_cast<uint8_t*>(df), t->cfg[CAPT_KERNEL_CONFIGS], user, err);
+            if (rc) return fail(rc, err);
+        } else {
+            if (!ensure_flags(t, C)) return fail(CAPT_E_NOMEM, "cudaMalloc of the flag buffer failed");
+            rc = capt::launch_query(t->args(), capt::kModeConfigs, static_cast<const float*>(dc), d_r, C, S,
+                                    t->d_zc_flags, t->cfg[CAPT_KERNEL_CONFIGS], user, err);
+            if (rc) return fail(rc, err);
+            CUDA_TRY(cudaMemcpyAsync(h_flags, t->d_zc_flags, C, cudaMemcpyDeviceToHost, user), "flags D2H");
+        }
+        CUDA_TRY(cudaStreamSynchronize(user), "synchronize");
+        return CAPT_OK;
+    }
     // chunk: 64 Ki configurations (about 47 MB of centres for S = 60)
     const size_t chunk = std::min<size_t>(C, 65536);
     const size_t cfloats = chunk * (size_t)S * 3;
-    if (t->pipe_cap < cfloats + 64) {
-        for (int i = 0; i < 2; i++) {
-            if (t->d_pipe_c[i]) cudaFree(t->d_pipe_c[i]);
-            if (t->d_pipe_f[i]) cudaFree(t->d_pipe_f[i]);
-            t->d_pipe_c[i] = nullptr;
-            t->d_pipe_f[i] = nullptr;
-        }
-        t->pipe_cap = 0;
-        for (int i = 0; i < 2; i++) {
-            if (cudaMalloc((void**)&t->d_pipe_c[i], (cfloats + 64) * sizeof(float)) != cudaSuccess ||
-                cudaMalloc((void**)&t->d_pipe_f[i], chunk + 256) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(CAPT_E_NOMEM, "cudaMalloc of the host-pipeline buffers failed");
-            }
-        }
-        t->pipe_cap = cfloats + 64;
-        if (!t->pipe_stream) CUDA_TRY(cudaStreamCreateWithFlags(&t->pipe_stream, cudaStreamNonBlocking), "stream");
-        for (auto& e : t->pipe_ev)
-            if (!e) CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
-    }
+    if (!ensure_pipe(t, chunk, S)) return fail(CAPT_E_NOMEM, "cudaMalloc of the host-pipeline buffers failed");
     // radii live in the tail of buffer 0's slack (S <= 64 floats)
     float* d_r = t->d_pipe_c[0] + cfloats;
     cudaStream_t cp = t->pipe_stream;
+    (void)err;
     // the copies start after the caller's queued work
     CUDA_TRY(cudaEventRecord(t->pipe_ev[2], user), "event record");
     CUDA_TRY(cudaStreamWaitEvent(cp, t->pipe_ev[2], 0), "wait");
     CUDA_TRY(cudaMemcpyAsync(d_r, h_radii, (size_t)S * sizeof(float), cudaMemcpyHostToDevice, cp), "radii H2D");
     const size_t nchunks = (C + chunk - 1) / chunk;
-    std::string err;
     for (size_t k = 0; k < nchunks; k++) {
         const int b = (int)(k & 1);
         const size_t c0 = k * chunk, cn = std::min(chunk, C - c0);

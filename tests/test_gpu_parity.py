@@ -194,9 +194,12 @@ def test_host_buffer_pipeline_matches_device_path(tabletop, capt_lib, torch_):
     r = tabletop["arm"].sphere_radius
     dev = capt_lib.capt_query_configs(tabletop["tree"], _cuda(torch_, cen), _cuda(torch_, r)).cpu().numpy()
     pinned = torch_.from_numpy(cen).pin_memory()
-    host = capt_lib.capt_query_configs_host(tabletop["tree"], pinned, r)
+    host = capt_lib.capt_query_configs_host(tabletop["tree"], pinned, r)   # read in place, flags copied
     assert np.array_equal(host, dev)
-    host2 = capt_lib.capt_query_configs_host(tabletop["tree"], cen, r)   # pageable memory
+    pflags = torch_.full((len(cen),), 7, dtype=torch_.uint8).pin_memory()
+    capt_lib.capt_query_configs_host(tabletop["tree"], pinned, r, pflags)  # both in place
+    assert np.array_equal(pflags.numpy(), dev)
+    host2 = capt_lib.capt_query_configs_host(tabletop["tree"], cen, r)   # pageable: chunked copies
     assert np.array_equal(host2, dev)
 
 
