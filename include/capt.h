@@ -62,10 +62,10 @@ typedef struct capt_tree_stats {
     uint64_t pruned_leaves;   /* leaves that kept {t} only (r_min condition, Alg. 1) */
     uint64_t empty_leaves;    /* leaves with |P_i| = 0 */
     uint64_t device_bytes;    /* bytes of the device layout (0 before upload) */
-    double build_ms;          /* wall time of capt_build */
+    double build_ms;          /* wall time of capt_build / capt_build_device */
     float r_min, r_max;
     int32_t device;           /* CUDA ordinal after upload, else -1 */
-    int32_t build_threads;
+    int32_t build_threads;    /* host threads of capt_build; 0 for capt_build_device */
 } capt_tree_stats;
 
 /* ---------------------------------------------------------------------------------
@@ -131,6 +131,25 @@ const char* capt_last_error(void);
  *   cloud  float[n][3] the input points (for the clearance gradient)
  * Calling it again re-uploads.  Errors: CAPT_E_ARG, CAPT_E_CUDA, CAPT_E_NOMEM. */
 int capt_upload(capt_tree* t, int device, void* stream);
+
+/* Build the CAPT on the current CUDA device (Alg. 1, Sec. IV-A/B) from points already
+ * in device memory.  The tree is the one capt_build makes from the same points and
+ * radii, bit for bit (splits, sets in ascending index, boxes, prune decisions), and it
+ * comes back already uploaded to the current device: the query calls can use it at
+ * once.  Instead of the recursion with a carried set z, each leaf's set is found
+ * directly as the points its closed cell affords (the same set, since the FP64
+ * distance only grows as a cell shrinks), the medians come from one sorted order per
+ * axis partitioned level by level.
+ * d_points: device float[n][3] on the current device, read during the call only.
+ * stream: the build's kernels and copies run on it; the call returns when they are
+ *   done.  Temporary device memory (about 100 bytes per leaf plus twice the affordance
+ *   sets) is allocated and freed inside the call.
+ * The host form (capt_stats, capt_export, capt_upload to another device) is copied
+ * back from the device the first time one of those calls needs it.
+ * Errors: CAPT_E_ARG (out == NULL, d_points == NULL with n > 0, n >= 2^30),
+ *         CAPT_E_RANGE (radii, or more than 2^32 point blocks in the sets),
+ *         CAPT_E_NONFINITE, CAPT_E_NOMEM, CAPT_E_CUDA. */
+int capt_build_device(const float* d_points, size_t n, float r_min, float r_max, void* stream, capt_tree** out);
 
 /* One flag per sphere (Alg. 3).  d_centers: device float[m][3]; d_radii: device
  * float[m]; d_flags: device uint8[m] receives 1 = collides, 0 = free.  m = 0 is a

@@ -22,7 +22,7 @@ __all__ = [
     "capt_get_launch_cfg", "capt_autotune_configs", "capt_validate_edges", "capt_edge_plan_create",
     "capt_edge_plan_launch", "capt_edge_plan_info", "capt_edge_plan_free", "capt_clearance_fwd",
     "capt_clearance_bwd", "capt_free", "capt_last_error", "make_arm", "CaptTree", "EdgePlan",
-    "capt_validate_edges_static", "CAPT_STATIC_MAX_EDGES",
+    "capt_validate_edges_static", "CAPT_STATIC_MAX_EDGES", "capt_build_device",
     "STATUS", "CAPT_STAGE_GLOBAL", "CAPT_STAGE_SMEM", "CAPT_KERNEL_SPHERES", "CAPT_KERNEL_CONFIGS",
     "CAPT_KERNEL_EDGES", "CAPT_KERNEL_CLEARANCE", "CAPT_EDGES_PERSISTENT", "CAPT_EDGES_PER_EDGE",
     "EXPORTED_SYMBOLS",
@@ -42,7 +42,7 @@ EXPORTED_SYMBOLS = [
     "capt_query_leaves", "capt_device_status", "capt_set_launch_cfg", "capt_get_launch_cfg",
     "capt_autotune_configs", "capt_validate_edges", "capt_edge_plan_create", "capt_edge_plan_launch",
     "capt_edge_plan_info", "capt_edge_plan_free", "capt_clearance_fwd", "capt_clearance_bwd",
-    "capt_validate_edges_static",
+    "capt_validate_edges_static", "capt_build_device",
 ]
 CAPT_STATIC_MAX_EDGES = 65536
 
@@ -91,6 +91,7 @@ def _load():
         "capt_stats": [P, C.POINTER(_Stats)],
         "capt_export": [P, P, P, P, P],
         "capt_upload": [P, I, P],
+        "capt_build_device": [P, SZ, F, F, P, C.POINTER(P)],
         "capt_query_spheres": [P, P, P, SZ, P, P],
         "capt_query_configs": [P, P, P, SZ, I, P, P],
         "capt_query_configs_host": [P, P, P, SZ, I, P, P],
@@ -230,6 +231,19 @@ def capt_free(tree: CaptTree):
 
 
 # --------------------------------------------------------------------------- device side
+
+def capt_build_device(points, r_min: float, r_max: float, stream=None) -> CaptTree:
+    """Build on the GPU from a contiguous float32 CUDA tensor [n, 3] on the current
+    device; the tree comes back uploaded to that device."""
+    import torch
+    if points.dim() != 2 or points.shape[1] != 3:
+        raise ValueError("points must be [n, 3]")
+    p = _dev(points, torch.float32, "points") if points.shape[0] else C.c_void_p(0)
+    h = C.c_void_p()
+    _check(_load().capt_build_device(p, points.shape[0], float(r_min), float(r_max), _stream(stream), C.byref(h)),
+           "capt_build_device")
+    return CaptTree(h)
+
 
 def capt_upload(tree: CaptTree, device: int = 0, stream=None):
     _check(_load().capt_upload(tree.h, int(device), _stream(stream)), "capt_upload")

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -11,6 +12,7 @@
 
 #include "../../include/capt.h"
 #include "capt_internal.h"
+#include "device_build.h"
 #include "kernels.h"
 
 using capt::DevArgs;
@@ -87,6 +89,13 @@ struct capt_tree {
     // edge validation scratch (persistent mode without a plan)
     uint32_t* d_edge_scratch = nullptr;
     size_t edge_scratch_cap = 0;
+    // tree built on the device: its plain arrays stay there until the host form is
+    // first needed (host_pending)
+    bool host_pending = false;
+    void* d_Tplain = nullptr;
+    void* d_set_idx = nullptr;
+    void* d_set_begin = nullptr;
+    void* d_pruned = nullptr;
     std::mutex mu;
 
     capt_tree() {
@@ -126,12 +135,14 @@ struct capt_tree {
         if (device < 0) return;
         DeviceGuard g(device);
         for (void* p : {d_T, d_leaves, d_blocks, d_ids, d_cloud, (void*)d_status, (void*)d_pipe_c[0], (void*)d_pipe_c[1],
-                        (void*)d_pipe_f[0], (void*)d_pipe_f[1], (void*)d_edge_scratch, (void*)d_zc_flags})
+                        (void*)d_pipe_f[0], (void*)d_pipe_f[1], (void*)d_edge_scratch, (void*)d_zc_flags, d_Tplain,
+                        d_set_idx, d_set_begin, d_pruned})
             if (p) cudaFree(p);
         for (auto& e : pipe_ev)
             if (e) cudaEventDestroy(e);
         if (pipe_stream) cudaStreamDestroy(pipe_stream);
         d_T = d_leaves = d_blocks = d_ids = d_cloud = nullptr;
+        d_Tplain = d_set_idx = d_set_begin = d_pruned = nullptr;
         d_status = nullptr;
         d_pipe_c[0] = d_pipe_c[1] = nullptr;
         d_pipe_f[0] = d_pipe_f[1] = nullptr;
@@ -240,6 +251,115 @@ int capt_build(const float* points, size_t n, float r_min, float r_max, capt_tre
     return capt_build_threads(points, n, r_min, r_max, 0, out);
 }
 
+namespace {
+
+// Fill the host form of a tree built on the device from its device arrays.
+int materialize_host(capt_tree* t) {
+    if (!t->host_pending) return CAPT_OK;
+    DeviceGuard g(t->device);
+    auto& h = t->h;
+    try {
+        h.pts.resize(3 * h.n);
+        h.T.resize(h.N > 1 ? h.N - 1 : 0);
+        h.set_begin.resize(h.N + 1);
+        h.pruned.resize(h.N);
+        h.aabb.resize(6 * h.N);
+        std::vector<capt::LeafRec> rec(h.N);
+        CUDA_TRY(cudaMemcpy(h.set_begin.data(), t->d_set_begin, (h.N + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost),
+                 "set offsets to host");
+        h.set_idx.resize(h.set_begin[h.N]);
+        if (!h.pts.empty())
+            CUDA_TRY(cudaMemcpy(h.pts.data(), t->d_cloud, h.pts.size() * sizeof(float), cudaMemcpyDeviceToHost),
+                     "points to host");
+        if (!h.T.empty())
+            CUDA_TRY(cudaMemcpy(h.T.data(), t->d_Tplain, h.T.size() * sizeof(float), cudaMemcpyDeviceToHost),
+                     "splits to host");
+        if (!h.set_idx.empty())
+            CUDA_TRY(cudaMemcpy(h.set_idx.data(), t->d_set_idx, h.set_idx.size() * sizeof(uint32_t),
+                                cudaMemcpyDeviceToHost),
+                     "sets to host");
+        CUDA_TRY(cudaMemcpy(h.pruned.data(), t->d_pruned, h.N, cudaMemcpyDeviceToHost), "prune flags to host");
+        CUDA_TRY(cudaMemcpy(rec.data(), t->d_leaves, h.N * sizeof(capt::LeafRec), cudaMemcpyDeviceToHost),
+                 "leaf records to host");
+        for (size_t l = 0; l < h.N; l++)
+            for (int d = 0; d < 3; d++) {
+                h.aabb[6 * l + d] = rec[l].lo[d];
+                h.aabb[6 * l + 3 + d] = rec[l].hi[d];
+            }
+    } catch (const std::bad_alloc&) {
+        return fail(CAPT_E_NOMEM, "host allocation failed while copying the tree to the host");
+    }
+    t->host_pending = false;
+    return CAPT_OK;
+}
+
+}  // namespace
+
+int capt_build_device(const float* d_points, size_t n, float r_min, float r_max, void* stream, capt_tree** out) {
+    if (!out) return fail(CAPT_E_ARG, "out is NULL");
+    *out = nullptr;
+    const auto t0 = std::chrono::steady_clock::now();
+    int dev = -1;
+    CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    capt_tree* t = nullptr;
+    try {
+        t = new capt_tree();
+    } catch (...) {
+        return fail(CAPT_E_NOMEM, "host allocation failed");
+    }
+    capt::DeviceTree d;
+    std::string err;
+    int rc = capt::device_build(d_points, n, r_min, r_max, static_cast<cudaStream_t>(stream), d, err);
+    if (rc != CAPT_OK) {
+        delete t;
+        return fail(rc, err);
+    }
+    int* status = nullptr;
+    cudaError_t e = cudaMalloc((void**)&status, 256);
+    if (e == cudaSuccess) e = cudaMemset(status, 0, 256);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (status) cudaFree(status);
+        d.release();
+        delete t;
+        return cuda_fail(e, "status word");
+    }
+    auto& h = t->h;
+    h.n = n;
+    h.N = d.N;
+    h.L = d.L;
+    h.r_min = r_min;
+    h.r_max = r_max;
+    h.build_threads = 0;
+    t->device = dev;
+    t->d_T = d.Tb;
+    t->d_leaves = d.leaves;
+    t->d_blocks = d.blocks;
+    t->d_ids = d.ids;
+    t->d_cloud = d.cloud;
+    t->d_status = status;
+    t->d_Tplain = d.Tplain;
+    t->d_set_idx = d.set_idx;
+    t->d_set_begin = d.set_begin;
+    t->d_pruned = d.pruned;
+    t->total_blocks = d.total_blocks;
+    t->tail_off = d.bs.tail_off;
+    t->K = d.bs.K;
+    t->R = d.bs.R;
+    t->Ks = d.bs.Ks;
+    t->tail_staged = d.bs.tail_staged;
+    t->stage_floats = d.bs.stage_floats;
+    for (int k = 0; k < 3; k++) {
+        t->box_lo[k] = d.box_lo[k];
+        t->box_hi[k] = d.box_hi[k];
+    }
+    t->dev_bytes = d.bytes + 256;
+    t->host_pending = true;
+    h.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = t;
+    return CAPT_OK;
+}
+
 int sfc_filter(const float* points, size_t n, float min_spacing, uint32_t* kept_idx, size_t* n_out) {
     std::string err;
     int rc = capt::host_sfc_filter(points, n, min_spacing, kept_idx, n_out, err);
@@ -248,6 +368,12 @@ int sfc_filter(const float* points, size_t n, float min_spacing, uint32_t* kept_
 
 int capt_stats(const capt_tree* t, capt_tree_stats* s) {
     if (!t || !s) return fail(CAPT_E_ARG, "NULL argument");
+    {
+        capt_tree* m = const_cast<capt_tree*>(t);
+        std::lock_guard<std::mutex> lk(m->mu);
+        const int rc = materialize_host(m);
+        if (rc) return rc;
+    }
     std::memset(s, 0, sizeof(*s));
     const auto& h = t->h;
     s->n_points = h.n;
@@ -277,6 +403,12 @@ int capt_stats(const capt_tree* t, capt_tree_stats* s) {
 
 int capt_export(const capt_tree* t, float* T, uint64_t* set_begin, uint32_t* set_idx, float* aabb) {
     if (!t) return fail(CAPT_E_ARG, "tree is NULL");
+    {
+        capt_tree* m = const_cast<capt_tree*>(t);
+        std::lock_guard<std::mutex> lk(m->mu);
+        const int rc = materialize_host(m);
+        if (rc) return rc;
+    }
     const auto& h = t->h;
     if (T && !h.T.empty()) std::memcpy(T, h.T.data(), h.T.size() * sizeof(float));
     if (set_begin) std::memcpy(set_begin, h.set_begin.data(), h.set_begin.size() * sizeof(uint64_t));
@@ -297,6 +429,8 @@ int capt_upload(capt_tree* t, int device, void* stream) {
     CUDA_TRY(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
     if (device < 0 || device >= ndev) return fail(CAPT_E_ARG, "device ordinal out of range");
     std::lock_guard<std::mutex> lk(t->mu);
+    int mrc = materialize_host(t);
+    if (mrc) return mrc;
     t->free_device();
     DeviceGuard g(device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);

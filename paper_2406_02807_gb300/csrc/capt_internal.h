@@ -50,7 +50,9 @@ struct BlockedSplits {
     uint32_t stage_floats = 0;  // prefix copied to shared memory by the staged kernels
     int Ks = 0;                 // super-levels inside that prefix
     int tail_staged = 0;        // 1 if the tail is inside it too
+    uint64_t total_floats = 0;  // size of data
 };
+void blocked_shape(int L, BlockedSplits& out);   // every field but data
 void blocked_splits(const HostTree& t, BlockedSplits& out);
 
 // Kernel view of an uploaded tree (raw device pointers, passed by value).

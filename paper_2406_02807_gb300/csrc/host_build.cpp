@@ -207,16 +207,33 @@ int build_host_tree(const float* points, size_t n, float r_min, float r_max, int
 // 8u+1 .. 8u+8), so one step is two 16-byte loads and three compares on x, y, z.
 // The last L mod 3 levels follow as one 4-float block per level-3K node
 // {T_i, T_2i+1, T_2i+2, +inf} (only T_i used when one level remains).
-void blocked_splits(const HostTree& t, BlockedSplits& out) {
-    const int L = t.L;
+void blocked_shape(int L, BlockedSplits& out) {
     out.K = L / 3;
     out.R = L % 3;
     uint64_t nblk = 0, p8 = 1;
     for (int k = 0; k < out.K; k++) { nblk += p8; p8 *= 8; }
     const uint64_t ntail = out.R ? (uint64_t(1) << (3 * out.K)) : 0;
     out.tail_off = (uint32_t)(8 * nblk);
-    out.data.assign(8 * nblk + 4 * ntail + 4, INFINITY);
+    out.total_floats = 8 * nblk + 4 * ntail + 4;
+    // shared-memory prefix: at most 4 super-levels (585 blocks, 18.7 KB), plus the tail
+    // when every super-level fits and the tail is at most 16 KB
+    out.Ks = out.K < 4 ? out.K : 4;
+    uint64_t sblk = 0;
+    p8 = 1;
+    for (int k = 0; k < out.Ks; k++) { sblk += p8; p8 *= 8; }
+    out.stage_floats = (uint32_t)(8 * sblk);
+    out.tail_staged = 0;
+    if (out.Ks == out.K && ntail && 4 * ntail <= 4096) {
+        out.stage_floats += (uint32_t)(4 * ntail);
+        out.tail_staged = 1;
+    }
+}
+
+void blocked_splits(const HostTree& t, BlockedSplits& out) {
+    blocked_shape(t.L, out);
+    out.data.assign(out.total_floats, INFINITY);
     const auto& T = t.T;
+    const uint64_t ntail = out.R ? (uint64_t(1) << (3 * out.K)) : 0;
     uint64_t base_u = 0;
     for (int k = 0; k < out.K; k++) {
         const uint64_t width = uint64_t(1) << (3 * k);
@@ -241,18 +258,6 @@ void blocked_splits(const HostTree& t, BlockedSplits& out) {
             b[1] = T[2 * i + 1];
             b[2] = T[2 * i + 2];
         }
-    }
-    // shared-memory prefix: at most 4 super-levels (585 blocks, 18.7 KB), plus the tail
-    // when every super-level fits and the tail is at most 16 KB
-    out.Ks = out.K < 4 ? out.K : 4;
-    uint64_t sblk = 0;
-    p8 = 1;
-    for (int k = 0; k < out.Ks; k++) { sblk += p8; p8 *= 8; }
-    out.stage_floats = (uint32_t)(8 * sblk);
-    out.tail_staged = 0;
-    if (out.Ks == out.K && ntail && 4 * ntail <= 4096) {
-        out.stage_floats += (uint32_t)(4 * ntail);
-        out.tail_staged = 1;
     }
 }
 
