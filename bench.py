@@ -38,7 +38,7 @@ R_MIN, R_MAX, R_FILTER = 0.02, 0.08, 0.01
 SM_MAX_MHZ = 2070.0
 # DRAM bytes (read + write) per launch of the configuration-query kernel from an ncu
 # capture, keyed by the hash of the kernel source it was taken on (null when stale).
-TRAFFIC = {"258953f80130fda8": 777239552 + 4401920}   # profiles/k_configs_tabletop_1M.md
+TRAFFIC = {"728b38eea5f8fb3a": 777285376 + 4831488}   # profiles/k_configs_tabletop_1M.md
 
 
 def parse():
@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--configs", type=int, default=1 << 20, help="configurations per GPU")
     ap.add_argument("--all", action="store_true", help="also time the clearance and the other clouds")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="time only the configuration query (for profiling); the JSON line lacks e2e and the rest")
     return ap.parse_args()
 
 
@@ -116,7 +118,7 @@ def src_hash(*names):
     return h.hexdigest()[:16]
 
 
-def tabletop_tree(capt):
+def tabletop_tree(capt, with_device=True):
     raw, _, arm = W.tabletop_scene(1001)
     t0 = time.perf_counter()
     kept = capt.sfc_filter(raw, R_FILTER)
@@ -128,11 +130,30 @@ def tabletop_tree(capt):
     del tree1
     tree = capt.capt_build(pts, R_MIN, R_MAX)
     st = capt.capt_stats(tree)
+    dev_ms = device_build_ms(capt, pts, R_MIN, R_MAX) if with_device else float("nan")
     return raw, pts, arm, tree, dict(filter_ms=round(filt_ms, 3), build_ms_1thread=round(build1_ms, 3),
                                      build_ms=round(st["build_ms"], 3), build_threads=st["build_threads"],
+                                     device_build_ms=round(dev_ms, 3),
                                      n_points=int(st["n_points"]), n_leaves=int(st["n_leaves"]),
                                      mean_set=round(st["total_afforded"] / st["n_leaves"], 2),
                                      max_set=int(st["max_set"]))
+
+
+def device_build_ms(capt, pts, r_min, r_max, reps=5):
+    """Median wall time of capt_build_device (points already on the device; the call
+    returns once the tree is complete), after one untimed call."""
+    import torch
+    d = torch.from_numpy(np.ascontiguousarray(pts, np.float32)).cuda()
+    capt.capt_build_device(d, r_min, r_max)
+    ts = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        t = capt.capt_build_device(d, r_min, r_max)
+        torch.cuda.synchronize()
+        ts.append((time.perf_counter() - t0) * 1e3)
+        del t
+    return statistics.median(ts)
 
 
 def time_events(torch, fn, steps, stream):
@@ -144,6 +165,23 @@ def time_events(torch, fn, steps, stream):
     e1.record(stream)
     e1.synchronize()
     return e0.elapsed_time(e1) / steps
+
+
+def time_events_flushed(torch, fn, steps, stream, flush):
+    """Mean device time of fn over `steps` calls, each timed alone with CUDA events
+    after a write of `flush` (a buffer larger than L2), so no call finds the previous
+    call's inputs in L2."""
+    total = 0.0
+    for _ in range(steps):
+        flush.add_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    return total / steps
 
 
 def cpu_baseline(pts, arm, sample_cfgs):
@@ -219,13 +257,12 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
 
-    raw, pts, arm, tree, host = tabletop_tree(capt)
+    raw, pts, arm, tree, host = tabletop_tree(capt, with_device=not args.headline_only)
     capt.capt_upload(tree, local)
     C = args.configs
     first, _ = weak_slice(C, rank)          # this rank's own configurations (weak scaling)
     q = W.random_configs(C, 1001, first=first)
     cen_host = torch.from_numpy(W.fk_centers(arm, q)).pin_memory()
-    del q
     cen = cen_host.to(dev, non_blocking=False)
     r_host = torch.from_numpy(arm.sphere_radius.copy())
     r = r_host.to(dev)
@@ -258,6 +295,57 @@ def main():
     value = world * C * SPHERES / (ms / 1e3)
     collide = float(flags.float().mean().item())
 
+    sec = None if args.headline_only else secondary(capt, torch, dev, stream, tree, arm, q, cen_host, r_host,
+                                                    flags, C, args, pg)
+
+    out = None
+    if rank == 0:
+        props = torch.cuda.get_device_properties(dev)
+        sms = props.multi_processor_count
+        peak_tops = sms * 128 * SM_MAX_MHZ * 1e6 / 1e12
+        achieved = ops_per_launch / (ms / 1e3) / 1e12
+        h = src_hash("kernels_query.cu", "scan.cuh", "device_common.cuh", "capt_internal.h")
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "tabletop_configs", "cloud": f"30,000-point tabletop, Morton filter at 1 cm -> "
+                                                                f"{len(pts)} points", "configs_per_gpu": C,
+                       "spheres_per_config": SPHERES, "r_min": R_MIN, "r_max": R_MAX,
+                       "l2": "inputs larger than L2 (755 MB of centres per step); the tree stays resident by design",
+                       "parallelism": f"replicas x{world}, configurations sharded by rank", "launch_cfg": tuned},
+            "ns_per_sphere_query": 1e9 / value * world,
+            "configs_per_s": world * C / (ms / 1e3),
+            "collision_fraction": collide,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "TFLOP/s",
+                         "frac": achieved / peak_tops, "traffic": TRAFFIC.get(h),
+                         "peak_basis": f"{sms} SMs x 128 FP32 lanes x {SM_MAX_MHZ:.0f} MHz (no FMA on this path)",
+                         "ops_per_launch": ops_per_launch,
+                         "work": {"spheres_examined": int(counts[0]), "near_cloud_box": int(counts[1]),
+                                  "leaf_box_pass": int(counts[2]), "points_scanned": int(counts[3]), "depth": L},
+                         "l1_bytes_per_launch": bytes_per_launch,
+                         "l1_frac": bytes_per_launch / (ms / 1e3) / (sms * 128 * SM_MAX_MHZ * 1e6)},
+            "host": host,
+            "gpu_launches": args.steps,
+            "clocks": clk,
+        }
+        if sec:
+            out.update(sec)
+        if args.all:
+            out["extra"] = extra_workloads(capt, torch, dev, stream, pts, arm, args)
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(pts, arm, 32768)
+        print(json.dumps(out), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+def secondary(capt, torch, dev, stream, tree, arm, q, cen_host, r_host, flags, C, args, pg):
+    """The host-buffer (e2e) run of the headline, edges (persistent graph vs per edge)
+    and the joint-angle configuration query, as extra keys of the JSON line."""
+    from paper_2406_02807_gb300.shard import max_over_ranks
+    world = pg.get_world_size() if pg else 1
     # end to end through the host-buffer entry point (copies inside the timed region)
     h_flags = torch.empty(C, dtype=torch.uint8).pin_memory()
     capt.capt_query_configs_host(tree, cen_host, r_host, h_flags)
@@ -296,52 +384,32 @@ def main():
     per_edge_ms = (time.perf_counter() - t0) * 1e3 / per_edge_steps
     edges_equal = bool(torch.equal(v_plan, valid2))
 
-    out = None
-    if rank == 0:
-        props = torch.cuda.get_device_properties(dev)
-        sms = props.multi_processor_count
-        peak_tops = sms * 128 * SM_MAX_MHZ * 1e6 / 1e12
-        achieved = ops_per_launch / (ms / 1e3) / 1e12
-        h = src_hash("kernels_query.cu", "scan.cuh", "device_common.cuh", "capt_internal.h")
-        out = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "tabletop_configs", "cloud": f"30,000-point tabletop, Morton filter at 1 cm -> "
-                                                                f"{len(pts)} points", "configs_per_gpu": C,
-                       "spheres_per_config": SPHERES, "r_min": R_MIN, "r_max": R_MAX,
-                       "l2": "inputs larger than L2 (755 MB of centres per step); the tree stays resident by design",
-                       "parallelism": f"replicas x{world}, configurations sharded by rank", "launch_cfg": tuned},
-            "ns_per_sphere_query": 1e9 / value * world,
-            "configs_per_s": world * C / (ms / 1e3),
-            "collision_fraction": collide,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "TFLOP/s",
-                         "frac": achieved / peak_tops, "traffic": TRAFFIC.get(h),
-                         "peak_basis": f"{sms} SMs x 128 FP32 lanes x {SM_MAX_MHZ:.0f} MHz (no FMA on this path)",
-                         "ops_per_launch": ops_per_launch,
-                         "work": {"spheres_examined": int(counts[0]), "near_cloud_box": int(counts[1]),
-                                  "leaf_box_pass": int(counts[2]), "points_scanned": int(counts[3]), "depth": L},
-                         "l1_bytes_per_launch": bytes_per_launch,
-                         "l1_frac": bytes_per_launch / (ms / 1e3) / (sms * 128 * SM_MAX_MHZ * 1e6)},
-            "e2e": {"value": world * C * SPHERES / e2e_s, "unit": UNIT,
-                    "h2d_bytes_per_step": C * SPHERES * 12 + SPHERES * 4, "d2h_bytes_per_step": C,
-                    "flags_equal_device_path": e2e_ok},
-            "edges": {"edges": 4096, "configs": int(ns.sum()), "persistent_graph_ms": edge_ms,
-                      "edges_per_s_persistent": 4096 / (edge_ms / 1e3), "per_edge_launch_ms": per_edge_ms,
-                      "edges_per_s_per_edge": 4096 / (per_edge_ms / 1e3), "valid_fraction": float(valid2.float().mean()),
-                      "equal_results": edges_equal, "launch_cfg": ecfg},
-            "host": host,
-            "gpu_launches": args.steps,
-            "clocks": clk,
-        }
-        if args.all:
-            out["extra"] = extra_workloads(capt, torch, dev, stream, pts, arm, args)
-        if world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(pts, arm, 32768)
-        print(json.dumps(out), flush=True)
-    if pg:
-        pg.barrier()
-        pg.destroy_process_group()
+    # the same configurations given by joint angles: kinematics inside the kernel, so
+    # the 755 MB of centres never exist (29 MB of joint angles instead; L2 flushed
+    # before every timed call because they would fit in it)
+    dq = torch.from_numpy(q).to(dev)
+    jflags = torch.empty(C, dtype=torch.uint8, device=dev)
+    jcfg, _ = capt.capt_autotune_joint_configs(tree, arm, dq, jflags)
+    flush = torch.zeros(64 << 20, dtype=torch.float32, device=dev)   # 256 MB > L2
+    for _ in range(3):
+        capt.capt_query_joint_configs(tree, arm, dq, jflags)
+    joint_ms = time_events_flushed(torch, lambda: capt.capt_query_joint_configs(tree, arm, dq, jflags), args.steps,
+                                   stream, flush)
+    del flush
+
+    return {
+        "e2e": {"value": world * C * SPHERES / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": C * SPHERES * 12 + SPHERES * 4, "d2h_bytes_per_step": C,
+                "flags_equal_device_path": e2e_ok},
+        "edges": {"edges": 4096, "configs": int(ns.sum()), "persistent_graph_ms": edge_ms,
+                  "edges_per_s_persistent": 4096 / (edge_ms / 1e3), "per_edge_launch_ms": per_edge_ms,
+                  "edges_per_s_per_edge": 4096 / (per_edge_ms / 1e3), "valid_fraction": float(valid2.float().mean()),
+                  "equal_results": edges_equal, "launch_cfg": ecfg},
+        "joint_configs": {"configs": C, "ms": joint_ms, "configs_per_s": world * C / (joint_ms / 1e3),
+                          "sphere_queries_per_s": world * C * SPHERES / (joint_ms / 1e3),
+                          "collision_fraction": float(jflags.float().mean().item()), "launch_cfg": jcfg,
+                          "input_bytes": int(q.nbytes), "l2": "flushed before every timed call"},
+    }
 
 
 def extra_workloads(capt, torch, dev, stream, pts, arm, args):
@@ -383,7 +451,7 @@ def extra_workloads(capt, torch, dev, stream, pts, arm, args):
     fl = torch.empty(1 << 22, dtype=torch.uint8, device=dev)
     ms = time_events(torch, lambda: capt.capt_query_spheres(tr, dc, dr, fl), 10, stream)
     res["room200k"] = {"spheres": 1 << 22, "ms": ms, "sphere_queries_per_s": (1 << 22) / (ms / 1e3),
-                       "build_ms": bms, "tree_device_bytes": int(st["device_bytes"]),
+                       "build_ms": bms, "device_build_ms": device_build_ms(capt, pr, 0.02, 0.10, reps=3), "tree_device_bytes": int(st["device_bytes"]),
                        "total_afforded": int(st["total_afforded"]), "max_set": int(st["max_set"])}
     return res
 

@@ -100,6 +100,22 @@ int capt_build_threads(const float* points, size_t n, float r_min, float r_max, 
  * Errors: CAPT_E_ARG, CAPT_E_RANGE (min_spacing < 0 or NaN), CAPT_E_NONFINITE, CAPT_E_NOMEM. */
 int sfc_filter(const float* points, size_t n, float min_spacing, uint32_t* kept_idx, size_t* n_out);
 
+/* sfc_filter on the GPU (Alg. 2, Sec. IV-C): the same kept indices in the same order.
+ * Each pass sorts the survivors by Morton key with a stable device radix sort and
+ * replaces the sequential sweep by its chain form (the next kept point after p_j is the
+ * first later point farther than min_spacing from p_j), marked by pointer doubling.
+ * d_points: device float[n][3] on the current device; d_kept: device uint32[n]
+ * (caller-owned) receives the kept indices in the last pass's curve order; *n_out
+ * (host) their count.  Work is stream-ordered on `stream`; the call synchronises it
+ * twice (finite check, count) and allocates and frees its temporaries with
+ * cudaMallocAsync / cudaFreeAsync on it.  The sweep costs the lengths of the runs of
+ * points within min_spacing of each other along the curve (quadratic in a run of
+ * coincident points).
+ * Errors: CAPT_E_ARG (NULL pointer, n >= 2^31), CAPT_E_RANGE (min_spacing < 0 or NaN),
+ *         CAPT_E_NONFINITE, CAPT_E_NOMEM, CAPT_E_CUDA. */
+int sfc_filter_device(const float* d_points, size_t n, float min_spacing, uint32_t* d_kept, size_t* n_out,
+                      void* stream);
+
 /* Statistics of a tree (host memory).  Errors: CAPT_E_ARG. */
 int capt_stats(const capt_tree* t, capt_tree_stats* out);
 
@@ -201,14 +217,16 @@ int capt_device_status(const capt_tree* t, void* stream);
 enum { CAPT_STAGE_GLOBAL = 0, /* T read through L1/L2 */
        CAPT_STAGE_SMEM = 1    /* the top levels of T copied to shared memory by a bulk
                                  asynchronous (TMA) copy at block start */ };
-enum { CAPT_KERNEL_SPHERES = 0, CAPT_KERNEL_CONFIGS = 1, CAPT_KERNEL_EDGES = 2, CAPT_KERNEL_CLEARANCE = 3 };
+enum { CAPT_KERNEL_SPHERES = 0, CAPT_KERNEL_CONFIGS = 1, CAPT_KERNEL_EDGES = 2, CAPT_KERNEL_CLEARANCE = 3,
+       CAPT_KERNEL_JOINTS = 4, CAPT_N_KERNELS = 5 };
 
 typedef struct capt_launch_cfg {
     int32_t warps_per_block;   /* 1..16 */
     int32_t spheres_per_lane;  /* tile size.  Spheres: 1, 2, 4 or 8 spheres per lane
                                   (32 x that per warp tile).  Configurations: 2, 4 or 8,
-                                  for 4, 8 or 16 configurations per warp tile.  Edges:
-                                  not used (one configuration per lane). */
+                                  for 4, 8 or 16 configurations per warp tile.  Edges
+                                  and joint-angle configurations: not used (one
+                                  configuration per lane). */
     int32_t staging;           /* CAPT_STAGE_* */
     int32_t chunk;             /* edges: configurations per work item (1..1024, rounded
                                   up to a multiple of 32) */
@@ -283,6 +301,23 @@ int capt_validate_edges(capt_tree* t, const capt_arm* arm, const float* d_qa, co
 #define CAPT_STATIC_MAX_EDGES 65536
 int capt_validate_edges_static(const capt_tree* t, const capt_arm* arm, const float* d_qa, const float* d_qb,
                                const int32_t* d_nsteps, size_t E, uint8_t* d_valid, void* stream);
+
+/* One flag per configuration given by its joint angles: the arm's kinematics run
+ * inside the kernel (the same FP32 chain and sin/cos as the edge validator, one lane
+ * per configuration) and each sphere centre is tested as it appears, so the sphere
+ * centres never exist in memory.  Flag = 1 iff any sphere collides (Sec. IV-D: a
+ * configuration stops being checked at its first colliding sphere); the flags equal
+ * those of capt_query_configs on the centres that kinematics gives.
+ * d_q: device float[C][arm->n_joints]; d_flags: device uint8[C]; arm: host pointer,
+ * copied.  C = 0 is a no-op.  Errors: CAPT_E_ARG, CAPT_E_STATE, CAPT_E_CUDA. */
+int capt_query_joint_configs(const capt_tree* t, const capt_arm* arm, const float* d_q, size_t C,
+                             uint8_t* d_flags, void* stream);
+
+/* Time every supported launch configuration of capt_query_joint_configs (warps per
+ * block x staging) on these inputs, keep the fastest on the tree and return it.
+ * d_flags is overwritten; best_ms may be NULL.  Synchronises `stream`. */
+int capt_autotune_joint_configs(capt_tree* t, const capt_arm* arm, const float* d_q, size_t C, uint8_t* d_flags,
+                                void* stream, capt_launch_cfg* best, float* best_ms);
 
 /* A captured CUDA graph of the persistent edge validator for fixed buffers: one
  * capt_edge_plan_launch replays {work-counter reset, per-edge prefix of work items,

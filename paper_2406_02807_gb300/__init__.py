@@ -22,8 +22,8 @@ __all__ = [
     "capt_get_launch_cfg", "capt_autotune_configs", "capt_validate_edges", "capt_edge_plan_create",
     "capt_edge_plan_launch", "capt_edge_plan_info", "capt_edge_plan_free", "capt_clearance_fwd",
     "capt_clearance_bwd", "capt_free", "capt_last_error", "make_arm", "CaptTree", "EdgePlan",
-    "capt_validate_edges_static", "CAPT_STATIC_MAX_EDGES", "capt_build_device",
-    "STATUS", "CAPT_STAGE_GLOBAL", "CAPT_STAGE_SMEM", "CAPT_KERNEL_SPHERES", "CAPT_KERNEL_CONFIGS",
+    "capt_validate_edges_static", "CAPT_STATIC_MAX_EDGES", "capt_build_device", "capt_query_joint_configs",
+    "capt_autotune_joint_configs", "CAPT_KERNEL_JOINTS", "sfc_filter_device", "STATUS", "CAPT_STAGE_GLOBAL", "CAPT_STAGE_SMEM", "CAPT_KERNEL_SPHERES", "CAPT_KERNEL_CONFIGS",
     "CAPT_KERNEL_EDGES", "CAPT_KERNEL_CLEARANCE", "CAPT_EDGES_PERSISTENT", "CAPT_EDGES_PER_EDGE",
     "EXPORTED_SYMBOLS",
 ]
@@ -31,7 +31,7 @@ __all__ = [
 STATUS = {0: "CAPT_OK", -1: "CAPT_E_ARG", -2: "CAPT_E_RANGE", -3: "CAPT_E_NONFINITE", -4: "CAPT_E_NOMEM",
           -5: "CAPT_E_CUDA", -6: "CAPT_E_TIMEOUT", -7: "CAPT_E_BOUNDS", -8: "CAPT_E_STATE"}
 CAPT_STAGE_GLOBAL, CAPT_STAGE_SMEM = 0, 1
-CAPT_KERNEL_SPHERES, CAPT_KERNEL_CONFIGS, CAPT_KERNEL_EDGES, CAPT_KERNEL_CLEARANCE = 0, 1, 2, 3
+CAPT_KERNEL_SPHERES, CAPT_KERNEL_CONFIGS, CAPT_KERNEL_EDGES, CAPT_KERNEL_CLEARANCE, CAPT_KERNEL_JOINTS = 0, 1, 2, 3, 4
 CAPT_EDGES_PERSISTENT, CAPT_EDGES_PER_EDGE = 0, 1
 MAX_JOINTS, MAX_SPHERES = 16, 64
 
@@ -42,7 +42,8 @@ EXPORTED_SYMBOLS = [
     "capt_query_leaves", "capt_device_status", "capt_set_launch_cfg", "capt_get_launch_cfg",
     "capt_autotune_configs", "capt_validate_edges", "capt_edge_plan_create", "capt_edge_plan_launch",
     "capt_edge_plan_info", "capt_edge_plan_free", "capt_clearance_fwd", "capt_clearance_bwd",
-    "capt_validate_edges_static", "capt_build_device",
+    "capt_validate_edges_static", "capt_build_device", "capt_query_joint_configs", "capt_autotune_joint_configs",
+    "sfc_filter_device",
 ]
 CAPT_STATIC_MAX_EDGES = 65536
 
@@ -88,6 +89,7 @@ def _load():
         "capt_build": [P, SZ, F, F, C.POINTER(P)],
         "capt_build_threads": [P, SZ, F, F, I, C.POINTER(P)],
         "sfc_filter": [P, SZ, F, P, C.POINTER(SZ)],
+        "sfc_filter_device": [P, SZ, F, P, C.POINTER(SZ), P],
         "capt_stats": [P, C.POINTER(_Stats)],
         "capt_export": [P, P, P, P, P],
         "capt_upload": [P, I, P],
@@ -103,6 +105,8 @@ def _load():
         "capt_autotune_configs": [P, P, P, SZ, I, P, P, C.POINTER(_LaunchCfg), C.POINTER(F)],
         "capt_validate_edges": [P, C.POINTER(_Arm), P, P, P, SZ, P, I, P],
         "capt_validate_edges_static": [P, C.POINTER(_Arm), P, P, P, SZ, P, P],
+        "capt_query_joint_configs": [P, C.POINTER(_Arm), P, SZ, P, P],
+        "capt_autotune_joint_configs": [P, C.POINTER(_Arm), P, SZ, P, P, C.POINTER(_LaunchCfg), C.POINTER(F)],
         "capt_edge_plan_create": [P, C.POINTER(_Arm), P, P, P, SZ, P, C.POINTER(_LaunchCfg), P, C.POINTER(P)],
         "capt_edge_plan_launch": [P, P],
         "capt_edge_plan_info": [P, C.POINTER(_LaunchCfg), C.POINTER(F)],
@@ -205,6 +209,21 @@ def sfc_filter(points, min_spacing: float) -> np.ndarray:
     n = C.c_size_t(0)
     _check(_load().sfc_filter(_ptr(p), p.shape[0], float(min_spacing), _ptr(out), C.byref(n)), "sfc_filter")
     return out[: n.value].copy()
+
+
+def sfc_filter_device(points, min_spacing: float, stream=None):
+    """Alg. 2 on the GPU: points is a float32 CUDA tensor [n, 3]; returns the kept
+    indices (int32 CUDA tensor, last pass's curve order), equal to sfc_filter's."""
+    import torch
+    if points.dim() != 2 or points.shape[1] != 3:
+        raise ValueError("points must be [n, 3]")
+    n = points.shape[0]
+    kept = torch.empty(max(n, 1), dtype=torch.int32, device=points.device)
+    p = _dev(points, torch.float32, "points") if n else C.c_void_p(0)
+    cnt = C.c_size_t(0)
+    _check(_load().sfc_filter_device(p, n, float(min_spacing), _dev(kept, torch.int32, "kept"), C.byref(cnt),
+                                     _stream(stream)), "sfc_filter_device")
+    return kept[: cnt.value]
 
 
 def capt_stats(tree: CaptTree) -> dict:
@@ -382,6 +401,36 @@ def capt_validate_edges(tree: CaptTree, arm, qa, qb, nsteps, valid=None, mode=CA
                                        _dev(nsteps, torch.int32, "nsteps"), E, _dev(valid, torch.uint8, "valid"),
                                        int(mode), _stream(stream)), "capt_validate_edges")
     return valid
+
+
+def capt_query_joint_configs(tree: CaptTree, arm, q, flags=None, stream=None):
+    """One flag per configuration given by joint angles q [C, n_joints] (float32 CUDA
+    tensor); the kinematics run inside the kernel."""
+    import torch
+    a = arm if isinstance(arm, _Arm) else make_arm(arm)
+    if q.dim() != 2 or q.shape[1] != a.n_joints:
+        raise ValueError("q must be [C, n_joints]")
+    Cn = q.shape[0]
+    if flags is None:
+        flags = torch.empty(Cn, dtype=torch.uint8, device=q.device)
+    _check(_load().capt_query_joint_configs(tree.h, C.byref(a), _dev(q, torch.float32, "q"), Cn,
+                                            _dev(flags, torch.uint8, "flags"), _stream(stream)),
+           "capt_query_joint_configs")
+    return flags
+
+
+def capt_autotune_joint_configs(tree: CaptTree, arm, q, flags=None, stream=None):
+    import torch
+    a = arm if isinstance(arm, _Arm) else make_arm(arm)
+    Cn = q.shape[0]
+    if flags is None:
+        flags = torch.empty(Cn, dtype=torch.uint8, device=q.device)
+    c = _LaunchCfg()
+    ms = C.c_float()
+    _check(_load().capt_autotune_joint_configs(tree.h, C.byref(a), _dev(q, torch.float32, "q"), Cn,
+                                               _dev(flags, torch.uint8, "flags"), _stream(stream), C.byref(c),
+                                               C.byref(ms)), "capt_autotune_joint_configs")
+    return {k: getattr(c, k) for k, _ in _LaunchCfg._fields_}, ms.value
 
 
 def capt_validate_edges_static(tree: CaptTree, arm, qa, qb, nsteps, valid=None, stream=None):

@@ -57,6 +57,7 @@ bool valid_cfg(int kernel, const capt_launch_cfg& c) {
     if (kernel == CAPT_KERNEL_CONFIGS) return spl == 2 || spl == 4 || spl == 8;
     if (kernel == CAPT_KERNEL_EDGES) return c.chunk >= 1 && c.chunk <= 1024;   // one configuration per lane
     if (kernel == CAPT_KERNEL_CLEARANCE) return true;
+    if (kernel == CAPT_KERNEL_JOINTS) return true;   // one configuration per lane
     return false;
 }
 
@@ -77,7 +78,7 @@ struct capt_tree {
     float box_lo[3] = {INFINITY, INFINITY, INFINITY};     // bounding box of every point
     float box_hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     int K = 0, R = 0, Ks = 0, tail_staged = 0;
-    capt_launch_cfg cfg[4];
+    capt_launch_cfg cfg[CAPT_N_KERNELS];
     // host-buffer pipeline
     float* d_pipe_c[2] = {nullptr, nullptr};
     uint8_t* d_pipe_f[2] = {nullptr, nullptr};
@@ -103,6 +104,7 @@ struct capt_tree {
         cfg[CAPT_KERNEL_CONFIGS] = {8, 2, CAPT_STAGE_SMEM, 0};
         cfg[CAPT_KERNEL_EDGES] = {8, 2, CAPT_STAGE_SMEM, 32};
         cfg[CAPT_KERNEL_CLEARANCE] = {8, 2, CAPT_STAGE_SMEM, 0};
+        cfg[CAPT_KERNEL_JOINTS] = {4, 1, CAPT_STAGE_GLOBAL, 0};
     }
 
     DevArgs args() const {
@@ -363,6 +365,13 @@ int capt_build_device(const float* d_points, size_t n, float r_min, float r_max,
 int sfc_filter(const float* points, size_t n, float min_spacing, uint32_t* kept_idx, size_t* n_out) {
     std::string err;
     int rc = capt::host_sfc_filter(points, n, min_spacing, kept_idx, n_out, err);
+    return rc == CAPT_OK ? rc : fail(rc, err);
+}
+
+int sfc_filter_device(const float* d_points, size_t n, float min_spacing, uint32_t* d_kept, size_t* n_out,
+                      void* stream) {
+    std::string err;
+    int rc = capt::device_sfc_filter(d_points, n, min_spacing, d_kept, n_out, static_cast<cudaStream_t>(stream), err);
     return rc == CAPT_OK ? rc : fail(rc, err);
 }
 
@@ -628,14 +637,14 @@ int capt_device_status(const capt_tree* t, void* stream) {
 }
 
 int capt_set_launch_cfg(capt_tree* t, int kernel, const capt_launch_cfg* cfg) {
-    if (!t || !cfg || kernel < 0 || kernel > 3) return fail(CAPT_E_ARG, "bad argument");
+    if (!t || !cfg || kernel < 0 || kernel >= CAPT_N_KERNELS) return fail(CAPT_E_ARG, "bad argument");
     if (!valid_cfg(kernel, *cfg)) return fail(CAPT_E_ARG, "unsupported launch configuration");
     t->cfg[kernel] = *cfg;
     return CAPT_OK;
 }
 
 int capt_get_launch_cfg(const capt_tree* t, int kernel, capt_launch_cfg* cfg) {
-    if (!t || !cfg || kernel < 0 || kernel > 3) return fail(CAPT_E_ARG, "bad argument");
+    if (!t || !cfg || kernel < 0 || kernel >= CAPT_N_KERNELS) return fail(CAPT_E_ARG, "bad argument");
     *cfg = t->cfg[kernel];
     return CAPT_OK;
 }
@@ -764,6 +773,62 @@ int capt_validate_edges(capt_tree* t, const capt_arm* arm, const float* d_qa, co
     rc = capt::launch_edges_persistent(t->args(), *arm, d_qa, d_qb, d_nsteps, E, d_valid, t->d_edge_scratch,
                                        t->cfg[CAPT_KERNEL_EDGES], st, err);
     return rc ? fail(rc, err) : CAPT_OK;
+}
+
+int capt_query_joint_configs(const capt_tree* t, const capt_arm* arm, const float* d_q, size_t C, uint8_t* d_flags,
+                             void* stream) {
+    int rc = check_ready(t);
+    if (rc) return rc;
+    if ((rc = check_arm(arm))) return rc;
+    if (C == 0) return CAPT_OK;
+    if (!d_q || !d_flags) return fail(CAPT_E_ARG, "NULL device pointer");
+    std::string err;
+    rc = capt::launch_joint_configs(t->args(), *arm, d_q, C, d_flags, t->cfg[CAPT_KERNEL_JOINTS],
+                                    static_cast<cudaStream_t>(stream), err);
+    return rc ? fail(rc, err) : CAPT_OK;
+}
+
+int capt_autotune_joint_configs(capt_tree* t, const capt_arm* arm, const float* d_q, size_t C, uint8_t* d_flags,
+                                void* stream, capt_launch_cfg* best, float* best_ms) {
+    int rc = check_ready(t);
+    if (rc) return rc;
+    if ((rc = check_arm(arm))) return rc;
+    if (C == 0) return fail(CAPT_E_ARG, "need C > 0");
+    if (!d_q || !d_flags) return fail(CAPT_E_ARG, "NULL device pointer");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0), "event");
+    CUDA_TRY(cudaEventCreate(&e1), "event");
+    float best_t = INFINITY;
+    capt_launch_cfg best_c = t->cfg[CAPT_KERNEL_JOINTS];
+    std::string err;
+    for (int warps : {2, 4, 8, 16})
+        for (int stage : {CAPT_STAGE_GLOBAL, CAPT_STAGE_SMEM}) {
+            capt_launch_cfg c = {warps, 1, stage, 0};
+            float tt = INFINITY;
+            for (int rep = 0; rep < 3; rep++) {
+                cudaEventRecord(e0, st);
+                rc = capt::launch_joint_configs(t->args(), *arm, d_q, C, d_flags, c, st, err);
+                cudaEventRecord(e1, st);
+                if (rc) break;
+                if (cudaEventSynchronize(e1) != cudaSuccess) { rc = CAPT_E_CUDA; break; }
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) tt = std::min(tt, ms);
+            }
+            if (rc) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return fail(rc, err.empty() ? "autotune failed" : err);
+            }
+            if (tt < best_t) { best_t = tt; best_c = c; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    t->cfg[CAPT_KERNEL_JOINTS] = best_c;
+    if (best) *best = best_c;
+    if (best_ms) *best_ms = best_t;
+    return CAPT_OK;
 }
 
 void capt_edge_plan_free(capt_edge_plan* p) {

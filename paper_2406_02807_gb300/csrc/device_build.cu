@@ -37,13 +37,6 @@
 namespace capt {
 namespace {
 
-// Order-preserving unsigned key of a float (-0 and +0 share one key, as they compare
-// equal).
-__host__ __device__ __forceinline__ uint32_t fkey_bits(uint32_t u) {
-    if (u == 0x80000000u) u = 0u;
-    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
-__device__ __forceinline__ uint32_t fkey(float f) { return fkey_bits(__float_as_uint(f)); }
 
 __device__ __forceinline__ float coord(const float* __restrict__ pts, uint32_t n, uint32_t i, int d) {
     return i < n ? pts[3 * (size_t)i + d] : INFINITY;

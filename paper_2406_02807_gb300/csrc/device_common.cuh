@@ -173,6 +173,17 @@ __device__ __forceinline__ const float* stage_splits(const DevArgs& t, void* sme
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
+// Order-preserving unsigned key of a float (-0 and +0 share one key, as they compare
+// equal), and its inverse.
+__host__ __device__ __forceinline__ uint32_t fkey_bits(uint32_t u) {
+    if (u == 0x80000000u) u = 0u;
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ uint32_t fkey(float f) { return fkey_bits(__float_as_uint(f)); }
+__device__ __forceinline__ float fkey_float(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
 // Inclusive warp prefix sum.
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
     const uint32_t lane = lane_id();

@@ -1,0 +1,430 @@
+// Space-filling-curve filter on the GPU (Alg. 2, Sec. IV-C).  The result is the host
+// filter's bit for bit: the same kept points, in the same (last pass's curve) order.
+//
+// Per pass (one per axis permutation):
+//  1. The survivors, taken in ascending point index, get their 63-bit Morton key (21
+//     bits per axis over the input's bounding box, quantised in FP64 exactly as the
+//     host does) and are sorted by it with a stable LSD radix sort: 8 digits of 8 bits,
+//     4096 elements per block, stable inside a block because it ranks rounds of 256
+//     elements in index order.
+//  2. The greedy sweep of Alg. 2 keeps p_j iff its FP32 squared distance to the last
+//     kept point exceeds fl(r^2).  That is a chain: with next(j) = the first k > j whose
+//     distance to p_j exceeds the spacing, the kept positions are 0, next(0),
+//     next(next(0)), ...  Every next(j) comes from an independent forward scan; the
+//     chain is then marked by pointer doubling, ceil(log2 n) rounds in which every
+//     marked position marks its 2^k-th successor (after round k every chain element of
+//     rank below 2^(k+1) is marked).
+//  3. The marked points survive into the next pass.
+// The forward scans cost the lengths of the runs of points lying within the spacing of
+// each other along the curve: a few points for sampled surfaces, but quadratic in the
+// run length for many coincident points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+
+#include "capt_internal.h"
+#include "device_common.cuh"
+#include "kernels.h"
+
+namespace capt {
+namespace {
+
+constexpr int kFT = 256;                  // threads per block
+constexpr int kFE = 16;                   // elements per thread in the blocked kernels
+constexpr uint32_t kFTile = kFT * kFE;    // 4096 elements per block
+constexpr int kScanThreads = 1024;
+
+// Spread the low 21 bits of v so that bit b moves to bit 3b.
+__device__ __forceinline__ uint64_t spread21(uint32_t v) {
+    uint64_t x = v & 0x1fffffu;
+    x = (x | (x << 32)) & 0x1f00000000ffffull;
+    x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+// box: lo keys [0..2], hi keys [3..5], non-finite flag [6].
+__global__ void kf_bbox(const float* __restrict__ pts, uint32_t n, uint32_t* __restrict__ box) {
+    uint32_t lo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, hi[3] = {0u, 0u, 0u};
+    uint32_t bad = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        for (int d = 0; d < 3; d++) {
+            const float v = pts[3 * (size_t)i + d];
+            bad |= isfinite(v) ? 0u : 1u;
+            const uint32_t k = fkey(v);
+            lo[d] = min(lo[d], k);
+            hi[d] = max(hi[d], k);
+        }
+    for (int o = 16; o > 0; o >>= 1)
+        for (int d = 0; d < 3; d++) {
+            lo[d] = min(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+            hi[d] = max(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+        }
+    bad = __any_sync(0xffffffffu, bad != 0) ? 1u : 0u;
+    if (lane_id() == 0) {
+        for (int d = 0; d < 3; d++) {
+            atomicMin(box + d, lo[d]);
+            atomicMax(box + 3 + d, hi[d]);
+        }
+        if (bad) atomicOr(box + 6, 1u);
+    }
+}
+
+// Spread quantised coordinates: q = min(2^21 - 1, floor((p - lo) / (hi - lo) * 2^21)) in
+// FP64, q = 0 on an axis of zero extent.
+__global__ void kf_spread(const float* __restrict__ pts, uint32_t n, const uint32_t* __restrict__ box,
+                          uint64_t* __restrict__ sp) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int a = 0; a < 3; a++) {
+        const double lo = (double)fkey_float(box[a]);
+        const double hi = (double)fkey_float(box[3 + a]);
+        const double ext = __dsub_rn(hi, lo);
+        uint32_t v = 0;
+        if (ext > 0.0) {
+            const double f = floor(__dmul_rn(__ddiv_rn(__dsub_rn((double)pts[3 * (size_t)i + a], lo), ext), 2097152.0));
+            v = f >= 2097151.0 ? 2097151u : (uint32_t)f;
+        }
+        sp[3 * (size_t)i + a] = spread21(v);
+    }
+}
+
+// Block-wide exclusive prefix of one flag per thread (256 threads); returns the prefix
+// and writes the block total to *total.  Uses ws[8].
+__device__ __forceinline__ uint32_t block_prefix(bool f, uint32_t* ws, uint32_t* total) {
+    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+    const uint32_t b = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) ws[warp] = __popc(b);
+    __syncthreads();
+    uint32_t before = 0, all = 0;
+#pragma unroll
+    for (int w = 0; w < kFT / 32; w++) {
+        const uint32_t c = ws[w];
+        before += (uint32_t)w < warp ? c : 0u;
+        all += c;
+    }
+    __syncthreads();
+    *total = all;
+    return before + __popc(b & ((1u << lane) - 1u));
+}
+
+// Set flags per block of 4096 positions (positions < len, len = *d_len if given).
+__global__ void __launch_bounds__(kFT) kf_flag_count(const uint8_t* __restrict__ flags, const uint32_t* d_len,
+                                                      uint32_t len, uint32_t* __restrict__ counts) {
+    __shared__ uint32_t ws[kFT / 32];
+    if (d_len) len = *d_len;
+    uint32_t c = 0;
+    for (int r = 0; r < kFE; r++) {
+        const uint32_t i = blockIdx.x * kFTile + (uint32_t)r * kFT + threadIdx.x;
+        c += (i < len && flags[i]) ? 1u : 0u;
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane_id() == 0) ws[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t s = 0;
+        for (int w = 0; w < kFT / 32; w++) s += ws[w];
+        counts[blockIdx.x] = s;
+    }
+}
+
+// Exclusive prefix of len values in place by one block; the sum goes to *total if given.
+__global__ void __launch_bounds__(kScanThreads) kf_scan(uint32_t* __restrict__ v, uint32_t len,
+                                                         uint32_t* __restrict__ total) {
+    __shared__ uint32_t ws[32];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (uint32_t base = 0; base < len; base += blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        const uint32_t x = i < len ? v[i] : 0u;
+        const uint32_t incl = warp_incl_scan(x);
+        if (lane == 31) ws[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t y = lane < nw ? ws[lane] : 0u;
+            y = warp_incl_scan(y);
+            if (lane < nw) ws[lane] = y;
+        }
+        __syncthreads();
+        const uint32_t before = carry + (warp ? ws[warp - 1] : 0u);
+        if (i < len) v[i] = before + incl - x;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += ws[nw - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
+// Stable compaction: out[k] = the k-th set position (or vals[position]) in order.
+__global__ void __launch_bounds__(kFT) kf_flag_compact(const uint8_t* __restrict__ flags, const uint32_t* d_len,
+                                                        uint32_t len, const uint32_t* __restrict__ offs,
+                                                        const uint32_t* __restrict__ vals,
+                                                        uint32_t* __restrict__ out) {
+    __shared__ uint32_t ws[kFT / 32];
+    if (d_len) len = *d_len;
+    uint32_t base = offs[blockIdx.x];
+    for (int r = 0; r < kFE; r++) {
+        const uint32_t i = blockIdx.x * kFTile + (uint32_t)r * kFT + threadIdx.x;
+        const bool f = i < len && flags[i];
+        uint32_t tot;
+        const uint32_t pre = block_prefix(f, ws, &tot);
+        if (f) out[base + pre] = vals ? vals[i] : i;
+        base += tot;
+    }
+}
+
+// Morton keys of the survivors under one axis permutation (X[0] most significant in
+// every bit triple), split into low and high words; val = point index.
+__global__ void kf_keys(const uint32_t* __restrict__ asc, const uint32_t* __restrict__ d_m,
+                        const uint64_t* __restrict__ sp, int x0, int x1, int x2, uint32_t* __restrict__ klo,
+                        uint32_t* __restrict__ khi, uint32_t* __restrict__ val) {
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= *d_m) return;
+    const uint32_t i = asc[j];
+    const uint64_t* s = sp + 3 * (size_t)i;
+    const uint64_t key = (s[x0] << 2) | (s[x1] << 1) | s[x2];
+    klo[j] = (uint32_t)key;
+    khi[j] = (uint32_t)(key >> 32);
+    val[j] = i;
+}
+
+__global__ void __launch_bounds__(kFT) kf_hist(const uint32_t* __restrict__ kw, const uint32_t* __restrict__ d_m,
+                                                int shift, uint32_t* __restrict__ hist, uint32_t nblk) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t m = *d_m;
+    for (int r = 0; r < kFE; r++) {
+        const uint32_t i = blockIdx.x * kFTile + (uint32_t)r * kFT + threadIdx.x;
+        if (i < m) atomicAdd(&h[(kw[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];   // digit-major
+}
+
+// Stable scatter by the digit of ka at `shift`; kb and val travel with it.
+__global__ void __launch_bounds__(kFT) kf_scatter(const uint32_t* __restrict__ ka, const uint32_t* __restrict__ kb,
+                                                   const uint32_t* __restrict__ val, const uint32_t* __restrict__ d_m,
+                                                   int shift, const uint32_t* __restrict__ off, uint32_t nblk,
+                                                   uint32_t* __restrict__ ka_o, uint32_t* __restrict__ kb_o,
+                                                   uint32_t* __restrict__ val_o) {
+    __shared__ uint32_t base[256];
+    __shared__ uint32_t cnt[kFT / 32][256];
+    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+    base[threadIdx.x] = off[threadIdx.x * nblk + blockIdx.x];
+    const uint32_t m = *d_m;
+    for (int r = 0; r < kFE; r++) {
+        for (int w = 0; w < kFT / 32; w++) cnt[w][threadIdx.x] = 0;
+        __syncthreads();
+        const uint32_t i = blockIdx.x * kFTile + (uint32_t)r * kFT + threadIdx.x;
+        const bool valid = i < m;
+        const uint32_t a = valid ? ka[i] : 0u;
+        const uint32_t d = valid ? ((a >> shift) & 255u) : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+        if (valid && rank == 0) cnt[warp][d] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            uint32_t before = 0;
+            for (uint32_t w = 0; w < warp; w++) before += cnt[w][d];
+            const uint32_t pos = base[d] + before + rank;
+            ka_o[pos] = a;
+            kb_o[pos] = kb[i];
+            val_o[pos] = val[i];
+        }
+        __syncthreads();
+        uint32_t tot = 0;
+        for (int w = 0; w < kFT / 32; w++) tot += cnt[w][threadIdx.x];
+        base[threadIdx.x] += tot;
+        __syncthreads();
+    }
+}
+
+// Coordinates of the sorted survivors, structure of arrays.
+__global__ void kf_gather(const uint32_t* __restrict__ val, const uint32_t* __restrict__ d_m,
+                          const float* __restrict__ pts, float* __restrict__ xs, float* __restrict__ ys,
+                          float* __restrict__ zs) {
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= *d_m) return;
+    const float* p = pts + 3 * (size_t)val[j];
+    xs[j] = p[0];
+    ys[j] = p[1];
+    zs[j] = p[2];
+}
+
+// next(j) = first k > j with fl(d^2(p_j, p_k)) > r2 (m if none); marks position 0.
+__global__ void kf_next(const float* __restrict__ xs, const float* __restrict__ ys, const float* __restrict__ zs,
+                        const uint32_t* __restrict__ d_m, float r2, uint32_t* __restrict__ next,
+                        uint8_t* __restrict__ mark) {
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t m = *d_m;
+    if (j >= m) return;
+    const float ax = xs[j], ay = ys[j], az = zs[j];
+    uint32_t k = j + 1;
+    for (; k < m; k++) {
+        const float dx = __fsub_rn(ax, xs[k]);
+        const float dy = __fsub_rn(ay, ys[k]);
+        const float dz = __fsub_rn(az, zs[k]);
+        const float s = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+        if (s > r2) break;
+    }
+    next[j] = k;
+    mark[j] = j == 0 ? 1 : 0;
+}
+
+// One round of pointer doubling: every marked position marks jin[j], and
+// jout[j] = jin[jin[j]] (m where the chain ends).
+__global__ void kf_double(const uint32_t* __restrict__ jin, uint32_t* __restrict__ jout,
+                          const uint32_t* __restrict__ d_m, uint8_t* mark) {
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t m = *d_m;
+    if (j >= m) return;
+    const uint32_t k = jin[j];
+    if (k < m) {
+        if (mark[j]) mark[k] = 1;
+        jout[j] = jin[k];
+    } else {
+        jout[j] = m;
+    }
+}
+
+__global__ void kf_survive(const uint8_t* __restrict__ mark, const uint32_t* __restrict__ val,
+                           const uint32_t* __restrict__ d_m, uint8_t* __restrict__ alive) {
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < *d_m) alive[val[j]] = mark[j];
+}
+
+__global__ void kf_fill_u8(uint8_t* __restrict__ p, uint32_t n, uint8_t v) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+const int kPerm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+unsigned blocks_of(uint64_t work, unsigned per) { return (unsigned)std::max<uint64_t>(1, (work + per - 1) / per); }
+
+}  // namespace
+
+int device_sfc_filter(const float* d_points, size_t n, float r, uint32_t* d_kept, size_t* n_out, cudaStream_t st,
+                      std::string& err) {
+    if (!n_out || (n && (!d_points || !d_kept))) { err = "NULL argument"; return CAPT_E_ARG; }
+    if (!(r >= 0.f)) { err = "min_spacing must be >= 0"; return CAPT_E_RANGE; }
+    if (n >= (size_t(1) << 31)) { err = "the device filter takes fewer than 2^31 points"; return CAPT_E_ARG; }
+    *n_out = 0;
+    if (n == 0) return CAPT_OK;
+    const uint32_t un = (uint32_t)n;
+    const uint32_t nblk = blocks_of(n, kFTile);
+    // one allocation, carved into 256-byte aligned pieces
+    size_t total = 0;
+    auto take = [&](size_t bytes) { const size_t o = total; total += (bytes + 255) & ~size_t(255); return o; };
+    const size_t o_box = take(8 * 4), o_m = take(4), o_cnt = take(4), o_counts = take(4 * (size_t)nblk);
+    const size_t o_hist = take(4 * 256 * (size_t)nblk), o_sp = take(24 * n), o_alive = take(n), o_mark = take(n);
+    size_t o_w[11];
+    for (auto& o : o_w) o = take(4 * n);   // asc, klo/khi/val x 2, xs, ys, zs, next/jump
+    char* buf = nullptr;
+    cudaError_t ce = cudaMallocAsync((void**)&buf, total, st);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        err = "device allocation failed in the filter";
+        return CAPT_E_NOMEM;
+    }
+    auto U = [&](size_t o) { return reinterpret_cast<uint32_t*>(buf + o); };
+    uint32_t* box = U(o_box);
+    uint32_t* d_m = U(o_m);
+    uint32_t* d_cnt = U(o_cnt);
+    uint32_t* counts = U(o_counts);
+    uint32_t* hist = U(o_hist);
+    uint64_t* sp = reinterpret_cast<uint64_t*>(buf + o_sp);
+    uint8_t* alive = reinterpret_cast<uint8_t*>(buf + o_alive);
+    uint8_t* mark = reinterpret_cast<uint8_t*>(buf + o_mark);
+    uint32_t* asc = U(o_w[0]);
+    uint32_t* ka[2] = {U(o_w[1]), U(o_w[4])};
+    uint32_t* kb[2] = {U(o_w[2]), U(o_w[5])};
+    uint32_t* vv[2] = {U(o_w[3]), U(o_w[6])};
+    float* xs = reinterpret_cast<float*>(U(o_w[7]));
+    float* ys = reinterpret_cast<float*>(U(o_w[8]));
+    float* zs = reinterpret_cast<float*>(U(o_w[9]));
+    uint32_t* jmp[2] = {U(o_w[10]), asc};   // asc is free once the keys are made
+    int rc = CAPT_OK;
+    auto check = [&](const char* what) {
+        if (rc) return false;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) { err = std::string(what) + ": " + cudaGetErrorString(e); rc = CAPT_E_CUDA; }
+        return rc == CAPT_OK;
+    };
+    uint32_t hbox[8];
+    const uint32_t box0[8] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u, 0u, 0u};
+    const unsigned gn = blocks_of(n, kFT);
+    ce = cudaMemcpyAsync(box, box0, sizeof(box0), cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) {
+        kf_bbox<<<std::min(gn, 1024u), kFT, 0, st>>>(d_points, un, box);
+        ce = cudaMemcpyAsync(hbox, box, sizeof(hbox), cudaMemcpyDeviceToHost, st);
+    }
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) { err = std::string("filter bounding box: ") + cudaGetErrorString(ce); rc = CAPT_E_CUDA; }
+    if (!rc && hbox[6]) { err = "non-finite coordinate in points"; rc = CAPT_E_NONFINITE; }
+    if (!rc) {
+        kf_spread<<<gn, kFT, 0, st>>>(d_points, un, box, sp);
+        kf_fill_u8<<<gn, kFT, 0, st>>>(alive, un, 1);
+        check("filter setup");
+    }
+    int rounds = 0;
+    while ((1ull << rounds) < n) rounds++;
+    const float r2 = r * r;   // fl(r^2), as the host filter
+    for (int p = 0; p < 6 && !rc; p++) {
+        // survivors in ascending index order; m = their count
+        kf_flag_count<<<nblk, kFT, 0, st>>>(alive, nullptr, un, counts);
+        kf_scan<<<1, kScanThreads, 0, st>>>(counts, nblk, d_m);
+        kf_flag_compact<<<nblk, kFT, 0, st>>>(alive, nullptr, un, counts, nullptr, asc);
+        kf_keys<<<gn, kFT, 0, st>>>(asc, d_m, sp, kPerm[p][0], kPerm[p][1], kPerm[p][2], ka[0], kb[0], vv[0]);
+        // stable sort by the low word, then by the high word (4 digits each)
+        int cur = 0;
+        for (int word = 0; word < 2; word++)
+            for (int shift = 0; shift < 32; shift += 8) {
+                const uint32_t* kw = word == 0 ? ka[cur] : kb[cur];
+                const uint32_t* ko = word == 0 ? kb[cur] : ka[cur];
+                uint32_t* kw_o = word == 0 ? ka[cur ^ 1] : kb[cur ^ 1];
+                uint32_t* ko_o = word == 0 ? kb[cur ^ 1] : ka[cur ^ 1];
+                kf_hist<<<nblk, kFT, 0, st>>>(kw, d_m, shift, hist, nblk);
+                kf_scan<<<1, kScanThreads, 0, st>>>(hist, 256 * nblk, nullptr);
+                kf_scatter<<<nblk, kFT, 0, st>>>(kw, ko, vv[cur], d_m, shift, hist, nblk, kw_o, ko_o, vv[cur ^ 1]);
+                cur ^= 1;
+            }
+        const uint32_t* val = vv[cur];
+        // greedy sweep as a chain, marked by pointer doubling
+        kf_gather<<<gn, kFT, 0, st>>>(val, d_m, d_points, xs, ys, zs);
+        kf_next<<<gn, kFT, 0, st>>>(xs, ys, zs, d_m, r2, jmp[0], mark);
+        int j = 0;
+        for (int k = 0; k < rounds; k++, j ^= 1) kf_double<<<gn, kFT, 0, st>>>(jmp[j], jmp[j ^ 1], d_m, mark);
+        if (p < 5) {
+            kf_survive<<<gn, kFT, 0, st>>>(mark, val, d_m, alive);
+        } else {
+            kf_flag_count<<<nblk, kFT, 0, st>>>(mark, d_m, un, counts);
+            kf_scan<<<1, kScanThreads, 0, st>>>(counts, nblk, d_cnt);
+            kf_flag_compact<<<nblk, kFT, 0, st>>>(mark, d_m, un, counts, val, d_kept);
+        }
+        check("filter pass");
+    }
+    uint32_t kept = 0;
+    if (!rc) {
+        ce = cudaMemcpyAsync(&kept, d_cnt, 4, cudaMemcpyDeviceToHost, st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+        if (ce != cudaSuccess) { err = std::string("filter result: ") + cudaGetErrorString(ce); rc = CAPT_E_CUDA; }
+    }
+    cudaFreeAsync(buf, st);
+    if (rc) {
+        cudaStreamSynchronize(st);
+        cudaGetLastError();
+        return rc;
+    }
+    *n_out = kept;
+    return CAPT_OK;
+}
+
+}  // namespace capt

@@ -39,6 +39,15 @@ int launch_edges_per_edge(const DevArgs& t, const capt_arm& arm, const float* qa
                           const int32_t* h_ns, uint64_t E, uint8_t* valid, const capt_launch_cfg& cfg,
                           cudaStream_t st, std::string& err);
 
+// Configurations given by joint angles q [C][J]: kinematics in-kernel, one flag each.
+int launch_joint_configs(const DevArgs& t, const capt_arm& arm, const float* q, uint64_t C, uint8_t* out,
+                         const capt_launch_cfg& cfg, cudaStream_t st, std::string& err);
+
+// Alg. 2 on the device: d_points [n][3] -> kept indices (d_kept, caller-owned, n
+// entries) in the last pass's curve order, *n_out = their count.  Synchronises st.
+int device_sfc_filter(const float* d_points, size_t n, float r, uint32_t* d_kept, size_t* n_out, cudaStream_t st,
+                      std::string& err);
+
 // Number of SMs of the current device (cached per device).
 int sm_count();
 

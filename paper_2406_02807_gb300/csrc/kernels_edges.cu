@@ -278,6 +278,135 @@ __global__ void __launch_bounds__(512, 2) k_edge_single(DevArgs t, const __grid_
     }
 }
 
+// ------------------------------------------------------------------------------------
+// Configurations given by their joint angles: the kinematics of the edge kernel, one
+// lane per configuration, with the per-configuration early exit of Sec. IV-D (a hit
+// resolves its own configuration only; the others of the pass go on).
+// ------------------------------------------------------------------------------------
+struct JointScratch {
+    float4 nc[64];     // queued near spheres: centre and r^2 (< 32 left over + 32 new)
+    uint32_t ng[64];   // their configuration (lane of the pass)
+    uint32_t ghit[32]; // per configuration of the pass: 1 once it collides
+    RoundEntries re;
+};
+
+template <bool STAGE>
+__global__ void __launch_bounds__(512, 2) k_joint_configs(DevArgs t, const __grid_constant__ ArmPlan arm,
+                                                          const float* __restrict__ q, uint64_t C,
+                                                          uint8_t* __restrict__ out) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t bar;
+    const float* Ts = nullptr;
+    uint32_t off = 0;
+    if constexpr (STAGE) {
+        Ts = stage_splits(t, smem_raw, &bar);
+        off = stage_offset(t);
+    }
+    const uint32_t lane = lane_id();
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    JointScratch* ws = reinterpret_cast<JointScratch*>(smem_raw + off) + (threadIdx.x >> 5);
+    const float4 rlo = make_float4(t.lo[0], t.lo[1], t.lo[2], 0.f);
+    const float4 rhi = make_float4(t.hi[0], t.hi[1], t.hi[2], 0.f);
+    const uint64_t passes = (C + 31) / 32;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    const int J = arm.J;
+    auto run_round = [&](uint32_t n) {
+        const bool in_queue = lane < n;
+        const float4 c = in_queue ? ws->nc[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const uint32_t g = in_queue ? ws->ng[lane] : 0u;
+        sphere_round<false>(t, Ts, &ws->re, ws->ghit, c, g, in_queue, lane, lt_mask);
+    };
+    for (uint64_t pass = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); pass < passes;
+         pass += nwarps) {
+        const uint64_t k = pass * 32 + lane;
+        const bool live = k < C;
+        const float* qk = q + (live ? k : 0) * (uint64_t)J;
+        ws->ghit[lane] = 0;
+        __syncwarp();
+        bool done = !live;   // this lane's configuration needs no more spheres
+        float R[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+        float p[3] = {arm.base[0], arm.base[1], arm.base[2]};
+        uint32_t n_near = 0;
+        for (int j = 0; j < J; j++) {
+            float sj, cj;
+            sincos_cw(live ? __ldg(qk + j) : 0.f, sj, cj);
+            rotate_frame(R, arm.axis[j], sj, cj);
+            for (int i = arm.sbeg[j]; i < arm.sbeg[j + 1]; i++) {
+                const float ox = arm.off[i][0], oy = arm.off[i][1], oz = arm.off[i][2];
+                const float cx = __fadd_rn(p[0], row_dot(R, 0, ox, oy, oz));
+                const float cy = __fadd_rn(p[1], row_dot(R, 1, ox, oy, oz));
+                const float cz = __fadd_rn(p[2], row_dot(R, 2, ox, oy, oz));
+                const float r2 = arm.r2[i];
+                const bool near = !done && box_dist2(cx, cy, cz, rlo, rhi) <= r2;
+                const uint32_t mask = __ballot_sync(0xffffffffu, near);
+                if (near) {
+                    const uint32_t pos = n_near + __popc(mask & lt_mask);
+                    ws->nc[pos] = make_float4(cx, cy, cz, r2);
+                    ws->ng[pos] = lane;
+                }
+                n_near += __popc(mask);
+                if (n_near >= 32) {
+                    __syncwarp();
+                    run_round(32);
+                    const uint32_t rest = n_near - 32;
+                    float4 cc = make_float4(0.f, 0.f, 0.f, 0.f);
+                    uint32_t gg = 0;
+                    if (lane < rest) {
+                        cc = ws->nc[32 + lane];
+                        gg = ws->ng[32 + lane];
+                    }
+                    __syncwarp();
+                    if (lane < rest) {
+                        ws->nc[lane] = cc;
+                        ws->ng[lane] = gg;
+                    }
+                    __syncwarp();
+                    n_near = rest;
+                    done = done || ws->ghit[lane] != 0;
+                }
+            }
+            // every configuration of the pass resolved: the rest of the chain is moot
+            if (__all_sync(0xffffffffu, done) && n_near == 0) break;
+            const float l0 = arm.link[j][0], l1 = arm.link[j][1], l2 = arm.link[j][2];
+            const float tx = row_dot(R, 0, l0, l1, l2);
+            const float ty = row_dot(R, 1, l0, l1, l2);
+            const float tz = row_dot(R, 2, l0, l1, l2);
+            p[0] = __fadd_rn(p[0], tx);
+            p[1] = __fadd_rn(p[1], ty);
+            p[2] = __fadd_rn(p[2], tz);
+        }
+        if (n_near) {
+            __syncwarp();
+            run_round(n_near);
+        }
+        __syncwarp();
+        if (live) out[k] = (uint8_t)ws->ghit[lane];
+        __syncwarp();
+    }
+}
+
+int launch_joint_configs(const DevArgs& t, const capt_arm& arm, const float* q, uint64_t C, uint8_t* out,
+                         const capt_launch_cfg& cfg, cudaStream_t st, std::string& err) {
+    if (C == 0) return CAPT_OK;
+    const bool stage = cfg.staging == CAPT_STAGE_SMEM && t.stage_floats > 0;
+    auto fn = stage ? k_joint_configs<true> : k_joint_configs<false>;
+    const int warps = std::max(1, std::min(16, (int)cfg.warps_per_block));
+    const size_t smem = (stage ? stage_offset(t) : 0u) + sizeof(JointScratch) * (size_t)warps;
+    cudaError_t ce = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (ce != cudaSuccess) { err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)fn, warps * 32, smem);
+    occ = std::max(1, occ);
+    const uint64_t passes = (C + 31) / 32;
+    const uint64_t need = (passes + warps - 1) / warps;
+    const uint64_t blocks = std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)sm_count() * occ, need));
+    const ArmPlan plan = make_plan(arm);
+    fn<<<(unsigned)blocks, warps * 32, smem, st>>>(t, plan, q, C, out);
+    ce = cudaGetLastError();
+    if (ce != cudaSuccess) { err = std::string("joint configuration launch: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
+    return CAPT_OK;
+}
+
 size_t edge_scratch_words(size_t E) { return E + 2 + 62; }
 
 namespace {

@@ -117,3 +117,18 @@ def test_device_calls_reject_unuploaded_tree_without_gpu(capt_lib):
     assert rc == -1
     st = capt_lib.capt_stats(t)
     assert st["device"] == -1 and st["device_bytes"] == 0
+
+
+def test_joint_and_filter_calls_reject_bad_arguments_without_gpu(capt_lib):
+    """capt_query_joint_configs and sfc_filter_device check their arguments on the host
+    before any CUDA call."""
+    t = capt_lib.capt_build(W.uniform_cloud(50, 3), 0.01, 0.08)
+    L = capt_lib._load()
+    arm = capt_lib.make_arm(W.arm_7dof())
+    assert L.capt_query_joint_configs(t.h, ctypes.byref(arm), None, 10, None, None) == -8   # not uploaded
+    assert L.capt_query_joint_configs(None, ctypes.byref(arm), None, 10, None, None) == -1
+    n = ctypes.c_size_t(7)
+    assert L.sfc_filter_device(None, 10, 0.01, None, ctypes.byref(n), None) == -1      # NULL points
+    assert L.sfc_filter_device(None, 0, -1.0, None, ctypes.byref(n), None) == -2       # negative spacing
+    assert L.sfc_filter_device(None, 0, 0.01, None, ctypes.byref(n), None) == 0 and n.value == 0
+    assert L.sfc_filter_device(None, 0, 0.01, None, None, None) == -1
