@@ -131,9 +131,10 @@ def tabletop_tree(capt, with_device=True):
     tree = capt.capt_build(pts, R_MIN, R_MAX)
     st = capt.capt_stats(tree)
     dev_ms = device_build_ms(capt, pts, R_MIN, R_MAX) if with_device else float("nan")
+    dev_filt_ms = device_filter_ms(capt, raw, R_FILTER) if with_device else float("nan")
     return raw, pts, arm, tree, dict(filter_ms=round(filt_ms, 3), build_ms_1thread=round(build1_ms, 3),
                                      build_ms=round(st["build_ms"], 3), build_threads=st["build_threads"],
-                                     device_build_ms=round(dev_ms, 3),
+                                     device_build_ms=round(dev_ms, 3), device_filter_ms=round(dev_filt_ms, 3),
                                      n_points=int(st["n_points"]), n_leaves=int(st["n_leaves"]),
                                      mean_set=round(st["total_afforded"] / st["n_leaves"], 2),
                                      max_set=int(st["max_set"]))
@@ -153,6 +154,30 @@ def device_build_ms(capt, pts, r_min, r_max, reps=5):
         torch.cuda.synchronize()
         ts.append((time.perf_counter() - t0) * 1e3)
         del t
+    return statistics.median(ts)
+
+
+def host_filter_ms(capt, raw, r, reps=3):
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        capt.sfc_filter(raw, r)
+        ts.append((time.perf_counter() - t0) * 1e3)
+    return statistics.median(ts)
+
+
+def device_filter_ms(capt, raw, r, reps=5):
+    """Median wall time of sfc_filter_device (points already on the device; the call
+    returns with the kept count on the host), after one untimed call."""
+    import torch
+    d = torch.from_numpy(np.ascontiguousarray(raw, np.float32)).cuda()
+    capt.sfc_filter_device(d, r)
+    ts = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        capt.sfc_filter_device(d, r)
+        ts.append((time.perf_counter() - t0) * 1e3)
     return statistics.median(ts)
 
 
@@ -441,6 +466,8 @@ def extra_workloads(capt, torch, dev, stream, pts, arm, args):
     res["uniform2k"] = {"spheres": 100_000, "ms": ms, "sphere_queries_per_s": 1e5 / (ms / 1e3)}
     # room: 200,000 points, 4,194,304 spheres
     pr = W.room_cloud(1004)
+    res["room_filter_2cm"] = {"points": len(pr), "host_ms": host_filter_ms(capt, pr, 0.02),
+                              "device_ms": device_filter_ms(capt, pr, 0.02, reps=3)}
     t0 = time.perf_counter()
     tr = capt.capt_build(pr, 0.02, 0.10)
     bms = (time.perf_counter() - t0) * 1e3

@@ -53,6 +53,26 @@ def test_joint_configs_every_launch_cfg(scene, orc, capt_lib, torch_, warps, sta
     assert np.array_equal(f, ref)
 
 
+def _long_arm():
+    """16 joints (the most an arm may have), one sphere per link."""
+    from types import SimpleNamespace
+    J = 16
+    return SimpleNamespace(base=[-0.05, 0.0, 0.06], axis=[2 if j % 2 == 0 else 1 for j in range(J)],
+                           link=[[0.0, 0.0, 0.05]] * J, sphere_link=list(range(J)),
+                           sphere_offset=[[0.0, 0.0, 0.025]] * J, sphere_radius=[0.03] * J, n_joints=J, n_spheres=J)
+
+
+def test_joint_configs_long_arm(scene, orc, capt_lib, torch_):
+    """A 16-joint arm with one sphere per link, against the oracle's kinematics and
+    brute force."""
+    arm = _long_arm()
+    q = W.random_configs(3000, 17, n_joints=16)
+    f = capt_lib.capt_query_joint_configs(scene["tree"], arm, _q(torch_, q)).cpu().numpy()
+    ref = orc.brute_config_flags(scene["pts"], orc.fk32(arm, q), np.float32(arm.sphere_radius))
+    assert np.array_equal(f, ref)
+    assert 0.05 < ref.mean() < 0.95
+
+
 @pytest.mark.parametrize("C", [1, 31, 32, 33, 95, 1000])
 def test_joint_configs_ragged_counts(scene, orc, capt_lib, torch_, C):
     q = W.random_configs(C, 7, first=123)
