@@ -145,6 +145,10 @@ const char* capt_last_error(void);
  *          then all z quads; unused slots hold +inf
  *   ids    uint32[4 * total_blocks] point index per slot (0xffffffff in unused slots)
  *   cloud  float[n][3] the input points (for the clearance gradient)
+ *   cbox   float[ceil(total_blocks / 8)][8]: per chunk of 8 consecutive blocks the
+ *          FP32 min / max of its finite coordinates {lo.xyz, 0, hi.xyz, 0}; the scan
+ *          skips a chunk whose box the sphere does not reach (exact: a box holding p
+ *          is never farther than p)
  * Calling it again re-uploads.  Errors: CAPT_E_ARG, CAPT_E_CUDA, CAPT_E_NOMEM. */
 int capt_upload(capt_tree* t, int device, void* stream);
 
@@ -194,11 +198,15 @@ int capt_query_configs_host(capt_tree* t, const float* h_centers, const float* h
                             uint8_t* h_flags, void* stream);
 
 /* Algorithmic work of capt_query_configs, counted sequentially per configuration (for
- * roofline accounting): d_counts device uint64[4] receives += [spheres examined (up to
+ * roofline accounting): d_counts device uint64[6] receives += [spheres examined (up to
  * and including each configuration's first hit), spheres within reach of the cloud's
  * bounding box (these descend), spheres passing their leaf's box test (Alg. 3),
- * affordance points scanned (in stored order, up to and including the first hit)].
- * The caller zeroes d_counts.  Errors as capt_query_configs. */
+ * affordance points scanned by Alg. 3 alone (in stored order, up to and including the
+ * first hit), chunk boxes tested, points scanned in the chunks whose box the sphere
+ * reaches (up to and including the first hit)].  The query kernels do the work of
+ * entries 0-2, 4 and 5; entry 3 is the plain method's scan for comparison.  The two
+ * walks must find the same hits: a disagreement latches CAPT_E_BOUNDS in the device
+ * status word.  The caller zeroes d_counts.  Errors as capt_query_configs. */
 int capt_count_config_work(const capt_tree* t, const float* d_centers, const float* d_radii, size_t C, int S,
                            uint64_t* d_counts, void* stream);
 

@@ -319,7 +319,7 @@ def capt_query_configs_host(tree: CaptTree, centers, radii, flags=None, stream=N
 def capt_count_config_work(tree: CaptTree, centers, radii, stream=None):
     import torch
     Cn, S = centers.shape[0], centers.shape[1]
-    counts = torch.zeros(4, dtype=torch.int64, device=centers.device)
+    counts = torch.zeros(6, dtype=torch.int64, device=centers.device)
     _check(_load().capt_count_config_work(tree.h, _dev(centers, torch.float32, "centers"),
                                           _dev(radii, torch.float32, "radii"), Cn, S,
                                           _dev(counts, torch.int64, "counts"), _stream(stream)),

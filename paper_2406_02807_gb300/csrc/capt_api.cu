@@ -71,6 +71,7 @@ struct capt_tree {
     void* d_blocks = nullptr;
     void* d_ids = nullptr;
     void* d_cloud = nullptr;
+    void* d_cbox = nullptr;      // chunk boxes (chunk_count(total_blocks) x 8 floats)
     int* d_status = nullptr;
     uint64_t total_blocks = 0;
     size_t dev_bytes = 0;
@@ -120,6 +121,7 @@ struct capt_tree {
         a.blocks = static_cast<const float*>(d_blocks);
         a.plane = total_blocks > 0 ? total_blocks : 1;
         a.ids = static_cast<const uint32_t*>(d_ids);
+        a.cbox = static_cast<const float*>(d_cbox);
         a.cloud = static_cast<const float*>(d_cloud);
         a.status = d_status;
         a.N = (uint32_t)h.N;
@@ -136,14 +138,14 @@ struct capt_tree {
     void free_device() {
         if (device < 0) return;
         DeviceGuard g(device);
-        for (void* p : {d_T, d_leaves, d_blocks, d_ids, d_cloud, (void*)d_status, (void*)d_pipe_c[0], (void*)d_pipe_c[1],
+        for (void* p : {d_T, d_leaves, d_blocks, d_ids, d_cloud, d_cbox, (void*)d_status, (void*)d_pipe_c[0], (void*)d_pipe_c[1],
                         (void*)d_pipe_f[0], (void*)d_pipe_f[1], (void*)d_edge_scratch, (void*)d_zc_flags, d_Tplain,
                         d_set_idx, d_set_begin, d_pruned})
             if (p) cudaFree(p);
         for (auto& e : pipe_ev)
             if (e) cudaEventDestroy(e);
         if (pipe_stream) cudaStreamDestroy(pipe_stream);
-        d_T = d_leaves = d_blocks = d_ids = d_cloud = nullptr;
+        d_T = d_leaves = d_blocks = d_ids = d_cloud = d_cbox = nullptr;
         d_Tplain = d_set_idx = d_set_begin = d_pruned = nullptr;
         d_status = nullptr;
         d_pipe_c[0] = d_pipe_c[1] = nullptr;
@@ -317,14 +319,24 @@ int capt_build_device(const float* d_points, size_t n, float r_min, float r_max,
         return fail(rc, err);
     }
     int* status = nullptr;
+    void* cbox = nullptr;
+    const size_t sz_cbox = capt::chunk_count(d.total_blocks) * 8 * sizeof(float);
     cudaError_t e = cudaMalloc((void**)&status, 256);
     if (e == cudaSuccess) e = cudaMemset(status, 0, 256);
+    if (e == cudaSuccess) e = cudaMalloc(&cbox, sz_cbox);
+    if (e == cudaSuccess) {
+        const cudaStream_t st = static_cast<cudaStream_t>(stream);
+        if (capt::launch_chunk_boxes(d.blocks, d.total_blocks, static_cast<float*>(cbox), st, err) != CAPT_OK)
+            e = cudaErrorLaunchFailure;
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         if (status) cudaFree(status);
+        if (cbox) cudaFree(cbox);
         d.release();
         delete t;
-        return cuda_fail(e, "status word");
+        return cuda_fail(e, "status word and chunk boxes");
     }
     auto& h = t->h;
     h.n = n;
@@ -339,6 +351,7 @@ int capt_build_device(const float* d_points, size_t n, float r_min, float r_max,
     t->d_blocks = d.blocks;
     t->d_ids = d.ids;
     t->d_cloud = d.cloud;
+    t->d_cbox = cbox;
     t->d_status = status;
     t->d_Tplain = d.Tplain;
     t->d_set_idx = d.set_idx;
@@ -355,7 +368,7 @@ int capt_build_device(const float* d_points, size_t n, float r_min, float r_max,
         t->box_lo[k] = d.box_lo[k];
         t->box_hi[k] = d.box_hi[k];
     }
-    t->dev_bytes = d.bytes + 256;
+    t->dev_bytes = d.bytes + sz_cbox + 256;
     t->host_pending = true;
     h.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     *out = t;
@@ -473,9 +486,11 @@ int capt_upload(capt_tree* t, int device, void* stream) {
         return CAPT_OK;
     };
     int rc;
+    const size_t sz_cbox = capt::chunk_count(lay.total_blocks) * 8 * sizeof(float);
     if ((rc = alloc(&t->d_T, sz_T, "T")) || (rc = alloc(&t->d_leaves, sz_leaves, "leaves")) ||
         (rc = alloc(&t->d_blocks, sz_blocks, "blocks")) || (rc = alloc(&t->d_ids, sz_ids, "ids")) ||
-        (rc = alloc(&t->d_cloud, sz_cloud, "cloud")) || (rc = alloc((void**)&t->d_status, 256, "status")))
+        (rc = alloc(&t->d_cloud, sz_cloud, "cloud")) || (rc = alloc(&t->d_cbox, sz_cbox, "chunk boxes")) ||
+        (rc = alloc((void**)&t->d_status, 256, "status")))
         return rc;
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMemcpyAsync(t->d_T, bs.data.data(), sz_T, cudaMemcpyHostToDevice, st);
@@ -485,6 +500,12 @@ int capt_upload(capt_tree* t, int device, void* stream) {
     if (e == cudaSuccess && !h.pts.empty())
         e = cudaMemcpyAsync(t->d_cloud, h.pts.data(), h.pts.size() * sizeof(float), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(t->d_status, 0, 256, st);
+    if (e == cudaSuccess) {
+        std::string cerr;
+        if (capt::launch_chunk_boxes(static_cast<const float*>(t->d_blocks), lay.total_blocks,
+                                     static_cast<float*>(t->d_cbox), st, cerr) != CAPT_OK)
+            e = cudaErrorLaunchFailure;
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // the staging vectors die here
     if (e != cudaSuccess) {
         t->free_device();
@@ -506,7 +527,7 @@ int capt_upload(capt_tree* t, int device, void* stream) {
     t->Ks = bs.Ks;
     t->tail_staged = bs.tail_staged;
     t->stage_floats = bs.stage_floats;
-    t->dev_bytes = sz_T + sz_leaves + sz_blocks + sz_ids + sz_cloud + 256;
+    t->dev_bytes = sz_T + sz_leaves + sz_blocks + sz_ids + sz_cloud + sz_cbox + 256;
     return CAPT_OK;
 }
 

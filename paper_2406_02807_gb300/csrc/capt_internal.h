@@ -55,6 +55,13 @@ struct BlockedSplits {
 void blocked_shape(int L, BlockedSplits& out);   // every field but data
 void blocked_splits(const HostTree& t, BlockedSplits& out);
 
+// Blocks per chunk of the point buffer: chunk k holds blocks [8k, 8k + 8) (a chunk may
+// straddle two sets); its box is the FP32 min / max of the finite coordinates in it.
+constexpr uint32_t kChunkBlocks = 8;
+inline uint64_t chunk_count(uint64_t total_blocks) {
+    return ((total_blocks > 0 ? total_blocks : 1) + kChunkBlocks - 1) / kChunkBlocks;
+}
+
 // Kernel view of an uploaded tree (raw device pointers, passed by value).
 struct DevArgs {
     const float* T = nullptr;        // blocked split array (BlockedSplits::data)
@@ -65,6 +72,7 @@ struct DevArgs {
     const float* blocks = nullptr;   // 4-point blocks in three planes of float4 (x, y, z quads)
     uint64_t plane = 1;              // blocks per plane (float4 stride between the planes)
     const uint32_t* ids = nullptr;   // 4 per block
+    const float* cbox = nullptr;     // chunk boxes: 8 floats each {lo.xyz, 0, hi.xyz, 0}
     const float* cloud = nullptr;    // [n][3]
     int* status = nullptr;           // latched device status bits
     uint32_t N = 1;

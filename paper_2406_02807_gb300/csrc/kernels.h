@@ -19,6 +19,9 @@ int launch_query(const DevArgs& t, int mode, const float* centers, const float* 
 int launch_count_configs(const DevArgs& t, const float* centers, const float* radii, uint64_t C, int S,
                          uint64_t* counts, cudaStream_t st, std::string& err);
 
+// Boxes of the chunks of kChunkBlocks blocks (cbox: 8 floats per chunk, chunk_count).
+int launch_chunk_boxes(const float* blocks, uint64_t total_blocks, float* cbox, cudaStream_t st, std::string& err);
+
 int launch_leaves(const DevArgs& t, const float* centers, uint64_t m, uint32_t* leaves, cudaStream_t st,
                   std::string& err);
 

@@ -327,11 +327,14 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs(DevArgs t, cons
 // root box test; a sphere within reach of the cloud's box descends and gets the leaf box
 // test of Alg. 3; a sphere passing that scans its set in stored order up to its first hit.
 // counts += [spheres examined, spheres near the cloud box, spheres passing the leaf box,
-// points scanned].
+// points scanned (Alg. 3 alone), chunk boxes tested, points scanned in the chunks whose
+// box the sphere reaches (up to the first hit)].  The first four are the plain method's
+// work; the query kernels do the first three, then the last two instead of the fourth.
 __global__ void k_count_configs(DevArgs t, const float* __restrict__ centers, const float* __restrict__ radii,
                                 uint64_t C, int S, unsigned long long* counts) {
     const uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long nsph = 0, nnear = 0, npass = 0, npts = 0;
+    unsigned long long nsph = 0, nnear = 0, npass = 0, npts = 0, nbox = 0, ncpts = 0;
+    const float4* cbox = reinterpret_cast<const float4*>(t.cbox);
     const float4 rlo = make_float4(t.lo[0], t.lo[1], t.lo[2], 0.f);
     const float4 rhi = make_float4(t.hi[0], t.hi[1], t.hi[2], 0.f);
     if (c < C) {
@@ -348,13 +351,28 @@ __global__ void k_count_configs(DevArgs t, const float* __restrict__ centers, co
             if (cnt == 0 || !(box_dist2(x[0], x[1], x[2], a, b) <= r2)) continue;
             npass++;
             const uint32_t b0 = __float_as_uint(a.w);
+            const size_t pl = 4 * (size_t)t.plane;
             bool hit = false;
             for (uint32_t j = 0; j < cnt && !hit; j++) {
                 const float* bx = t.blocks + 4 * (size_t)(b0 + j / 4) + (j & 3u);
-                const size_t pl = 4 * (size_t)t.plane;
                 npts++;
                 hit = sq_dist(x[0], x[1], x[2], bx[0], bx[pl], bx[2 * pl]) <= r2;
             }
+            // the same set walked chunk by chunk, points only in chunks whose box passes
+            const uint32_t b1 = b0 + (cnt + 3u) / 4u;
+            bool chit = false;
+            for (uint32_t k = b0 / kChunkBlocks; k <= (b1 - 1u) / kChunkBlocks && !chit; k++) {
+                nbox++;
+                if (!(box_dist2(x[0], x[1], x[2], cbox[2 * k], cbox[2 * k + 1]) <= r2)) continue;
+                const uint32_t j0 = max(b0, k * kChunkBlocks) * 4u - 4u * b0;
+                const uint32_t j1 = min(b1 * 4u, (k + 1u) * kChunkBlocks * 4u) - 4u * b0;
+                for (uint32_t j = j0; j < j1 && j < cnt && !chit; j++) {
+                    const float* bx = t.blocks + 4 * (size_t)(b0 + j / 4) + (j & 3u);
+                    ncpts++;
+                    chit = sq_dist(x[0], x[1], x[2], bx[0], bx[pl], bx[2 * pl]) <= r2;
+                }
+            }
+            if (chit != hit) atomicOr(t.status, kStatusBounds);   // the two walks must agree
             if (hit) break;
         }
     }
@@ -363,13 +381,40 @@ __global__ void k_count_configs(DevArgs t, const float* __restrict__ centers, co
         nnear += __shfl_xor_sync(0xffffffffu, nnear, o);
         npass += __shfl_xor_sync(0xffffffffu, npass, o);
         npts += __shfl_xor_sync(0xffffffffu, npts, o);
+        nbox += __shfl_xor_sync(0xffffffffu, nbox, o);
+        ncpts += __shfl_xor_sync(0xffffffffu, ncpts, o);
     }
     if ((threadIdx.x & 31) == 0 && nsph) {
         atomicAdd(counts, nsph);
         atomicAdd(counts + 1, nnear);
         atomicAdd(counts + 2, npass);
         atomicAdd(counts + 3, npts);
+        atomicAdd(counts + 4, nbox);
+        atomicAdd(counts + 5, ncpts);
     }
+}
+
+// Chunk boxes: chunk k covers blocks [8k, 8k + 8); its box is the min / max of the
+// finite coordinates there (unused slots hold +inf and are left out; a chunk with none
+// gets the empty box lo = +inf, hi = -inf, which no sphere reaches).
+__global__ void k_chunk_boxes(const float4* __restrict__ blocks, uint64_t plane, uint64_t total_blocks,
+                              uint64_t n_chunks, float4* __restrict__ cbox) {
+    const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_chunks) return;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    const uint64_t b_end = min(total_blocks, (k + 1) * kChunkBlocks);
+    for (uint64_t b = k * kChunkBlocks; b < b_end; b++)
+        for (int d = 0; d < 3; d++) {
+            const float4 q = blocks[d * plane + b];
+            const float v[4] = {q.x, q.y, q.z, q.w};
+            for (int u = 0; u < 4; u++)
+                if (isfinite(v[u])) {
+                    lo[d] = fminf(lo[d], v[u]);
+                    hi[d] = fmaxf(hi[d], v[u]);
+                }
+        }
+    cbox[2 * k] = make_float4(lo[0], lo[1], lo[2], 0.f);
+    cbox[2 * k + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
 }
 
 __global__ void k_leaves(DevArgs t, const float* __restrict__ centers, uint64_t m, uint32_t* __restrict__ leaves) {
@@ -505,6 +550,17 @@ int launch_count_configs(const DevArgs& t, const float* centers, const float* ra
         t, centers, radii, C, S, reinterpret_cast<unsigned long long*>(counts));
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) { err = std::string("count launch: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
+    return CAPT_OK;
+}
+
+int launch_chunk_boxes(const float* blocks, uint64_t total_blocks, float* cbox, cudaStream_t st, std::string& err) {
+    const uint64_t n = chunk_count(total_blocks);
+    const uint64_t plane = total_blocks > 0 ? total_blocks : 1;
+    const unsigned threads = 256;
+    k_chunk_boxes<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(
+        reinterpret_cast<const float4*>(blocks), plane, total_blocks, n, reinterpret_cast<float4*>(cbox));
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) { err = std::string("chunk box launch: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
     return CAPT_OK;
 }
 

@@ -189,6 +189,81 @@ def test_work_counters_match_oracle(tabletop, capt_lib, torch_):
     assert g[1] <= near.sum() and g[1] >= near[flags == 0].sum()
 
 
+def _chunk_model_counts(ex, pts, cen, r, L):
+    """Chunked-scan work counted sequentially in FP32 from the oracle's tree: the block
+    layout (each set from a 4-point block boundary, sets in leaf order), boxes of chunks
+    of 8 consecutive blocks, then per configuration, sphere by sphere until the first
+    hit: chunk boxes tested and points scanned in the chunks whose box the sphere
+    reaches."""
+    T, sb, si, aabb = ex["T"], ex["set_begin"].astype(np.int64), ex["set_idx"], ex["aabb"].reshape(-1, 6)
+    N = len(sb) - 1
+    cnt = np.diff(sb)
+    fb = np.concatenate([[0], np.cumsum((cnt + 3) // 4)]).astype(np.int64)
+    slots = np.full((int(fb[-1]) * 4 + 32, 3), np.inf, np.float32)
+    for leaf in range(N):
+        if cnt[leaf]:
+            slots[fb[leaf] * 4: fb[leaf] * 4 + cnt[leaf]] = pts[si[sb[leaf]:sb[leaf + 1]]]
+    nch = (max(int(fb[-1]), 1) + 7) // 8
+    ch = slots[: nch * 32].reshape(nch, 32, 3)
+    fin = np.isfinite(ch)
+    clo, chi = np.where(fin, ch, np.inf).min(1), np.where(fin, ch, -np.inf).max(1)
+    lo, hi = pts.min(0), pts.max(0)
+
+    def bd2(x, a, b):
+        d = (x - np.clip(x, a, b)).astype(np.float32)
+        q = d * d
+        return (q[0] + q[1]) + q[2]
+
+    def d2(x, P):
+        d = (x[None, :] - P).astype(np.float32)
+        q = d * d
+        return (q[:, 0] + q[:, 1]) + q[:, 2]
+
+    nbox = ncpts = 0
+    r2 = (r * r).astype(np.float32)
+    for c in range(cen.shape[0]):
+        for s in range(cen.shape[1]):
+            x = cen[c, s]
+            if not bd2(x, lo, hi) <= r2[s]:
+                continue
+            i = 0
+            for l in range(L):
+                i = 2 * i + 1 + int(x[l % 3] > T[i])
+            leaf = i - (N - 1)
+            if cnt[leaf] == 0 or not bd2(x, aabb[leaf, :3], aabb[leaf, 3:]) <= r2[s]:
+                continue
+            b0, b1 = int(fb[leaf]), int(fb[leaf + 1])
+            hit = False
+            for k in range(b0 // 8, (b1 - 1) // 8 + 1):
+                nbox += 1
+                if not bd2(x, clo[k], chi[k]) <= r2[s]:
+                    continue
+                j0, j1 = max(b0, 8 * k) * 4, min(b1 * 4, (k + 1) * 32, b0 * 4 + int(cnt[leaf]))
+                h = np.nonzero(d2(x, slots[j0:j1]) <= r2[s])[0]
+                if len(h):
+                    ncpts += int(h[0]) + 1
+                    hit = True
+                    break
+                ncpts += j1 - j0
+            if hit:
+                break
+    return nbox, ncpts
+
+
+def test_chunk_work_counters_match_model(tabletop, capt_lib, torch_):
+    """The chunk counters of capt_count_config_work equal a sequential FP32 count over
+    the oracle's tree, and the chunked walk finds exactly the plain walk's hits (the
+    device status stays clean)."""
+    cen = _configs(tabletop, 300, first=4321)
+    r = tabletop["arm"].sphere_radius
+    g = capt_lib.capt_count_config_work(tabletop["tree"], _cuda(torch_, cen), _cuda(torch_, r)).cpu().numpy()
+    ex = tabletop["oracle_tree"].export()
+    L = capt_lib.capt_stats(tabletop["tree"])["depth"]
+    assert (int(g[4]), int(g[5])) == _chunk_model_counts(ex, tabletop["pts"], cen, r, L)
+    assert g[5] < g[3] and g[4] > 0
+    assert capt_lib.capt_device_status(tabletop["tree"]) == 0
+
+
 def test_host_buffer_pipeline_matches_device_path(tabletop, capt_lib, torch_):
     cen = _configs(tabletop, 140_000, first=5)                   # three chunks, ragged last
     r = tabletop["arm"].sphere_radius
