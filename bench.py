@@ -38,7 +38,17 @@ R_MIN, R_MAX, R_FILTER = 0.02, 0.08, 0.01
 SM_MAX_MHZ = 2070.0
 # DRAM bytes (read + write) per launch of the configuration-query kernel from an ncu
 # capture, keyed by the hash of the kernel source it was taken on (null when stale).
-TRAFFIC = {"728b38eea5f8fb3a": 777285376 + 4831488}   # profiles/k_configs_tabletop_1M.md
+TRAFFIC = {"eb42a554c3597632": 778528256 + 4305152}   # profiles/k_configs_tabletop_1M.md
+HBM_FALLBACK_GBS = 6800.0   # used only when MEASURED_PEAKS.json is absent
+
+
+def hbm_peak():
+    """Measured copy bandwidth of this machine's GB300 (GB/s) and where it came from."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, ValueError, KeyError):
+        return HBM_FALLBACK_GBS, "fallback (no MEASURED_PEAKS.json)"
 
 
 def parse():
@@ -296,10 +306,16 @@ def main():
     tuned, tuned_ms = capt.capt_autotune_configs(tree, cen, r, flags)
     counts = capt.capt_count_config_work(tree, cen, r).cpu().numpy().astype(np.int64)
     L = capt.capt_stats(tree)["depth"]
-    # FP32 operations of the method per launch: a root box test for every examined
-    # sphere (15), a descent and leaf box test for the near ones (L + 15), 9 per point
-    ops_per_launch = int(counts[0]) * 15 + int(counts[1]) * (L + 15) + int(counts[3]) * 9
-    bytes_per_launch = int(counts[0]) * 12 + int(counts[1]) * (32 + 4 * L) + int(counts[3]) * 12
+    # FP32 operations per launch of the method as the kernel runs it: a root box test
+    # for every examined sphere (15), a descent and leaf box test for the near ones
+    # (L + 15), a box test per chunk walked (15) and 9 per point scanned in the chunks
+    # that pass; on-chip bytes likewise (12 per centre, 32 per leaf record, 4 per split,
+    # 32 per chunk box, 12 per point)
+    ops_per_launch = int(counts[0]) * 15 + int(counts[1]) * (L + 15) + int(counts[4]) * 15 + int(counts[5]) * 9
+    bytes_per_launch = (int(counts[0]) * 12 + int(counts[1]) * (32 + 4 * L) + int(counts[4]) * 32 +
+                        int(counts[5]) * 12)
+    # DRAM bytes the step must move: every centre once, the flags, the radii
+    hbm_bytes = C * SPHERES * 12 + C + SPHERES * 4
 
     def step():
         capt.capt_query_configs(tree, cen, r, flags)
@@ -329,6 +345,8 @@ def main():
         sms = props.multi_processor_count
         peak_tops = sms * 128 * SM_MAX_MHZ * 1e6 / 1e12
         achieved = ops_per_launch / (ms / 1e3) / 1e12
+        peak_gbs, peak_src = hbm_peak()
+        achieved_gbs = hbm_bytes / (ms / 1e3) / 1e9
         h = src_hash("kernels_query.cu", "scan.cuh", "device_common.cuh", "capt_internal.h")
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -342,12 +360,21 @@ def main():
             "ns_per_sphere_query": 1e9 / value * world,
             "configs_per_s": world * C / (ms / 1e3),
             "collision_fraction": collide,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "TFLOP/s",
-                         "frac": achieved / peak_tops, "traffic": TRAFFIC.get(h),
-                         "peak_basis": f"{sms} SMs x 128 FP32 lanes x {SM_MAX_MHZ:.0f} MHz (no FMA on this path)",
+            # the binding floor is HBM: reading the centres once takes longer than the
+            # method's FP32 work at the ALU peak
+            "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak_gbs, "unit": "GB/s",
+                         "frac": achieved_gbs / peak_gbs, "traffic": TRAFFIC.get(h),
+                         "peak_basis": peak_src, "algorithmic_bytes_per_launch": hbm_bytes,
+                         "hbm_floor_ms": hbm_bytes / (peak_gbs * 1e9) * 1e3,
+                         "alu": {"achieved": achieved, "peak": peak_tops, "unit": "TFLOP/s",
+                                 "frac": achieved / peak_tops, "floor_ms": ops_per_launch / (peak_tops * 1e12) * 1e3,
+                                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x {SM_MAX_MHZ:.0f} MHz "
+                                               f"(no FMA on this path)"},
                          "ops_per_launch": ops_per_launch,
                          "work": {"spheres_examined": int(counts[0]), "near_cloud_box": int(counts[1]),
-                                  "leaf_box_pass": int(counts[2]), "points_scanned": int(counts[3]), "depth": L},
+                                  "leaf_box_pass": int(counts[2]), "chunk_boxes": int(counts[4]),
+                                  "points_scanned": int(counts[5]), "points_scanned_alg3_alone": int(counts[3]),
+                                  "depth": L},
                          "l1_bytes_per_launch": bytes_per_launch,
                          "l1_frac": bytes_per_launch / (ms / 1e3) / (sms * 128 * SM_MAX_MHZ * 1e6)},
             "host": host,
@@ -462,8 +489,9 @@ def extra_workloads(capt, torch, dev, stream, pts, arm, args):
     capt.capt_upload(tu, dev.index)
     dc, dr = torch.from_numpy(cu).to(dev), torch.from_numpy(ru).to(dev)
     fl = torch.empty(100_000, dtype=torch.uint8, device=dev)
+    ucfg, _ = capt.capt_autotune_spheres(tu, dc, dr, fl)
     ms = time_events(torch, lambda: capt.capt_query_spheres(tu, dc, dr, fl), 20, stream)
-    res["uniform2k"] = {"spheres": 100_000, "ms": ms, "sphere_queries_per_s": 1e5 / (ms / 1e3)}
+    res["uniform2k"] = {"spheres": 100_000, "ms": ms, "sphere_queries_per_s": 1e5 / (ms / 1e3), "launch_cfg": ucfg}
     # room: 200,000 points, 4,194,304 spheres
     pr = W.room_cloud(1004)
     res["room_filter_2cm"] = {"points": len(pr), "host_ms": host_filter_ms(capt, pr, 0.02),
@@ -476,9 +504,11 @@ def extra_workloads(capt, torch, dev, stream, pts, arm, args):
     cr, rr = W.room_queries(1 << 22, 1004)
     dc, dr = torch.from_numpy(cr).to(dev), torch.from_numpy(rr).to(dev)
     fl = torch.empty(1 << 22, dtype=torch.uint8, device=dev)
+    rcfg, _ = capt.capt_autotune_spheres(tr, dc, dr, fl)
     ms = time_events(torch, lambda: capt.capt_query_spheres(tr, dc, dr, fl), 10, stream)
     res["room200k"] = {"spheres": 1 << 22, "ms": ms, "sphere_queries_per_s": (1 << 22) / (ms / 1e3),
-                       "build_ms": bms, "device_build_ms": device_build_ms(capt, pr, 0.02, 0.10, reps=3), "tree_device_bytes": int(st["device_bytes"]),
+                       "build_ms": bms, "device_build_ms": device_build_ms(capt, pr, 0.02, 0.10, reps=3),
+                       "launch_cfg": rcfg, "tree_device_bytes": int(st["device_bytes"]),
                        "total_afforded": int(st["total_afforded"]), "max_set": int(st["max_set"])}
     return res
 

@@ -231,13 +231,17 @@ enum { CAPT_KERNEL_SPHERES = 0, CAPT_KERNEL_CONFIGS = 1, CAPT_KERNEL_EDGES = 2, 
 typedef struct capt_launch_cfg {
     int32_t warps_per_block;   /* 1..16 */
     int32_t spheres_per_lane;  /* tile size.  Spheres: 1, 2, 4 or 8 spheres per lane
-                                  (32 x that per warp tile).  Configurations: 2, 4 or 8,
-                                  for 4, 8 or 16 configurations per warp tile.  Edges
-                                  and joint-angle configurations: not used (one
-                                  configuration per lane). */
+                                  (32 x that per warp tile).  Configurations: 2, 4, 8
+                                  or 16, for 4, 8, 16 or 32 configurations per warp
+                                  tile.  Edges and joint-angle configurations: not
+                                  used (one configuration per lane). */
     int32_t staging;           /* CAPT_STAGE_* */
     int32_t chunk;             /* edges: configurations per work item (1..1024, rounded
-                                  up to a multiple of 32) */
+                                  up to a multiple of 32).  Spheres and configurations:
+                                  the affordance scan, 0 = whole sets (Alg. 3), 1 = by
+                                  chunks of 32 points, only those whose box the sphere
+                                  reaches (pays when a set's consecutive points are close
+                                  in space, as after the filter) */
 } capt_launch_cfg;
 
 /* Set / get the launch configuration used for `kernel` on this tree.
@@ -250,6 +254,10 @@ int capt_get_launch_cfg(const capt_tree* t, int kernel, capt_launch_cfg* cfg);
  * d_flags is overwritten.  best_ms may be NULL.  Synchronises `stream`. */
 int capt_autotune_configs(capt_tree* t, const float* d_centers, const float* d_radii, size_t C, int S,
                           uint8_t* d_flags, void* stream, capt_launch_cfg* best, float* best_ms);
+
+/* The same for the sphere-query kernel (capt_query_spheres' arguments). */
+int capt_autotune_spheres(capt_tree* t, const float* d_centers, const float* d_radii, size_t m, uint8_t* d_flags,
+                          void* stream, capt_launch_cfg* best, float* best_ms);
 
 /* ---------------------------------------------------------------------------------
  * Batched edge validation

@@ -23,7 +23,7 @@ __all__ = [
     "capt_edge_plan_launch", "capt_edge_plan_info", "capt_edge_plan_free", "capt_clearance_fwd",
     "capt_clearance_bwd", "capt_free", "capt_last_error", "make_arm", "CaptTree", "EdgePlan",
     "capt_validate_edges_static", "CAPT_STATIC_MAX_EDGES", "capt_build_device", "capt_query_joint_configs",
-    "capt_autotune_joint_configs", "CAPT_KERNEL_JOINTS", "sfc_filter_device", "STATUS", "CAPT_STAGE_GLOBAL", "CAPT_STAGE_SMEM", "CAPT_KERNEL_SPHERES", "CAPT_KERNEL_CONFIGS",
+    "capt_autotune_joint_configs", "CAPT_KERNEL_JOINTS", "sfc_filter_device", "capt_autotune_spheres", "STATUS", "CAPT_STAGE_GLOBAL", "CAPT_STAGE_SMEM", "CAPT_KERNEL_SPHERES", "CAPT_KERNEL_CONFIGS",
     "CAPT_KERNEL_EDGES", "CAPT_KERNEL_CLEARANCE", "CAPT_EDGES_PERSISTENT", "CAPT_EDGES_PER_EDGE",
     "EXPORTED_SYMBOLS",
 ]
@@ -43,7 +43,7 @@ EXPORTED_SYMBOLS = [
     "capt_autotune_configs", "capt_validate_edges", "capt_edge_plan_create", "capt_edge_plan_launch",
     "capt_edge_plan_info", "capt_edge_plan_free", "capt_clearance_fwd", "capt_clearance_bwd",
     "capt_validate_edges_static", "capt_build_device", "capt_query_joint_configs", "capt_autotune_joint_configs",
-    "sfc_filter_device",
+    "sfc_filter_device", "capt_autotune_spheres",
 ]
 CAPT_STATIC_MAX_EDGES = 65536
 
@@ -103,6 +103,7 @@ def _load():
         "capt_set_launch_cfg": [P, I, C.POINTER(_LaunchCfg)],
         "capt_get_launch_cfg": [P, I, C.POINTER(_LaunchCfg)],
         "capt_autotune_configs": [P, P, P, SZ, I, P, P, C.POINTER(_LaunchCfg), C.POINTER(F)],
+        "capt_autotune_spheres": [P, P, P, SZ, P, P, C.POINTER(_LaunchCfg), C.POINTER(F)],
         "capt_validate_edges": [P, C.POINTER(_Arm), P, P, P, SZ, P, I, P],
         "capt_validate_edges_static": [P, C.POINTER(_Arm), P, P, P, SZ, P, P],
         "capt_query_joint_configs": [P, C.POINTER(_Arm), P, SZ, P, P],
@@ -365,6 +366,19 @@ def capt_autotune_configs(tree: CaptTree, centers, radii, flags=None, stream=Non
                                          _dev(radii, torch.float32, "radii"), Cn, S,
                                          _dev(flags, torch.uint8, "flags"), _stream(stream), C.byref(c),
                                          C.byref(ms)), "capt_autotune_configs")
+    return {k: getattr(c, k) for k, _ in _LaunchCfg._fields_}, ms.value
+
+
+def capt_autotune_spheres(tree: CaptTree, centers, radii, flags=None, stream=None):
+    import torch
+    m = centers.shape[0]
+    if flags is None:
+        flags = torch.empty(m, dtype=torch.uint8, device=centers.device)
+    c = _LaunchCfg()
+    ms = C.c_float()
+    _check(_load().capt_autotune_spheres(tree.h, _dev(centers, torch.float32, "centers"),
+                                         _dev(radii, torch.float32, "radii"), m, _dev(flags, torch.uint8, "flags"),
+                                         _stream(stream), C.byref(c), C.byref(ms)), "capt_autotune_spheres")
     return {k: getattr(c, k) for k, _ in _LaunchCfg._fields_}, ms.value
 
 

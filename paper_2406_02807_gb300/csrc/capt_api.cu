@@ -53,8 +53,9 @@ bool valid_cfg(int kernel, const capt_launch_cfg& c) {
     if (c.warps_per_block < 1 || c.warps_per_block > 16) return false;
     if (c.staging != CAPT_STAGE_GLOBAL && c.staging != CAPT_STAGE_SMEM) return false;
     const int spl = c.spheres_per_lane;
-    if (kernel == CAPT_KERNEL_SPHERES) return spl == 1 || spl == 2 || spl == 4 || spl == 8;
-    if (kernel == CAPT_KERNEL_CONFIGS) return spl == 2 || spl == 4 || spl == 8;
+    if (kernel == CAPT_KERNEL_SPHERES) return (spl == 1 || spl == 2 || spl == 4 || spl == 8) && (c.chunk == 0 || c.chunk == 1);
+    if (kernel == CAPT_KERNEL_CONFIGS)
+        return (spl == 2 || spl == 4 || spl == 8 || spl == 16) && (c.chunk == 0 || c.chunk == 1);
     if (kernel == CAPT_KERNEL_EDGES) return c.chunk >= 1 && c.chunk <= 1024;   // one configuration per lane
     if (kernel == CAPT_KERNEL_CLEARANCE) return true;
     if (kernel == CAPT_KERNEL_JOINTS) return true;   // one configuration per lane
@@ -102,7 +103,7 @@ struct capt_tree {
 
     capt_tree() {
         cfg[CAPT_KERNEL_SPHERES] = {8, 2, CAPT_STAGE_SMEM, 0};
-        cfg[CAPT_KERNEL_CONFIGS] = {8, 2, CAPT_STAGE_SMEM, 0};
+        cfg[CAPT_KERNEL_CONFIGS] = {4, 8, CAPT_STAGE_GLOBAL, 1};
         cfg[CAPT_KERNEL_EDGES] = {8, 2, CAPT_STAGE_SMEM, 32};
         cfg[CAPT_KERNEL_CLEARANCE] = {8, 2, CAPT_STAGE_SMEM, 0};
         cfg[CAPT_KERNEL_JOINTS] = {4, 1, CAPT_STAGE_GLOBAL, 0};
@@ -670,47 +671,75 @@ int capt_get_launch_cfg(const capt_tree* t, int kernel, capt_launch_cfg* cfg) {
     return CAPT_OK;
 }
 
+namespace {
+
+// Time each candidate launch configuration of the sphere or configuration kernel on
+// these inputs (CUDA events, best of two after one untimed run) and keep the fastest.
+int autotune_query(capt_tree* t, int kernel, const std::vector<capt_launch_cfg>& cands, const float* d_centers,
+                   const float* d_radii, size_t n, int S, uint8_t* d_flags, cudaStream_t st, capt_launch_cfg* best,
+                   float* best_ms) {
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0), "event");
+    CUDA_TRY(cudaEventCreate(&e1), "event");
+    float best_t = INFINITY;
+    capt_launch_cfg best_c = t->cfg[kernel];
+    std::string err;
+    const int mode = kernel == CAPT_KERNEL_CONFIGS ? capt::kModeConfigs : capt::kModeSpheres;
+    int rc = CAPT_OK;
+    for (const capt_launch_cfg& c : cands) {
+        float tt = INFINITY;
+        for (int rep = 0; rep < 3; rep++) {
+            cudaEventRecord(e0, st);
+            rc = capt::launch_query(t->args(), mode, d_centers, d_radii, n, S, d_flags, c, st, err);
+            cudaEventRecord(e1, st);
+            if (rc) break;
+            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = CAPT_E_CUDA; break; }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) tt = std::min(tt, ms);
+        }
+        if (rc) break;
+        if (tt < best_t) { best_t = tt; best_c = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return fail(rc, err.empty() ? "autotune failed" : err);
+    t->cfg[kernel] = best_c;
+    if (best) *best = best_c;
+    if (best_ms) *best_ms = best_t;
+    return CAPT_OK;
+}
+
+}  // namespace
+
 int capt_autotune_configs(capt_tree* t, const float* d_centers, const float* d_radii, size_t C, int S,
                           uint8_t* d_flags, void* stream, capt_launch_cfg* best, float* best_ms) {
     int rc = check_ready(t);
     if (rc) return rc;
     if (S < 1 || S > CAPT_MAX_SPHERES || C == 0) return fail(CAPT_E_ARG, "need C > 0 and S in [1, 64]");
     if (!d_centers || !d_radii || !d_flags) return fail(CAPT_E_ARG, "NULL device pointer");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaEvent_t e0, e1;
-    CUDA_TRY(cudaEventCreate(&e0), "event");
-    CUDA_TRY(cudaEventCreate(&e1), "event");
-    float best_t = INFINITY;
-    capt_launch_cfg best_c = t->cfg[CAPT_KERNEL_CONFIGS];
-    std::string err;
+    std::vector<capt_launch_cfg> cands;
     for (int warps : {4, 8, 16})
-        for (int spl : {2, 4, 8})
-            for (int stage : {CAPT_STAGE_GLOBAL, CAPT_STAGE_SMEM}) {
-                capt_launch_cfg c = {warps, spl, stage, 0};
-                float tt = INFINITY;
-                for (int rep = 0; rep < 3; rep++) {
-                    cudaEventRecord(e0, st);
-                    rc = capt::launch_query(t->args(), capt::kModeConfigs, d_centers, d_radii, C, S, d_flags, c, st, err);
-                    cudaEventRecord(e1, st);
-                    if (rc) break;
-                    if (cudaEventSynchronize(e1) != cudaSuccess) { rc = CAPT_E_CUDA; break; }
-                    float ms = 0;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    if (rep > 0) tt = std::min(tt, ms);
-                }
-                if (rc) {
-                    cudaEventDestroy(e0);
-                    cudaEventDestroy(e1);
-                    return fail(rc, err.empty() ? "autotune failed" : err);
-                }
-                if (tt < best_t) { best_t = tt; best_c = c; }
-            }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    t->cfg[CAPT_KERNEL_CONFIGS] = best_c;
-    if (best) *best = best_c;
-    if (best_ms) *best_ms = best_t;
-    return CAPT_OK;
+        for (int spl : {2, 4, 8, 16})
+            for (int stage : {CAPT_STAGE_GLOBAL, CAPT_STAGE_SMEM})
+                for (int chunked : {0, 1}) cands.push_back({warps, spl, stage, chunked});
+    return autotune_query(t, CAPT_KERNEL_CONFIGS, cands, d_centers, d_radii, C, S, d_flags,
+                          static_cast<cudaStream_t>(stream), best, best_ms);
+}
+
+int capt_autotune_spheres(capt_tree* t, const float* d_centers, const float* d_radii, size_t m, uint8_t* d_flags,
+                          void* stream, capt_launch_cfg* best, float* best_ms) {
+    int rc = check_ready(t);
+    if (rc) return rc;
+    if (m == 0) return fail(CAPT_E_ARG, "need m > 0");
+    if (!d_centers || !d_radii || !d_flags) return fail(CAPT_E_ARG, "NULL device pointer");
+    std::vector<capt_launch_cfg> cands;
+    for (int warps : {4, 8, 16})
+        for (int spl : {1, 2, 4, 8})
+            for (int stage : {CAPT_STAGE_GLOBAL, CAPT_STAGE_SMEM})
+                for (int chunked : {0, 1}) cands.push_back({warps, spl, stage, chunked});
+    return autotune_query(t, CAPT_KERNEL_SPHERES, cands, d_centers, d_radii, m, 1, d_flags,
+                          static_cast<cudaStream_t>(stream), best, best_ms);
 }
 
 }  // extern "C"

@@ -48,7 +48,7 @@ __device__ __forceinline__ void bulk_copy(float* dst, const float* src, uint32_t
                  : "memory");
 }
 
-template <int SPL, bool STAGE>
+template <int SPL, bool STAGE, bool CHUNKED>
 __global__ void __launch_bounds__(512, 2)
     k_spheres(DevArgs t, const float* __restrict__ centers, const float* __restrict__ radii, uint64_t m,
               uint8_t* __restrict__ out) {
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(512, 2)
                 const float r = in[3 * E + j];
                 c = make_float4(in[3 * j], in[3 * j + 1], in[3 * j + 2], __fmul_rn(r, r));
             }
-            sphere_round<false>(t, Ts, &ws->re, ws->ghit, c, j, live, lane, lt_mask);
+            sphere_round<false, CHUNKED>(t, Ts, &ws->re, ws->ghit, c, j, live, lane, lt_mask);
         }
         __syncwarp();
 #pragma unroll
@@ -196,7 +196,7 @@ constexpr int kQueue = 160;   // near-sphere queue: < 32 left over + 128 from on
 struct CfgScratch {
     float4 nc[kQueue];     // queued near spheres: centre and r^2
     uint32_t ng[kQueue];   // their configuration within the tile
-    uint32_t ghit[16];     // per configuration of the tile: 1 once it collides
+    uint32_t ghit[32];     // per configuration of the tile: 1 once it collides
     RoundEntries re;
 };
 
@@ -204,7 +204,7 @@ struct CfgScratch {
 #define CFG_MIN_BLOCKS 2
 #endif
 
-template <int CPT, bool STAGE>
+template <int CPT, bool STAGE, bool CHUNKED>
 __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs(DevArgs t, const float* __restrict__ centers,
                                                                  const float* __restrict__ radii, uint64_t C, int S,
                                                                  uint8_t* __restrict__ out) {
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs(DevArgs t, cons
         const bool live = lane < n;
         const float4 c = live ? ws->nc[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
         const uint32_t g = live ? ws->ng[lane] : 0u;
-        sphere_round<false>(t, Ts, &ws->re, ws->ghit, c, g, live, lane, lt_mask);
+        sphere_round<false, CHUNKED>(t, Ts, &ws->re, ws->ghit, c, g, live, lane, lt_mask);
     };
 
     for (uint64_t tile = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp; tile < n_tiles; tile += nwarps) {
@@ -443,16 +443,18 @@ namespace {
 
 using SphereKernel = void (*)(DevArgs, const float*, const float*, uint64_t, uint8_t*);
 
-SphereKernel pick_spheres(int spl, bool stage) {
-    switch (spl * 2 + (stage ? 1 : 0)) {
-        case 2: return k_spheres<1, false>;
-        case 3: return k_spheres<1, true>;
-        case 4: return k_spheres<2, false>;
-        case 5: return k_spheres<2, true>;
-        case 8: return k_spheres<4, false>;
-        case 9: return k_spheres<4, true>;
-        case 16: return k_spheres<8, false>;
-        case 17: return k_spheres<8, true>;
+template <int SPL>
+SphereKernel pick_spheres_spl(bool stage, bool chunked) {
+    if (stage) return chunked ? k_spheres<SPL, true, true> : k_spheres<SPL, true, false>;
+    return chunked ? k_spheres<SPL, false, true> : k_spheres<SPL, false, false>;
+}
+
+SphereKernel pick_spheres(int spl, bool stage, bool chunked) {
+    switch (spl) {
+        case 1: return pick_spheres_spl<1>(stage, chunked);
+        case 2: return pick_spheres_spl<2>(stage, chunked);
+        case 4: return pick_spheres_spl<4>(stage, chunked);
+        case 8: return pick_spheres_spl<8>(stage, chunked);
         default: return nullptr;
     }
 }
@@ -487,14 +489,18 @@ int occupancy(const void* fn, int threads, size_t smem) {
 
 using ConfigKernel = void (*)(DevArgs, const float*, const float*, uint64_t, int, uint8_t*);
 
-ConfigKernel pick_configs(int spl, bool stage) {
-    switch (spl * 2 + (stage ? 1 : 0)) {
-        case 4: return k_configs<4, false>;
-        case 5: return k_configs<4, true>;
-        case 8: return k_configs<8, false>;
-        case 9: return k_configs<8, true>;
-        case 16: return k_configs<16, false>;
-        case 17: return k_configs<16, true>;
+template <int CPT>
+ConfigKernel pick_configs_cpt(bool stage, bool chunked) {
+    if (stage) return chunked ? k_configs<CPT, true, true> : k_configs<CPT, true, false>;
+    return chunked ? k_configs<CPT, false, true> : k_configs<CPT, false, false>;
+}
+
+ConfigKernel pick_configs(int spl, bool stage, bool chunked) {
+    switch (spl) {
+        case 2: return pick_configs_cpt<4>(stage, chunked);
+        case 4: return pick_configs_cpt<8>(stage, chunked);
+        case 8: return pick_configs_cpt<16>(stage, chunked);
+        case 16: return pick_configs_cpt<32>(stage, chunked);
         default: return nullptr;
     }
 }
@@ -502,8 +508,8 @@ ConfigKernel pick_configs(int spl, bool stage) {
 int launch_configs(const DevArgs& t, const float* centers, const float* radii, uint64_t C, int S, uint8_t* out,
                    const capt_launch_cfg& cfg, cudaStream_t st, std::string& err) {
     const bool stage = cfg.staging == CAPT_STAGE_SMEM && t.stage_floats > 0;
-    ConfigKernel fn = pick_configs(cfg.spheres_per_lane, stage);
-    if (!fn) { err = "configuration queries take spheres_per_lane 2, 4 or 8"; return CAPT_E_ARG; }
+    ConfigKernel fn = pick_configs(cfg.spheres_per_lane, stage, cfg.chunk != 0);
+    if (!fn) { err = "configuration queries take spheres_per_lane 2, 4, 8 or 16"; return CAPT_E_ARG; }
     const int cpt = 2 * cfg.spheres_per_lane;
     const int warps = std::max(1, std::min(16, (int)cfg.warps_per_block));
     const size_t smem = (stage ? stage_offset(t) : 0u) + sizeof(CfgScratch) * (size_t)warps;
@@ -525,7 +531,7 @@ int launch_query(const DevArgs& t, int mode, const float* centers, const float* 
     if (mode == kModeConfigs) return launch_configs(t, centers, radii, n_items, S, out, cfg, st, err);
     const int spl = cfg.spheres_per_lane;
     const bool stage = cfg.staging == CAPT_STAGE_SMEM && t.stage_floats > 0;
-    SphereKernel fn = pick_spheres(spl, stage);
+    SphereKernel fn = pick_spheres(spl, stage, cfg.chunk != 0);
     if (!fn) { err = "sphere queries take spheres_per_lane 1, 2, 4 or 8"; return CAPT_E_ARG; }
     const int warps = std::max(1, std::min(16, (int)cfg.warps_per_block));
     const size_t smem = (stage ? stage_offset(t) : 0u) + sphere_scratch_bytes(spl) * (size_t)warps;

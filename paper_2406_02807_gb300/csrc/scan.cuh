@@ -2,10 +2,10 @@
 //
 // A "round" takes up to 32 queued spheres (centre and r^2, one per lane): each lane
 // descends the tree, loads its leaf record and applies the leaf box test of Alg. 3;
-// the spheres that pass become entries.  Their sets are then walked chunk by chunk
-// (kChunkBlocks blocks of 4 points): every chunk first meets its FP32 bounding box,
-// one chunk per lane, and only the chunks whose box the sphere reaches are scanned,
-// 64 blocks per warp step.  Every lane test is three 16-byte loads and four FP32
+// the spheres that pass become entries.  In the chunked form their sets are then
+// walked chunk by chunk (kChunkBlocks blocks of 4 points): every chunk first meets its
+// FP32 bounding box, one chunk per lane, and only the chunks whose box the sphere
+// reaches are scanned, 64 blocks per warp step.  The plain form scans whole sets.  Every lane test is three 16-byte loads and four FP32
 // distance tests in packed FP32x2 arithmetic.
 // The blocks are stored as three planes of float4 (x quads, y quads, z quads), so the
 // loads of consecutive blocks by consecutive lanes are contiguous in each plane.
@@ -73,16 +73,20 @@ __device__ __forceinline__ bool block_hit2(const float4* __restrict__ blocks, ui
 // Per-warp storage of one round.
 struct RoundEntries {
     float4 c[32];       // entry: centre and r^2
+    uint32_t grp[32];   // its group (configuration of the tile)
+    // chunked form
     uint32_t b0[32];    // its set's first block
     uint32_t b1[32];    // its set's end block
-    uint32_t grp[32];   // its group (configuration of the tile)
     uint32_t cend[32];  // exclusive end of its chunks in the round's list of chunks
     uint2 q[64];        // chunks whose box the sphere reaches: {entry, chunk}
+    // plain form
+    int32_t boff[32];   // first block minus the entry's start in the concatenated list
+    uint32_t end[32];   // exclusive end of the entry in the concatenated list
 };
 
-// One round over the spheres (c, g) held by lanes < n.  Groups already marked in
-// ghit are skipped; a hit marks its group.  With SINGLE there is one group and the
-// first hit ends the round (return value: whether a hit was found).
+// One round over the spheres (c, g) held by lanes < n, chunked form.  Groups already
+// marked in ghit are skipped; a hit marks its group.  With SINGLE there is one group
+// and the first hit ends the round (return value: whether a hit was found).
 //  1. Each lane descends, loads its leaf record and applies the leaf box test of
 //     Alg. 3; the spheres that pass are the round's entries.
 //  2. Chunk boxes: the blocks are grouped in chunks of kChunkBlocks consecutive blocks
@@ -94,8 +98,8 @@ struct RoundEntries {
 //  3. Queued chunks are scanned 8 at a time: lane l takes block l % 8 of chunks l / 8
 //     and 4 + l / 8, within the entry's set; a hit resolves the entry's group.
 template <bool SINGLE>
-__device__ __forceinline__ bool sphere_round(const DevArgs& t, const float* Ts, RoundEntries* re, uint32_t* ghit,
-                                             float4 c, uint32_t g, bool live, uint32_t lane, uint32_t lt_mask) {
+__device__ __forceinline__ bool round_chunked(const DevArgs& t, const float* Ts, RoundEntries* re, uint32_t* ghit,
+                                              float4 c, uint32_t g, bool live, uint32_t lane, uint32_t lt_mask) {
     const float4* blocks = reinterpret_cast<const float4*>(t.blocks);
     const float4* cbox = reinterpret_cast<const float4*>(t.cbox);
     bool act = false;
@@ -204,6 +208,154 @@ __device__ __forceinline__ bool sphere_round(const DevArgs& t, const float* Ts, 
     }
     __syncwarp();
     return found;
+}
+
+// The plain form of a round (Alg. 3's scan of each whole set, no chunk boxes): when
+// the sets are large (at least 32 blocks each on average) the warp scans one set at a
+// time with all lanes (lane l on blocks l, l + 32, ..., two per step); otherwise it
+// walks the concatenation of all the sets 32 blocks at a time.  It wins where chunk
+// boxes are loose (point indices with no spatial order) or sets are a chunk or two.
+template <bool SINGLE>
+__device__ __forceinline__ bool round_plain(const DevArgs& t, const float* Ts, RoundEntries* re, uint32_t* ghit,
+                                             float4 c, uint32_t g, bool live, uint32_t lane, uint32_t lt_mask) {
+    const float4* blocks = reinterpret_cast<const float4*>(t.blocks);
+    bool act = false;
+    uint32_t nb = 0, fb = 0;
+    if (live && (SINGLE || !ghit[g])) {
+        const uint32_t leaf = descend(c.x, c.y, c.z, t, Ts);
+        float4 a, b;
+        load_leaf(t.leaves, leaf, a, b);
+        const uint32_t cnt = __float_as_uint(b.w);
+        act = cnt > 0 && box_dist2(c.x, c.y, c.z, a, b) <= c.w;
+        nb = act ? (cnt + 3u) >> 2 : 0u;
+        fb = __float_as_uint(a.w);
+    }
+    const uint32_t mask = __ballot_sync(0xffffffffu, act);
+    if (mask == 0) return false;
+    const uint32_t incl = warp_incl_scan(nb);
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    const uint32_t n_ent = __popc(mask);
+    __syncwarp();
+    if (act) {
+        const uint32_t pos = __popc(mask & lt_mask);
+        re->c[pos] = c;
+        re->boff[pos] = (int32_t)fb - (int32_t)(incl - nb);
+        re->end[pos] = incl;
+        re->grp[pos] = g;
+    }
+    __syncwarp();
+    bool found = false;
+    if (total >= 32u * n_ent) {
+    // Large sets: one entry at a time, the whole warp on its blocks (lane l takes blocks
+    // fb + l + 32 k, V per step), so block addresses need no per-lane lookup; a hit
+    // resolves the entry's group.
+    constexpr int V = 2;
+    for (uint32_t e = 0; e < n_ent; e++) {
+        const uint32_t ge = re->grp[e];
+        if (!SINGLE && ghit[ge]) continue;
+        const float4 ce = re->c[e];
+        const uint32_t b_end = re->end[e];
+        const uint32_t b_beg = e ? re->end[e - 1] : 0u;
+        const int64_t o = (int64_t)re->boff[e];
+        const uint64_t cxx = f2_dup(ce.x), cyy = f2_dup(ce.y), czz = f2_dup(ce.z);
+        bool hit = false;
+        for (uint32_t p = b_beg + lane; __any_sync(0xffffffffu, p < b_end); p += 32 * V) {
+            uint64_t s01[V], s23[V];
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                s01[v] = s23[v] = 0;
+                if (p + 32 * v < b_end) block_d2(blocks, t.plane, o + p + 32 * v, cxx, cyy, czz, s01[v], s23[v]);
+            }
+            bool h = false;
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                if (p + 32 * v < b_end) {
+                    const float2 x = f2_split(s01[v]), y = f2_split(s23[v]);
+                    h |= (x.x <= ce.w) | (x.y <= ce.w) | (y.x <= ce.w) | (y.y <= ce.w);
+                }
+            }
+            if (__any_sync(0xffffffffu, h)) { hit = true; break; }
+        }
+        if (hit) {
+            if (SINGLE) { found = true; break; }
+            if (lane == 0) ghit[ge] = 1;
+            __syncwarp();
+        }
+    }
+    } else {
+    // Small sets: the concatenated blocks of all entries, U per lane per step (32 U per
+    // warp step), lane l taking blocks base + l + 32 u; each lane keeps the fields of the
+    // entries it is in, reloading them only when it moves on.
+    constexpr int U = 1;
+    uint32_t ei[U], ce[U];
+    float4 cc[U];
+    int32_t oo[U];
+    uint32_t gg[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        ei[u] = 0;
+        ce[u] = 0xffffffffu;
+        cc[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        oo[u] = 0;
+        gg[u] = 0;
+    }
+    for (uint32_t base = 0; base < total; base += 32 * U) {
+        bool live[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const uint32_t p = base + lane + 32u * u;
+            live[u] = p < total;
+            if (live[u]) {
+                if (u > 0 && ei[u] < ei[u - 1]) ei[u] = ei[u - 1];
+                while (re->end[ei[u]] <= p) ei[u]++;
+                if (ei[u] != ce[u]) {
+                    cc[u] = re->c[ei[u]];
+                    oo[u] = re->boff[ei[u]];
+                    gg[u] = re->grp[ei[u]];
+                    ce[u] = ei[u];
+                }
+                live[u] = SINGLE || !ghit[gg[u]];
+            }
+        }
+        uint64_t s01[U], s23[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            s01[u] = s23[u] = 0;
+            if (live[u])
+                block_d2(blocks, t.plane, (int64_t)oo[u] + base + lane + 32u * u, f2_dup(cc[u].x), f2_dup(cc[u].y),
+                         f2_dup(cc[u].z), s01[u], s23[u]);
+        }
+        bool h = false;
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            if (!live[u]) continue;
+            const float2 x = f2_split(s01[u]), y = f2_split(s23[u]);
+            const bool hu = (x.x <= cc[u].w) | (x.y <= cc[u].w) | (y.x <= cc[u].w) | (y.y <= cc[u].w);
+            if (!SINGLE && hu) ghit[gg[u]] = 1;
+            h |= hu;
+        }
+        if (SINGLE) {
+            if (__any_sync(0xffffffffu, h)) { found = true; break; }
+            continue;
+        }
+        __syncwarp();
+        if (__any_sync(0xffffffffu, h)) {
+            // leave once every entry that still has blocks ahead is resolved
+            const bool open = lane < n_ent && re->end[lane] > base + 32 * U && !ghit[re->grp[lane]];
+            if (!__any_sync(0xffffffffu, open)) break;
+        }
+    }
+    }
+    __syncwarp();
+    return found;
+}
+
+// One round over the spheres (c, g) held by lanes < n, chunked (default) or plain.
+template <bool SINGLE, bool CHUNKED = true>
+__device__ __forceinline__ bool sphere_round(const DevArgs& t, const float* Ts, RoundEntries* re, uint32_t* ghit,
+                                             float4 c, uint32_t g, bool live, uint32_t lane, uint32_t lt_mask) {
+    if constexpr (CHUNKED) return round_chunked<SINGLE>(t, Ts, re, ghit, c, g, live, lane, lt_mask);
+    else return round_plain<SINGLE>(t, Ts, re, ghit, c, g, live, lane, lt_mask);
 }
 
 }  // namespace capt

@@ -13,7 +13,7 @@ import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-ALL_CFGS = [(w, s, st) for w in (4, 8, 16) for s in (1, 2, 4, 8) for st in (0, 1)]
+ALL_CFGS = [(w, s, st, ch) for w in (4, 8, 16) for s in (1, 2, 4, 8) for st in (0, 1) for ch in (0, 1)]
 
 
 @pytest.fixture(scope="module")
@@ -67,10 +67,19 @@ def test_spheres_uniform2k_bit_exact(uniform2k, capt_lib, torch_):
     assert capt_lib.capt_device_status(uniform2k["tree"]) == 0
 
 
-@pytest.mark.parametrize("warps,spl,stage", ALL_CFGS)
-def test_spheres_every_launch_cfg(uniform2k, capt_lib, torch_, warps, spl, stage):
+@pytest.mark.parametrize("warps,spl,stage,chunked", ALL_CFGS)
+def test_spheres_every_launch_cfg(uniform2k, capt_lib, torch_, warps, spl, stage, chunked):
     t = uniform2k["tree"]
-    capt_lib.capt_set_launch_cfg(t, capt_lib.CAPT_KERNEL_SPHERES, warps, spl, stage)
+    capt_lib.capt_set_launch_cfg(t, capt_lib.CAPT_KERNEL_SPHERES, warps, spl, stage, chunked)
+    f = capt_lib.capt_query_spheres(t, uniform2k["dc"], uniform2k["dr"])
+    assert np.array_equal(f.cpu().numpy(), uniform2k["ref"])
+    capt_lib.capt_set_launch_cfg(t, capt_lib.CAPT_KERNEL_SPHERES, 8, 2, 1)
+
+
+def test_spheres_autotune_keeps_results(uniform2k, capt_lib, torch_):
+    t = uniform2k["tree"]
+    cfg, ms = capt_lib.capt_autotune_spheres(t, uniform2k["dc"], uniform2k["dr"])
+    assert ms > 0 and cfg["chunk"] in (0, 1)
     f = capt_lib.capt_query_spheres(t, uniform2k["dc"], uniform2k["dr"])
     assert np.array_equal(f.cpu().numpy(), uniform2k["ref"])
     capt_lib.capt_set_launch_cfg(t, capt_lib.CAPT_KERNEL_SPHERES, 8, 2, 1)
@@ -150,15 +159,16 @@ def test_configs_bit_exact_against_brute_force(tabletop, orc, capt_lib, torch_):
     assert 0.05 < ref.mean() < 0.95
 
 
-@pytest.mark.parametrize("warps,spl,stage", [(w, s, st) for w in (4, 8, 16) for s in (2, 4, 8) for st in (0, 1)])
-def test_configs_every_launch_cfg(tabletop, orc, capt_lib, torch_, warps, spl, stage):
+@pytest.mark.parametrize("warps,spl,stage,chunked",
+                         [(w, s, st, ch) for w in (4, 8, 16) for s in (2, 4, 8, 16) for st in (0, 1) for ch in (0, 1)])
+def test_configs_every_launch_cfg(tabletop, orc, capt_lib, torch_, warps, spl, stage, chunked):
     cen = _configs(tabletop, 3001, first=777)                    # odd count: ragged last tile
     r = tabletop["arm"].sphere_radius
     ref, _ = tabletop["oracle_tree"].query_configs(cen, r)
     t = tabletop["tree"]
-    capt_lib.capt_set_launch_cfg(t, capt_lib.CAPT_KERNEL_CONFIGS, warps, spl, stage)
+    capt_lib.capt_set_launch_cfg(t, capt_lib.CAPT_KERNEL_CONFIGS, warps, spl, stage, chunked)
     f = capt_lib.capt_query_configs(t, _cuda(torch_, cen), _cuda(torch_, r))
-    capt_lib.capt_set_launch_cfg(t, capt_lib.CAPT_KERNEL_CONFIGS, 8, 2, 1)
+    capt_lib.capt_set_launch_cfg(t, capt_lib.CAPT_KERNEL_CONFIGS, 4, 8, 0, 1)
     assert np.array_equal(f.cpu().numpy(), ref)
 
 
@@ -461,3 +471,5 @@ def test_room_full_size(orc, capt_lib, torch_):
     assert np.array_equal(f, ref)
     idx = np.random.default_rng(0).choice(len(c), 20000, replace=False)
     assert np.array_equal(f[idx], orc.brute_flags(pts, c[idx], r[idx]))
+    capt_lib.capt_set_launch_cfg(tree, capt_lib.CAPT_KERNEL_SPHERES, 8, 2, 0, 1)   # chunked scan
+    assert np.array_equal(capt_lib.capt_query_spheres(tree, _cuda(torch_, c), _cuda(torch_, r)).cpu().numpy(), ref)
