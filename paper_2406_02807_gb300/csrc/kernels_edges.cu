@@ -11,8 +11,10 @@
 // hit invalidates the edge and ends the pass.
 //
 // Persistent mode: work items are (edge, chunk of configurations), enumerated edge by
-// edge.  A setup kernel writes the exclusive prefix of the per-edge item counts and
-// resets the work counter and the validity flags; the persistent kernel's warps take
+// edge; the chunks of an edge interleave its configurations (item ci of nci takes every
+// nci-th one from ci), so that the first items in flight sample the whole edge.  A
+// setup kernel writes the exclusive prefix of the per-edge item counts and resets the
+// work counter and the validity flags; the persistent kernel's warps take
 // items from the counter with one atomic each and skip items of edges already known to
 // collide.  capt_edge_plan_create captures both launches into a CUDA graph.
 // Per-edge mode (the baseline): one kernel launch per edge.
@@ -113,11 +115,11 @@ struct EdgeScratch {
     RoundEntries re;
 };
 
-// One pass: configurations k0 .. k0 + count - 1 (count <= 32) of the edge with n_e
-// configurations from qa_e to qb_e, lane i taking configuration k0 + i.  Returns true
+// One pass: configurations k0 + stride * i, i = 0 .. count - 1 (count <= 32), of the
+// edge with n_e configurations from qa_e to qb_e, lane i taking the i-th.  Returns true
 // as soon as one of them collides.
 __device__ bool edge_pass(const DevArgs& t, const ArmPlan& arm, const float* __restrict__ qa_e,
-                          const float* __restrict__ qb_e, int n_e, int k0, int count, const float* Ts,
+                          const float* __restrict__ qb_e, int n_e, int k0, int stride, int count, const float* Ts,
                           EdgeScratch* ws) {
     const uint32_t lane = lane_id();
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -125,7 +127,7 @@ __device__ bool edge_pass(const DevArgs& t, const ArmPlan& arm, const float* __r
     const float4 rlo = make_float4(t.lo[0], t.lo[1], t.lo[2], 0.f);
     const float4 rhi = make_float4(t.hi[0], t.hi[1], t.hi[2], 0.f);
     // q_k = q_a + (k / (n - 1)) (q_b - q_a)
-    const float tk = n_e > 1 ? __fdiv_rn((float)(k0 + (int)lane), (float)(n_e - 1)) : 0.f;
+    const float tk = n_e > 1 ? __fdiv_rn((float)(k0 + stride * (int)lane), (float)(n_e - 1)) : 0.f;
     float R[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
     float p[3] = {arm.base[0], arm.base[1], arm.base[2]};
     uint32_t n_near = 0;
@@ -247,12 +249,16 @@ __global__ void __launch_bounds__(512, 2) k_edges_persistent(DevArgs t, const __
         const uint32_t e = lo;
         if (load_volatile_u8(valid + e) == 0) continue;
         const int n_e = __ldg(ns + e);
-        const int k_begin = (int)((item - __ldg(scratch + e)) * chunk);
-        const int k_end = min(n_e, k_begin + (int)chunk);
+        // the edge's items interleave its configurations: item ci of nci takes
+        // ci, ci + nci, ci + 2 nci, ..., so its first passes sample the whole edge and a
+        // colliding stretch is met early wherever it lies
+        const int nci = (n_e + (int)chunk - 1) / (int)chunk;
+        const int ci = (int)(item - __ldg(scratch + e));
+        const int cnt = (n_e - ci + nci - 1) / nci;
         const float* qa_e = qa + (size_t)e * J;
         const float* qb_e = qb + (size_t)e * J;
-        for (int k = k_begin; k < k_end; k += 32) {
-            if (edge_pass(t, arm, qa_e, qb_e, n_e, k, min(32, k_end - k), Ts, ws)) {
+        for (int j = 0; j < cnt; j += 32) {
+            if (edge_pass(t, arm, qa_e, qb_e, n_e, ci + nci * j, nci, min(32, cnt - j), Ts, ws)) {
                 if (lane == 0) valid[e] = 0;
                 break;
             }
@@ -271,7 +277,7 @@ __global__ void __launch_bounds__(512, 2) k_edge_single(DevArgs t, const __grid_
     const int gw = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
     for (int k = gw * 32; k < n_e; k += warps * 32) {
         if (load_volatile_u8(valid_e) == 0) break;
-        if (edge_pass(t, arm, qa_e, qb_e, n_e, k, min(32, n_e - k), nullptr, ws)) {
+        if (edge_pass(t, arm, qa_e, qb_e, n_e, k, 1, min(32, n_e - k), nullptr, ws)) {
             if (lane_id() == 0) *valid_e = 0;
             break;
         }
