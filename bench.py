@@ -506,6 +506,17 @@ def extra_workloads(capt, torch, dev, stream, pts, arm, args):
     fl = torch.empty(1 << 22, dtype=torch.uint8, device=dev)
     rcfg, _ = capt.capt_autotune_spheres(tr, dc, dr, fl)
     ms = time_events(torch, lambda: capt.capt_query_spheres(tr, dc, dr, fl), 10, stream)
+    # the same cloud relabelled along the Z-order curve before the build (same point
+    # set, same flags): sets run along the curve and the chunked scan pays
+    order = capt.capt_morton_order(pr)
+    ts = capt.capt_build(pr[order], 0.02, 0.10)
+    capt.capt_upload(ts, dev.index)
+    fl2 = torch.empty_like(fl)
+    scfg, _ = capt.capt_autotune_spheres(ts, dc, dr, fl2)
+    ms_sorted = time_events(torch, lambda: capt.capt_query_spheres(ts, dc, dr, fl2), 10, stream)
+    res["room200k_zorder"] = {"spheres": 1 << 22, "ms": ms_sorted,
+                              "sphere_queries_per_s": (1 << 22) / (ms_sorted / 1e3), "launch_cfg": scfg,
+                              "flags_equal_unsorted": bool(torch.equal(fl, fl2))}
     res["room200k"] = {"spheres": 1 << 22, "ms": ms, "sphere_queries_per_s": (1 << 22) / (ms / 1e3),
                        "build_ms": bms, "device_build_ms": device_build_ms(capt, pr, 0.02, 0.10, reps=3),
                        "launch_cfg": rcfg, "tree_device_bytes": int(st["device_bytes"]),

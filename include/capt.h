@@ -100,6 +100,16 @@ int capt_build_threads(const float* points, size_t n, float r_min, float r_max, 
  * Errors: CAPT_E_ARG, CAPT_E_RANGE (min_spacing < 0 or NaN), CAPT_E_NONFINITE, CAPT_E_NOMEM. */
 int sfc_filter(const float* points, size_t n, float min_spacing, uint32_t* kept_idx, size_t* n_out);
 
+/* Order of the points along a Z-order curve (the locality measure of Sec. IV-C): 21
+ * bits per axis over the input's bounding box, x most significant in every bit triple,
+ * ties by point index.  points: host float[n][3]; order: host uint32[n] (caller-owned)
+ * receives the permutation.  A cloud relabelled in this order (points[order]) gives a
+ * tree whose affordance sets, stored in ascending index, run along the curve, so their
+ * 32-point chunks are spatially tight and the chunked scan skips most of them; the
+ * filter's output already has this property.  The flags of any query do not depend on
+ * the order.  Errors: CAPT_E_ARG, CAPT_E_NONFINITE, CAPT_E_NOMEM. */
+int capt_morton_order(const float* points, size_t n, uint32_t* order);
+
 /* sfc_filter on the GPU (Alg. 2, Sec. IV-C): the same kept indices in the same order.
  * Each pass sorts the survivors by Morton key with a stable device radix sort and
  * replaces the sequential sweep by its chain form (the next kept point after p_j is the

@@ -23,7 +23,8 @@ __all__ = [
     "capt_edge_plan_launch", "capt_edge_plan_info", "capt_edge_plan_free", "capt_clearance_fwd",
     "capt_clearance_bwd", "capt_free", "capt_last_error", "make_arm", "CaptTree", "EdgePlan",
     "capt_validate_edges_static", "CAPT_STATIC_MAX_EDGES", "capt_build_device", "capt_query_joint_configs",
-    "capt_autotune_joint_configs", "CAPT_KERNEL_JOINTS", "sfc_filter_device", "capt_autotune_spheres", "STATUS", "CAPT_STAGE_GLOBAL", "CAPT_STAGE_SMEM", "CAPT_KERNEL_SPHERES", "CAPT_KERNEL_CONFIGS",
+    "capt_autotune_joint_configs", "CAPT_KERNEL_JOINTS", "sfc_filter_device", "capt_autotune_spheres",
+    "capt_morton_order", "STATUS", "CAPT_STAGE_GLOBAL", "CAPT_STAGE_SMEM", "CAPT_KERNEL_SPHERES", "CAPT_KERNEL_CONFIGS",
     "CAPT_KERNEL_EDGES", "CAPT_KERNEL_CLEARANCE", "CAPT_EDGES_PERSISTENT", "CAPT_EDGES_PER_EDGE",
     "EXPORTED_SYMBOLS",
 ]
@@ -43,7 +44,7 @@ EXPORTED_SYMBOLS = [
     "capt_autotune_configs", "capt_validate_edges", "capt_edge_plan_create", "capt_edge_plan_launch",
     "capt_edge_plan_info", "capt_edge_plan_free", "capt_clearance_fwd", "capt_clearance_bwd",
     "capt_validate_edges_static", "capt_build_device", "capt_query_joint_configs", "capt_autotune_joint_configs",
-    "sfc_filter_device", "capt_autotune_spheres",
+    "sfc_filter_device", "capt_autotune_spheres", "capt_morton_order",
 ]
 CAPT_STATIC_MAX_EDGES = 65536
 
@@ -90,6 +91,7 @@ def _load():
         "capt_build_threads": [P, SZ, F, F, I, C.POINTER(P)],
         "sfc_filter": [P, SZ, F, P, C.POINTER(SZ)],
         "sfc_filter_device": [P, SZ, F, P, C.POINTER(SZ), P],
+        "capt_morton_order": [P, SZ, P],
         "capt_stats": [P, C.POINTER(_Stats)],
         "capt_export": [P, P, P, P, P],
         "capt_upload": [P, I, P],
@@ -210,6 +212,15 @@ def sfc_filter(points, min_spacing: float) -> np.ndarray:
     n = C.c_size_t(0)
     _check(_load().sfc_filter(_ptr(p), p.shape[0], float(min_spacing), _ptr(out), C.byref(n)), "sfc_filter")
     return out[: n.value].copy()
+
+
+def capt_morton_order(points) -> np.ndarray:
+    """Permutation of the points along a Z-order curve (x most significant, ties by
+    index); points[order] gives spatially tight affordance-set chunks."""
+    p = _host_f32(points, 3)
+    out = np.zeros(max(p.shape[0], 1), np.uint32)
+    _check(_load().capt_morton_order(_ptr(p), p.shape[0], _ptr(out)), "capt_morton_order")
+    return out[: p.shape[0]].copy()
 
 
 def sfc_filter_device(points, min_spacing: float, stream=None):

@@ -382,6 +382,12 @@ int sfc_filter(const float* points, size_t n, float min_spacing, uint32_t* kept_
     return rc == CAPT_OK ? rc : fail(rc, err);
 }
 
+int capt_morton_order(const float* points, size_t n, uint32_t* order) {
+    std::string err;
+    int rc = capt::host_morton_order(points, n, order, err);
+    return rc == CAPT_OK ? rc : fail(rc, err);
+}
+
 int sfc_filter_device(const float* d_points, size_t n, float min_spacing, uint32_t* d_kept, size_t* n_out,
                       void* stream) {
     std::string err;

@@ -117,4 +117,56 @@ int host_sfc_filter(const float* pts, size_t n, float r, uint32_t* kept, size_t*
     return CAPT_OK;
 }
 
+int host_morton_order(const float* pts, size_t n, uint32_t* order, std::string& err) {
+    if (n && (!pts || !order)) { err = "NULL argument"; return CAPT_E_ARG; }
+    if (n >= (size_t(1) << 32)) { err = "n must be below 2^32"; return CAPT_E_ARG; }
+    if (n == 0) return CAPT_OK;
+    float lo[3], hi[3];
+    for (int a = 0; a < 3; a++) lo[a] = hi[a] = pts[a];
+    for (size_t j = 0; j < n; j++)
+        for (int a = 0; a < 3; a++) {
+            float v = pts[3 * j + a];
+            if (!std::isfinite(v)) { err = "non-finite coordinate in points"; return CAPT_E_NONFINITE; }
+            lo[a] = v < lo[a] ? v : lo[a];
+            hi[a] = v > hi[a] ? v : hi[a];
+        }
+    try {
+        std::vector<uint64_t> key(n), ktmp(n);
+        std::vector<uint32_t> idx(n), tmp(n);
+        for (size_t j = 0; j < n; j++) {
+            uint64_t k = 0;
+            for (int a = 0; a < 3; a++) {
+                double ext = (double)hi[a] - (double)lo[a];
+                uint32_t v = 0;
+                if (ext > 0.0) {
+                    double f = std::floor(((double)pts[3 * j + a] - (double)lo[a]) / ext * 2097152.0);
+                    v = f >= 2097151.0 ? 2097151u : (uint32_t)f;
+                }
+                k |= spread3(v) << (2 - a);   // x most significant in every bit triple
+            }
+            key[j] = k;
+            idx[j] = (uint32_t)j;
+        }
+        std::vector<uint32_t> hist(1 << 11);
+        for (int shift = 0; shift < 63; shift += 11) {   // stable LSD radix sort by key
+            std::fill(hist.begin(), hist.end(), 0u);
+            for (size_t j = 0; j < n; j++) hist[(key[j] >> shift) & 2047u]++;
+            uint32_t run = 0;
+            for (auto& h : hist) { uint32_t c = h; h = run; run += c; }
+            for (size_t j = 0; j < n; j++) {
+                uint32_t dst = hist[(key[j] >> shift) & 2047u]++;
+                tmp[dst] = idx[j];
+                ktmp[dst] = key[j];
+            }
+            idx.swap(tmp);
+            key.swap(ktmp);
+        }
+        std::memcpy(order, idx.data(), n * sizeof(uint32_t));
+    } catch (const std::bad_alloc&) {
+        err = "host allocation failed in capt_morton_order";
+        return CAPT_E_NOMEM;
+    }
+    return CAPT_OK;
+}
+
 }  // namespace capt

@@ -473,3 +473,11 @@ def test_room_full_size(orc, capt_lib, torch_):
     assert np.array_equal(f[idx], orc.brute_flags(pts, c[idx], r[idx]))
     capt_lib.capt_set_launch_cfg(tree, capt_lib.CAPT_KERNEL_SPHERES, 8, 2, 0, 1)   # chunked scan
     assert np.array_equal(capt_lib.capt_query_spheres(tree, _cuda(torch_, c), _cuda(torch_, r)).cpu().numpy(), ref)
+    # the same cloud relabelled along the Z-order curve: the same point set, so the same
+    # flags, with either scan
+    order = capt_lib.capt_morton_order(pts)
+    ts = capt_lib.capt_build(pts[order], p["r_min"], p["r_max"])
+    capt_lib.capt_upload(ts, 0)
+    for chunked in (0, 1):
+        capt_lib.capt_set_launch_cfg(ts, capt_lib.CAPT_KERNEL_SPHERES, 8, 2, 0, chunked)
+        assert np.array_equal(capt_lib.capt_query_spheres(ts, _cuda(torch_, c), _cuda(torch_, r)).cpu().numpy(), ref)

@@ -132,3 +132,26 @@ def test_joint_and_filter_calls_reject_bad_arguments_without_gpu(capt_lib):
     assert L.sfc_filter_device(None, 0, -1.0, None, ctypes.byref(n), None) == -2       # negative spacing
     assert L.sfc_filter_device(None, 0, 0.01, None, ctypes.byref(n), None) == 0 and n.value == 0
     assert L.sfc_filter_device(None, 0, 0.01, None, None, None) == -1
+
+
+def test_morton_order_follows_the_oracles_curve(orc, capt_lib):
+    """capt_morton_order is a permutation along the oracle's Z-order key (21 bits per axis
+    over the bounding box, x most significant), ties in ascending index."""
+    pts = W.uniform_cloud(3000, 21)
+    pts[100:140] = pts[7]                          # coincident points: ties
+    pts[200:260, 2] = 0.5                          # a plane: equal z
+    order = capt_lib.capt_morton_order(pts)
+    assert sorted(order.tolist()) == list(range(len(pts)))
+    p64 = pts.astype(np.float64)
+    lo, hi = p64.min(0), p64.max(0)
+    q = np.minimum(2 ** 21 - 1, np.floor((p64 - lo) / (hi - lo) * 2097152.0)).astype(np.int64)
+    keys = np.array([orc.morton_key(q[i], (0, 1, 2)) for i in order], dtype=np.uint64)
+    assert np.all(keys[1:] >= keys[:-1])
+    same = keys[1:] == keys[:-1]
+    assert np.all(order[1:][same] > order[:-1][same])
+    assert capt_lib.capt_morton_order(np.zeros((0, 3), np.float32)).size == 0
+    bad = pts.copy()
+    bad[5, 0] = np.nan
+    with pytest.raises(capt_lib.CaptError) as e:
+        capt_lib.capt_morton_order(bad)
+    assert e.value.status == -3
