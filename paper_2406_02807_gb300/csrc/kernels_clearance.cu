@@ -5,17 +5,18 @@
 // cloud point whenever it is within r_max.  The forward pass therefore scans the whole
 // set (no early exit), keeping the minimum FP32 squared distance and its slot.
 //
-// Forward layout: one block per trajectory, each warp owning a contiguous range of its
-// waypoints.
-//  1. Passes of 128 consecutive spheres (4 per lane, three 16-byte loads): a sphere
-//     farther than r_max from the cloud's bounding box is farther than r_max from every
-//     point, so it gets d = r_max, argmin = -1 at once; the others are queued.
-//  2. Rounds of 32 queued spheres: descent and leaf box test against r_max; each set
-//     of a sphere that passes is scanned in full by the whole warp in packed FP32x2
-//     arithmetic, every lane keeping a running minimum of (d^2, slot) keys, reduced by
-//     one butterfly per set.
-//  3. Each waypoint's cost is summed from the written distances in a fixed order
-//     (lane-strided, then a butterfly) and one thread adds the waypoints in order, so
+// Forward, two kernels:
+//  1. Distances (k_clearance_dist): one block per trajectory, each warp owning a
+//     contiguous range of its waypoints (close in space, so the block's warps share set
+//     blocks in L1); passes of 128 consecutive spheres (4 per lane, three 16-byte
+//     loads): a sphere farther than r_max from the cloud's bounding box is farther than
+//     r_max from every point, so it gets d = r_max, argmin = -1 at once; the others are
+//     queued.  No block barrier: a warp leaves as soon as its range is done.  Rounds of 32 queued spheres: descent and leaf box test against r_max;
+//     each set of a sphere that passes is scanned in full by the whole warp in packed
+//     FP32x2 arithmetic, every lane keeping a running minimum of (d^2, slot) keys,
+//     reduced by one butterfly per set.
+//  2. Costs (k_clearance_cost): one warp per trajectory sums each waypoint's terms in a
+//     fixed order (lane-strided, then a butterfly) and adds the waypoints in order, so
 //     the cost is bitwise reproducible whatever the launch configuration.
 // Backward: elementwise, one thread per sphere, from the saved distance and argmin.
 #include <algorithm>
@@ -29,8 +30,8 @@ namespace capt {
 constexpr int kClearQueue = 160;
 
 struct ClearScratch {
-    float4 nq[kClearQueue];      // queued spheres: centre
-    uint32_t ni[kClearQueue];    // their index within the trajectory
+    float4 nq[kClearQueue];          // queued spheres: centre
+    unsigned long long ni[kClearQueue];   // their global sphere index
 };
 
 // One round over the first n queued spheres of the trajectory at `tbase` (sphere index
@@ -45,7 +46,8 @@ __device__ __forceinline__ void clearance_round(const DevArgs& t, const float* T
     const float4* blocks = reinterpret_cast<const float4*>(t.blocks);
     const bool live = lane < n;
     bool act = false;
-    uint32_t nb = 0, fb = 0, gi = 0;
+    uint32_t nb = 0, fb = 0;
+    uint64_t gi = 0;
     float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
     if (live) {
         c = ws->nq[lane];
@@ -114,31 +116,26 @@ __device__ __forceinline__ void clearance_round(const DevArgs& t, const float* T
 }
 
 template <bool STAGE>
-__global__ void __launch_bounds__(512, 2) k_clearance_fwd(DevArgs t, const float* __restrict__ centers,
-                                                          const float* __restrict__ radii, uint64_t T, int W, int S,
-                                                          float margin, float* __restrict__ cost,
-                                                          float* __restrict__ dist, int32_t* __restrict__ argmin) {
+__global__ void __launch_bounds__(512, 2) k_clearance_dist(DevArgs t, const float* __restrict__ centers, int W,
+                                                           int S, float* __restrict__ dist,
+                                                           int32_t* __restrict__ argmin) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t bar;
-    __shared__ float rm[64];    // r_s + margin
-    for (int i = (int)threadIdx.x; i < S; i += (int)blockDim.x) rm[i] = __fadd_rn(radii[i], margin);
     const float* Ts = nullptr;
     uint32_t off = 0;
     if constexpr (STAGE) {
         Ts = stage_splits(t, smem_raw, &bar);   // contains a block barrier
         off = stage_offset(t);
-    } else {
-        __syncthreads();
     }
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const uint32_t lt_mask = (1u << lane) - 1u;
     ClearScratch* ws = reinterpret_cast<ClearScratch*>(smem_raw + off) + warp;
-    float* partial = reinterpret_cast<float*>(smem_raw + off + sizeof(ClearScratch) * nw);   // [W]
     const float rmax = t.r_max, rmax2 = __fmul_rn(t.r_max, t.r_max);
     const float4 rlo = make_float4(t.lo[0], t.lo[1], t.lo[2], 0.f);
     const float4 rhi = make_float4(t.hi[0], t.hi[1], t.hi[2], 0.f);
     // one trajectory per block (the grid covers them all, so the hardware hands out
-    // blocks as earlier ones finish); warp k owns a contiguous range of waypoints
+    // blocks as earlier ones finish); warp k owns a contiguous range of waypoints, whose
+    // spheres are close in space, so the block's warps share set blocks in L1
     const uint64_t traj = blockIdx.x;
     const uint32_t w_lo = (uint32_t)(((uint64_t)W * warp) / nw), w_hi = (uint32_t)(((uint64_t)W * (warp + 1)) / nw);
     const uint64_t tbase = traj * (uint64_t)W * (uint64_t)S;        // first sphere of the trajectory
@@ -173,7 +170,7 @@ __global__ void __launch_bounds__(512, 2) k_clearance_fwd(DevArgs t, const float
             if (near) {
                 const uint32_t pos = n_q + __popc(mask & lt_mask);
                 ws->nq[pos] = make_float4(x, y, z, 0.f);
-                ws->ni[pos] = i0 + k;
+                ws->ni[pos] = tbase + i0 + k;
             }
             n_q += __popc(mask);
         }
@@ -183,17 +180,17 @@ __global__ void __launch_bounds__(512, 2) k_clearance_fwd(DevArgs t, const float
             for (; n_q - r0 >= 32; r0 += 32) {
                 if (r0) {
                     const float4 cc = ws->nq[r0 + lane];
-                    const uint32_t ii = ws->ni[r0 + lane];
+                    const unsigned long long ii = ws->ni[r0 + lane];
                     __syncwarp();
                     ws->nq[lane] = cc;
                     ws->ni[lane] = ii;
                     __syncwarp();
                 }
-                clearance_round(t, Ts, ws, 32, tbase, rmax, rmax2, dist, argmin, lane, lt_mask);
+                clearance_round(t, Ts, ws, 32, 0, rmax, rmax2, dist, argmin, lane, lt_mask);
             }
             const uint32_t rest = n_q - r0;
             float4 cc = make_float4(0.f, 0.f, 0.f, 0.f);
-            uint32_t ii = 0;
+            unsigned long long ii = 0;
             if (lane < rest) {
                 cc = ws->nq[r0 + lane];
                 ii = ws->ni[r0 + lane];
@@ -209,26 +206,38 @@ __global__ void __launch_bounds__(512, 2) k_clearance_fwd(DevArgs t, const float
     }
     if (n_q) {
         __syncwarp();
-        clearance_round(t, Ts, ws, n_q, tbase, rmax, rmax2, dist, argmin, lane, lt_mask);
+        clearance_round(t, Ts, ws, n_q, 0, rmax, rmax2, dist, argmin, lane, lt_mask);
     }
-    __syncwarp();
-    // per-waypoint cost in a fixed order: sphere s = lane + 32 m summed by lane, then a
-    // butterfly; the block then sums the waypoints in order
-    for (uint32_t w = w_lo; w < w_hi; w++) {
-        float term = 0.f;
-        for (uint32_t s = lane; s < (uint32_t)S; s += 32) {
-            const float hh = fmaxf(0.f, __fsub_rn(rm[s], dist[tbase + (uint64_t)w * S + s]));
-            term = __fadd_rn(term, __fmul_rn(hh, hh));
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) term = __fadd_rn(term, __shfl_xor_sync(0xffffffffu, term, o));
-        if (lane == 0) partial[w] = term;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
+}
+
+// Cost per trajectory from the written distances, one warp per trajectory, in a fixed
+// order: per waypoint, sphere s = lane + 32 m summed by its lane, then a butterfly; lane 0
+// adds the waypoints in order.  The result does not depend on the launch configuration.
+__global__ void k_clearance_cost(const float* __restrict__ radii, const float* __restrict__ dist, uint64_t T, int W,
+                                 int S, float margin, float* __restrict__ cost) {
+    const uint32_t lane = lane_id();
+    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    float rm0 = 0.f, rm1 = 0.f;   // r_s + margin for s = lane, lane + 32
+    if (lane < (uint32_t)S) rm0 = __fadd_rn(radii[lane], margin);
+    if (lane + 32 < (uint32_t)S) rm1 = __fadd_rn(radii[lane + 32], margin);
+    for (uint64_t traj = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); traj < T; traj += nwarps) {
+        const float* d = dist + traj * (uint64_t)W * (uint64_t)S;
         float acc = 0.f;
-        for (int w = 0; w < W; w++) acc = __fadd_rn(acc, partial[w]);
-        cost[traj] = acc;
+        for (int w = 0; w < W; w++) {
+            float term = 0.f;
+            if (lane < (uint32_t)S) {
+                const float hh = fmaxf(0.f, __fsub_rn(rm0, __ldg(d + (uint64_t)w * S + lane)));
+                term = __fadd_rn(term, __fmul_rn(hh, hh));
+            }
+            if (lane + 32 < (uint32_t)S) {
+                const float hh = fmaxf(0.f, __fsub_rn(rm1, __ldg(d + (uint64_t)w * S + lane + 32)));
+                term = __fadd_rn(term, __fmul_rn(hh, hh));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) term = __fadd_rn(term, __shfl_xor_sync(0xffffffffu, term, o));
+            acc = __fadd_rn(acc, term);
+        }
+        if (lane == 0) cost[traj] = acc;
     }
 }
 
@@ -265,12 +274,14 @@ int launch_clearance_fwd(const DevArgs& t, const float* centers, const float* ra
     if (W > 8192) { err = "clearance takes at most 8192 waypoints per trajectory"; return CAPT_E_ARG; }
     if (T > 0x7fffffffull) { err = "too many trajectories for one launch"; return CAPT_E_ARG; }
     const bool stage = cfg.staging == CAPT_STAGE_SMEM && t.stage_floats > 0;
-    auto fn = stage ? k_clearance_fwd<true> : k_clearance_fwd<false>;
+    auto fn = stage ? k_clearance_dist<true> : k_clearance_dist<false>;
     const int warps = std::max(1, std::min(16, std::min((int)cfg.warps_per_block, W)));
-    const size_t smem = (stage ? stage_offset(t) : 0u) + sizeof(ClearScratch) * (size_t)warps + sizeof(float) * (size_t)W;
+    const size_t smem = (stage ? stage_offset(t) : 0u) + sizeof(ClearScratch) * (size_t)warps;
     cudaError_t ce = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (ce != cudaSuccess) { err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
-    fn<<<(unsigned)T, warps * 32, smem, st>>>(t, centers, radii, T, W, S, margin, cost, dist, argmin);
+    fn<<<(unsigned)T, warps * 32, smem, st>>>(t, centers, W, S, dist, argmin);
+    const uint64_t cost_blocks = std::min<uint64_t>((T + 7) / 8, (uint64_t)sm_count() * 16);
+    k_clearance_cost<<<(unsigned)cost_blocks, 256, 0, st>>>(radii, dist, T, W, S, margin, cost);
     ce = cudaGetLastError();
     if (ce != cudaSuccess) { err = std::string("clearance launch: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
     return CAPT_OK;
