@@ -482,6 +482,24 @@ def extra_workloads(capt, torch, dev, stream, pts, arm, args):
     res["clearance"] = {"spheres": m, "fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "fwd_spheres_per_s": m / (fwd_ms / 1e3),
                         "fwd_bwd_spheres_per_s": m / ((fwd_ms + bwd_ms) / 1e3),
                         "bwd_hbm_GBps": m * (12 + 4 + 4 + 12 + 12) / (bwd_ms / 1e3) / 1e9}
+    # depth frame -> tree, host and device (the paper's Table III setting: a 640 x 480
+    # frame of 307,200 points, r_filter 1 / 1.5 / 2 cm, r_min 1.5 cm, r_max 8 cm)
+    frame = W.depth_frame()
+    df = torch.from_numpy(frame).to(dev)
+    rows = []
+    for rf in (0.01, 0.015, 0.02):
+        kept = capt.sfc_filter(frame, rf)
+        t0 = time.perf_counter()
+        tr_h = capt.capt_build(frame[kept], 0.015, 0.08)
+        hb = (time.perf_counter() - t0) * 1e3
+        kd = capt.sfc_filter_device(df, rf)
+        same = bool(np.array_equal(kd.cpu().numpy().astype(np.uint32), kept))
+        rows.append({"r_filter": rf, "kept": int(len(kept)), "host_filter_ms": host_filter_ms(capt, frame, rf),
+                     "host_build_ms": hb, "device_filter_ms": device_filter_ms(capt, frame, rf, reps=3),
+                     "device_build_ms": device_build_ms(capt, frame[kept], 0.015, 0.08, reps=3),
+                     "device_filter_equals_host": same,
+                     "total_afforded": int(capt.capt_stats(tr_h)["total_afforded"])})
+    res["depth_frame_to_tree"] = {"points": int(len(frame)), "rows": rows}
     # uniform 2k cloud, 100,000 spheres
     pu = W.uniform_cloud(2000, 1000)
     cu, ru = W.cube_queries(100_000, 1000)

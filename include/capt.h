@@ -116,11 +116,16 @@ int capt_morton_order(const float* points, size_t n, uint32_t* order);
  * first later point farther than min_spacing from p_j), marked by pointer doubling.
  * d_points: device float[n][3] on the current device; d_kept: device uint32[n]
  * (caller-owned) receives the kept indices in the last pass's curve order; *n_out
- * (host) their count.  Work is stream-ordered on `stream`; the call synchronises it
- * twice (finite check, count) and allocates and frees its temporaries with
- * cudaMallocAsync / cudaFreeAsync on it.  The sweep costs the lengths of the runs of
- * points within min_spacing of each other along the curve (quadratic in a run of
- * coincident points).
+ * (host) their count.  Work is stream-ordered on `stream` and the call synchronises it
+ * once (for the count).  The launch sequence of a call depends on n and min_spacing
+ * only: the first call for a (device, n, min_spacing) captures it into a CUDA graph
+ * with its own buffers (about 90 bytes per point), and later calls of the same size
+ * (frame after frame) replay it.  The library keeps the four most recently used such
+ * plans until the process exits; calls from several host threads are serialised.
+ * Make the first call of a size outside any stream capture of the caller's.  The sweep
+ * costs the lengths of the runs of points within min_spacing of each other along the
+ * curve (quadratic in a run of coincident points).  On an error the contents of d_kept
+ * are unspecified.
  * Errors: CAPT_E_ARG (NULL pointer, n >= 2^31), CAPT_E_RANGE (min_spacing < 0 or NaN),
  *         CAPT_E_NONFINITE, CAPT_E_NOMEM, CAPT_E_CUDA. */
 int sfc_filter_device(const float* d_points, size_t n, float min_spacing, uint32_t* d_kept, size_t* n_out,

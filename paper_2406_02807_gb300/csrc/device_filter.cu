@@ -22,6 +22,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
+#include <mutex>
 #include <string>
 
 #include "capt_internal.h"
@@ -272,7 +274,7 @@ __global__ void kf_next(const float* __restrict__ xs, const float* __restrict__ 
         const float dy = __fsub_rn(ay, ys[k]);
         const float dz = __fsub_rn(az, zs[k]);
         const float s = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-        if (s > r2) break;
+        if (!(s <= r2)) break;   // s > r2 for finite input; a NaN (rejected input) also stops
     }
     next[j] = k;
     mark[j] = j == 0 ? 1 : 0;
@@ -300,6 +302,12 @@ __global__ void kf_survive(const uint8_t* __restrict__ mark, const uint32_t* __r
     if (j < *d_m) alive[val[j]] = mark[j];
 }
 
+// box[0..2] = lo keys, box[3..5] = hi keys (empty), box[6] = non-finite flag, box[7] =
+// kept count (written at the end)
+__global__ void kf_box_init(uint32_t* __restrict__ box) {
+    if (threadIdx.x < 8) box[threadIdx.x] = threadIdx.x < 3 ? 0xffffffffu : 0u;
+}
+
 __global__ void kf_fill_u8(uint8_t* __restrict__ p, uint32_t n, uint8_t v) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) p[i] = v;
@@ -308,6 +316,162 @@ __global__ void kf_fill_u8(uint8_t* __restrict__ p, uint32_t n, uint8_t v) {
 const int kPerm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
 
 unsigned blocks_of(uint64_t work, unsigned per) { return (unsigned)std::max<uint64_t>(1, (work + per - 1) / per); }
+
+
+// Buffers of one filter plan, carved from one allocation.
+struct FilterBufs {
+    float* in = nullptr;          // copy of the input points [n][3]
+    uint32_t* kept = nullptr;     // kept indices (n slots)
+    uint32_t* box = nullptr;      // kf_box_init layout; box[6] non-finite, box[7] count
+    uint32_t* d_m = nullptr;
+    uint32_t* counts = nullptr;
+    uint32_t* hist = nullptr;
+    uint64_t* sp = nullptr;
+    uint8_t* alive = nullptr;
+    uint8_t* mark = nullptr;
+    uint32_t* w[11] = {};
+    uint32_t nblk = 0;
+};
+
+size_t carve(char* buf, size_t n, FilterBufs* b) {
+    const uint32_t nblk = blocks_of(n, kFTile);
+    size_t total = 0;
+    auto take = [&](size_t bytes) { const size_t o = total; total += (bytes + 255) & ~size_t(255); return o; };
+    const size_t o_in = take(12 * n), o_kept = take(4 * n), o_box = take(8 * 4), o_m = take(4);
+    const size_t o_counts = take(4 * (size_t)nblk), o_hist = take(4 * 256 * (size_t)nblk), o_sp = take(24 * n);
+    const size_t o_alive = take(n), o_mark = take(n);
+    size_t o_w[11];
+    for (auto& o : o_w) o = take(4 * n);   // asc, klo/khi/val x 2, xs, ys, zs, next/jump
+    if (buf && b) {
+        auto U = [&](size_t o) { return reinterpret_cast<uint32_t*>(buf + o); };
+        b->in = reinterpret_cast<float*>(buf + o_in);
+        b->kept = U(o_kept);
+        b->box = U(o_box);
+        b->d_m = U(o_m);
+        b->counts = U(o_counts);
+        b->hist = U(o_hist);
+        b->sp = reinterpret_cast<uint64_t*>(buf + o_sp);
+        b->alive = reinterpret_cast<uint8_t*>(buf + o_alive);
+        b->mark = reinterpret_cast<uint8_t*>(buf + o_mark);
+        for (int k = 0; k < 11; k++) b->w[k] = U(o_w[k]);
+        b->nblk = nblk;
+    }
+    return total;
+}
+
+// Every launch of one filter call on b (no host synchronisation, no host memory): the
+// sequence depends on n and r only, so it is captured once into a CUDA graph.
+void enqueue_filter(const FilterBufs& b, uint32_t n, float r, cudaStream_t st) {
+    const uint32_t nblk = b.nblk;
+    uint32_t* asc = b.w[0];
+    uint32_t* ka[2] = {b.w[1], b.w[4]};
+    uint32_t* kb[2] = {b.w[2], b.w[5]};
+    uint32_t* vv[2] = {b.w[3], b.w[6]};
+    float* xs = reinterpret_cast<float*>(b.w[7]);
+    float* ys = reinterpret_cast<float*>(b.w[8]);
+    float* zs = reinterpret_cast<float*>(b.w[9]);
+    uint32_t* jmp[2] = {b.w[10], asc};   // asc is free once the keys are made
+    const unsigned gn = blocks_of(n, kFT);
+    kf_box_init<<<1, 32, 0, st>>>(b.box);
+    kf_bbox<<<std::min(gn, 1024u), kFT, 0, st>>>(b.in, n, b.box);
+    kf_spread<<<gn, kFT, 0, st>>>(b.in, n, b.box, b.sp);
+    kf_fill_u8<<<gn, kFT, 0, st>>>(b.alive, n, 1);
+    int doublings = 0;   // 2^doublings >= n: enough rounds of pointer doubling for any chain
+    while ((1ull << doublings) < n) doublings++;
+    const float r2 = r * r;   // fl(r^2), as the host filter
+    for (int p = 0; p < 6; p++) {
+        // survivors in ascending index order; m = their count
+        kf_flag_count<<<nblk, kFT, 0, st>>>(b.alive, nullptr, n, b.counts);
+        kf_scan<<<1, kScanThreads, 0, st>>>(b.counts, nblk, b.d_m);
+        kf_flag_compact<<<nblk, kFT, 0, st>>>(b.alive, nullptr, n, b.counts, nullptr, asc);
+        kf_keys<<<gn, kFT, 0, st>>>(asc, b.d_m, b.sp, kPerm[p][0], kPerm[p][1], kPerm[p][2], ka[0], kb[0], vv[0]);
+        // stable sort by the low word, then by the high word (4 digits each)
+        int cur = 0;
+        for (int word = 0; word < 2; word++)
+            for (int shift = 0; shift < 32; shift += 8) {
+                const uint32_t* kw = word == 0 ? ka[cur] : kb[cur];
+                const uint32_t* ko = word == 0 ? kb[cur] : ka[cur];
+                uint32_t* kw_o = word == 0 ? ka[cur ^ 1] : kb[cur ^ 1];
+                uint32_t* ko_o = word == 0 ? kb[cur ^ 1] : ka[cur ^ 1];
+                kf_hist<<<nblk, kFT, 0, st>>>(kw, b.d_m, shift, b.hist, nblk);
+                kf_scan<<<1, kScanThreads, 0, st>>>(b.hist, 256 * nblk, nullptr);
+                kf_scatter<<<nblk, kFT, 0, st>>>(kw, ko, vv[cur], b.d_m, shift, b.hist, nblk, kw_o, ko_o, vv[cur ^ 1]);
+                cur ^= 1;
+            }
+        const uint32_t* val = vv[cur];
+        // greedy sweep as a chain, marked by pointer doubling
+        kf_gather<<<gn, kFT, 0, st>>>(val, b.d_m, b.in, xs, ys, zs);
+        kf_next<<<gn, kFT, 0, st>>>(xs, ys, zs, b.d_m, r2, jmp[0], b.mark);
+        int j = 0;
+        for (int k = 0; k < doublings; k++, j ^= 1) kf_double<<<gn, kFT, 0, st>>>(jmp[j], jmp[j ^ 1], b.d_m, b.mark);
+        if (p < 5) {
+            kf_survive<<<gn, kFT, 0, st>>>(b.mark, val, b.d_m, b.alive);
+        } else {
+            kf_flag_count<<<nblk, kFT, 0, st>>>(b.mark, b.d_m, n, b.counts);
+            kf_scan<<<1, kScanThreads, 0, st>>>(b.counts, nblk, b.box + 7);
+            kf_flag_compact<<<nblk, kFT, 0, st>>>(b.mark, b.d_m, n, b.counts, val, b.kept);
+        }
+    }
+}
+
+// A captured filter for one (device, n, r): its own buffers and graph.  A few are kept
+// (least recently used out first), so that filtering frame after frame of one size costs
+// one graph launch and two small copies.
+struct FilterPlan {
+    int dev = -1;
+    size_t n = 0;
+    uint32_t r_bits = 0;
+    char* buf = nullptr;
+    FilterBufs b;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t used = 0;
+    void release() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (buf) cudaFree(buf);
+        exec = nullptr;
+        buf = nullptr;
+    }
+};
+
+constexpr int kPlans = 4;
+std::mutex g_plan_mu;
+FilterPlan g_plans[kPlans];
+uint64_t g_plan_clock = 0;
+
+int make_plan(FilterPlan& pl, int dev, size_t n, float r, std::string& err) {
+    pl.release();
+    pl.dev = dev;
+    pl.n = n;
+    std::memcpy(&pl.r_bits, &r, 4);
+    const size_t bytes = carve(nullptr, n, nullptr);
+    if (cudaMalloc((void**)&pl.buf, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        pl.buf = nullptr;
+        pl.n = 0;
+        err = "device allocation failed in the filter";
+        return CAPT_E_NOMEM;
+    }
+    carve(pl.buf, n, &pl.b);
+    cudaStream_t cs = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (ce == cudaSuccess) {
+        enqueue_filter(pl.b, (uint32_t)n, r, cs);
+        ce = cudaStreamEndCapture(cs, &g);
+    }
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&pl.exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (cs) cudaStreamDestroy(cs);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        pl.release();
+        pl.n = 0;
+        err = std::string("filter graph: ") + cudaGetErrorString(ce);
+        return CAPT_E_CUDA;
+    }
+    return CAPT_OK;
+}
 
 }  // namespace
 
@@ -318,112 +482,36 @@ int device_sfc_filter(const float* d_points, size_t n, float r, uint32_t* d_kept
     if (n >= (size_t(1) << 31)) { err = "the device filter takes fewer than 2^31 points"; return CAPT_E_ARG; }
     *n_out = 0;
     if (n == 0) return CAPT_OK;
-    const uint32_t un = (uint32_t)n;
-    const uint32_t nblk = blocks_of(n, kFTile);
-    // one allocation, carved into 256-byte aligned pieces
-    size_t total = 0;
-    auto take = [&](size_t bytes) { const size_t o = total; total += (bytes + 255) & ~size_t(255); return o; };
-    const size_t o_box = take(8 * 4), o_m = take(4), o_cnt = take(4), o_counts = take(4 * (size_t)nblk);
-    const size_t o_hist = take(4 * 256 * (size_t)nblk), o_sp = take(24 * n), o_alive = take(n), o_mark = take(n);
-    size_t o_w[11];
-    for (auto& o : o_w) o = take(4 * n);   // asc, klo/khi/val x 2, xs, ys, zs, next/jump
-    char* buf = nullptr;
-    cudaError_t ce = cudaMallocAsync((void**)&buf, total, st);
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) { err = std::string("cudaGetDevice: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
+    uint32_t r_bits;
+    std::memcpy(&r_bits, &r, 4);
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    FilterPlan* pl = nullptr;
+    for (auto& p : g_plans)
+        if (p.exec && p.dev == dev && p.n == n && p.r_bits == r_bits) pl = &p;
+    if (!pl) {
+        pl = &g_plans[0];
+        for (auto& p : g_plans)
+            if (!p.exec || p.used < pl->used) pl = &p;
+        const int rc = make_plan(*pl, dev, n, r, err);
+        if (rc) return rc;
+    }
+    pl->used = ++g_plan_clock;
+    uint32_t res[2] = {0u, 0u};
+    ce = cudaMemcpyAsync(pl->b.in, d_points, 12 * n, cudaMemcpyDeviceToDevice, st);
+    if (ce == cudaSuccess) ce = cudaGraphLaunch(pl->exec, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(d_kept, pl->b.kept, 4 * n, cudaMemcpyDeviceToDevice, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(res, pl->b.box + 6, sizeof(res), cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) {
         cudaGetLastError();
-        err = "device allocation failed in the filter";
-        return CAPT_E_NOMEM;
+        err = std::string("filter: ") + cudaGetErrorString(ce);
+        return CAPT_E_CUDA;
     }
-    auto U = [&](size_t o) { return reinterpret_cast<uint32_t*>(buf + o); };
-    uint32_t* box = U(o_box);
-    uint32_t* d_m = U(o_m);
-    uint32_t* d_cnt = U(o_cnt);
-    uint32_t* counts = U(o_counts);
-    uint32_t* hist = U(o_hist);
-    uint64_t* sp = reinterpret_cast<uint64_t*>(buf + o_sp);
-    uint8_t* alive = reinterpret_cast<uint8_t*>(buf + o_alive);
-    uint8_t* mark = reinterpret_cast<uint8_t*>(buf + o_mark);
-    uint32_t* asc = U(o_w[0]);
-    uint32_t* ka[2] = {U(o_w[1]), U(o_w[4])};
-    uint32_t* kb[2] = {U(o_w[2]), U(o_w[5])};
-    uint32_t* vv[2] = {U(o_w[3]), U(o_w[6])};
-    float* xs = reinterpret_cast<float*>(U(o_w[7]));
-    float* ys = reinterpret_cast<float*>(U(o_w[8]));
-    float* zs = reinterpret_cast<float*>(U(o_w[9]));
-    uint32_t* jmp[2] = {U(o_w[10]), asc};   // asc is free once the keys are made
-    int rc = CAPT_OK;
-    auto check = [&](const char* what) {
-        if (rc) return false;
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) { err = std::string(what) + ": " + cudaGetErrorString(e); rc = CAPT_E_CUDA; }
-        return rc == CAPT_OK;
-    };
-    uint32_t hbox[8];
-    const uint32_t box0[8] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u, 0u, 0u};
-    const unsigned gn = blocks_of(n, kFT);
-    ce = cudaMemcpyAsync(box, box0, sizeof(box0), cudaMemcpyHostToDevice, st);
-    if (ce == cudaSuccess) {
-        kf_bbox<<<std::min(gn, 1024u), kFT, 0, st>>>(d_points, un, box);
-        ce = cudaMemcpyAsync(hbox, box, sizeof(hbox), cudaMemcpyDeviceToHost, st);
-    }
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-    if (ce != cudaSuccess) { err = std::string("filter bounding box: ") + cudaGetErrorString(ce); rc = CAPT_E_CUDA; }
-    if (!rc && hbox[6]) { err = "non-finite coordinate in points"; rc = CAPT_E_NONFINITE; }
-    if (!rc) {
-        kf_spread<<<gn, kFT, 0, st>>>(d_points, un, box, sp);
-        kf_fill_u8<<<gn, kFT, 0, st>>>(alive, un, 1);
-        check("filter setup");
-    }
-    int rounds = 0;
-    while ((1ull << rounds) < n) rounds++;
-    const float r2 = r * r;   // fl(r^2), as the host filter
-    for (int p = 0; p < 6 && !rc; p++) {
-        // survivors in ascending index order; m = their count
-        kf_flag_count<<<nblk, kFT, 0, st>>>(alive, nullptr, un, counts);
-        kf_scan<<<1, kScanThreads, 0, st>>>(counts, nblk, d_m);
-        kf_flag_compact<<<nblk, kFT, 0, st>>>(alive, nullptr, un, counts, nullptr, asc);
-        kf_keys<<<gn, kFT, 0, st>>>(asc, d_m, sp, kPerm[p][0], kPerm[p][1], kPerm[p][2], ka[0], kb[0], vv[0]);
-        // stable sort by the low word, then by the high word (4 digits each)
-        int cur = 0;
-        for (int word = 0; word < 2; word++)
-            for (int shift = 0; shift < 32; shift += 8) {
-                const uint32_t* kw = word == 0 ? ka[cur] : kb[cur];
-                const uint32_t* ko = word == 0 ? kb[cur] : ka[cur];
-                uint32_t* kw_o = word == 0 ? ka[cur ^ 1] : kb[cur ^ 1];
-                uint32_t* ko_o = word == 0 ? kb[cur ^ 1] : ka[cur ^ 1];
-                kf_hist<<<nblk, kFT, 0, st>>>(kw, d_m, shift, hist, nblk);
-                kf_scan<<<1, kScanThreads, 0, st>>>(hist, 256 * nblk, nullptr);
-                kf_scatter<<<nblk, kFT, 0, st>>>(kw, ko, vv[cur], d_m, shift, hist, nblk, kw_o, ko_o, vv[cur ^ 1]);
-                cur ^= 1;
-            }
-        const uint32_t* val = vv[cur];
-        // greedy sweep as a chain, marked by pointer doubling
-        kf_gather<<<gn, kFT, 0, st>>>(val, d_m, d_points, xs, ys, zs);
-        kf_next<<<gn, kFT, 0, st>>>(xs, ys, zs, d_m, r2, jmp[0], mark);
-        int j = 0;
-        for (int k = 0; k < rounds; k++, j ^= 1) kf_double<<<gn, kFT, 0, st>>>(jmp[j], jmp[j ^ 1], d_m, mark);
-        if (p < 5) {
-            kf_survive<<<gn, kFT, 0, st>>>(mark, val, d_m, alive);
-        } else {
-            kf_flag_count<<<nblk, kFT, 0, st>>>(mark, d_m, un, counts);
-            kf_scan<<<1, kScanThreads, 0, st>>>(counts, nblk, d_cnt);
-            kf_flag_compact<<<nblk, kFT, 0, st>>>(mark, d_m, un, counts, val, d_kept);
-        }
-        check("filter pass");
-    }
-    uint32_t kept = 0;
-    if (!rc) {
-        ce = cudaMemcpyAsync(&kept, d_cnt, 4, cudaMemcpyDeviceToHost, st);
-        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-        if (ce != cudaSuccess) { err = std::string("filter result: ") + cudaGetErrorString(ce); rc = CAPT_E_CUDA; }
-    }
-    cudaFreeAsync(buf, st);
-    if (rc) {
-        cudaStreamSynchronize(st);
-        cudaGetLastError();
-        return rc;
-    }
-    *n_out = kept;
+    if (res[0]) { err = "non-finite coordinate in points"; return CAPT_E_NONFINITE; }
+    *n_out = res[1];
     return CAPT_OK;
 }
 

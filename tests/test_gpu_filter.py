@@ -71,6 +71,14 @@ def test_filter_room(orc, capt_lib, torch_):
     _same(orc, capt_lib, torch_, pts, 0.02)
 
 
+@pytest.mark.parametrize("rf", [0.01, 0.02])
+def test_filter_depth_frame(orc, capt_lib, torch_, rf):
+    """A 640 x 480 depth frame (307,200 points): device, host and oracle agree."""
+    frame = W.depth_frame()
+    ref = _same(orc, capt_lib, torch_, frame, rf)
+    assert np.array_equal(ref, capt_lib.sfc_filter(frame, rf))
+
+
 def test_filter_errors_and_empty(capt_lib, torch_):
     assert _gpu_filter(capt_lib, torch_, np.zeros((0, 3), np.float32), 0.01).size == 0
     bad = W.uniform_cloud(100, 1)

@@ -155,3 +155,11 @@ def test_morton_order_follows_the_oracles_curve(orc, capt_lib):
     with pytest.raises(capt_lib.CaptError) as e:
         capt_lib.capt_morton_order(bad)
     assert e.value.status == -3
+
+
+def test_depth_frame_is_a_full_deterministic_frame():
+    f = W.depth_frame()
+    assert f.shape == (640 * 480, 3) and f.dtype == np.float32 and np.all(np.isfinite(f))
+    assert np.array_equal(f, W.depth_frame())
+    # the camera looks down at the table: most pixels see the table top or what is on it
+    assert ((f[:, 2] > -0.01) & (f[:, 0] >= -0.01) & (f[:, 0] <= 1.21)).mean() > 0.5

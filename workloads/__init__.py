@@ -25,7 +25,7 @@ import numpy as np
 
 __all__ = [
     "Stream", "ArmModel", "arm_7dof", "fk_centers",
-    "uniform_cloud", "tabletop_cloud", "room_cloud",
+    "uniform_cloud", "tabletop_cloud", "room_cloud", "depth_frame",
     "cube_queries", "room_queries", "random_configs", "random_edges",
     "random_trajectories", "WORKLOADS",
 ]
@@ -232,6 +232,79 @@ def room_cloud(seed: int, n: int = 200000, sigma: float = 0.003):
     pts = _sample_rects(rects, areas, n, Stream(seed, P_POINTS))
     pts += sigma * Stream(seed, P_NOISE).normal(3 * n).reshape(n, 3)
     return pts.astype(np.float32)
+
+
+def depth_frame(seed: int = 1001, width: int = 640, height: int = 480, sigma: float = 0.002,
+                cam=(0.6, 0.0, 0.6), target=(0.7, 0.0, 0.0), hfov_deg: float = 87.0):
+    """A depth-camera frame of the tabletop scene: one point per pixel of a pinhole camera
+    (640 x 480, 87 degree horizontal field of view, as a RealSense D455's depth stream)
+    0.6 m above the table looking down at it, where the pixel's ray first meets the
+    scene (307,200 points, the size of the paper's real-robot frames, Table III; the
+    Morton filter keeps 34,892 / 15,703 / 7,900 of them at 1 / 1.5 / 2 cm).
+
+    The scene is the tabletop layout of `tabletop_cloud(seed)` (table top, boxes,
+    vertical cylinders) inside a room that catches every other ray: a floor at
+    z = -0.75, a back wall at x = 2.5 and side walls at y = +-1.5 (no ceiling is needed:
+    the camera looks down).  Each point is perturbed along its ray by N(0, sigma^2).
+    Returns float32 [height * width, 3], row-major over the image.
+    """
+    _, layout = tabletop_cloud(seed, n=1)
+    o = np.asarray(cam, np.float64)
+    fwd = np.asarray(target, np.float64) - o
+    fwd /= np.linalg.norm(fwd)
+    right = np.cross(fwd, [0.0, 0.0, 1.0])
+    right /= np.linalg.norm(right)
+    up = np.cross(right, fwd)
+    fx = (width / 2) / math.tan(math.radians(hfov_deg) / 2)
+    u = (np.arange(width) + 0.5 - width / 2) / fx
+    v = (np.arange(height) + 0.5 - height / 2) / fx
+    uu, vv = np.meshgrid(u, v)
+    d = fwd[None, None, :] + uu[..., None] * right[None, None, :] - vv[..., None] * up[None, None, :]
+    d = d.reshape(-1, 3)
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        best = np.full(len(d), np.inf)
+
+        def take(t, ok):
+            t = np.where(ok & (t > 1e-9), t, np.inf)
+            np.minimum(best, t, out=best)
+
+        def plane(axis, value, lo=None, hi=None):
+            t = (value - o[axis]) / d[:, axis]
+            ok = np.isfinite(t)
+            if lo is not None:
+                p = o[None, :] + t[:, None] * d
+                for a in range(3):
+                    if a != axis:
+                        ok &= (p[:, a] >= lo[a]) & (p[:, a] <= hi[a])
+            take(t, ok)
+
+        plane(2, 0.0, (0.0, -0.4, 0.0), (1.2, 0.4, 0.0))          # table top
+        plane(2, -0.75)                                            # floor
+        plane(0, 2.5)                                              # back wall
+        plane(1, 1.5)
+        plane(1, -1.5)                                             # side walls
+        for lo, hi in layout["boxes"]:
+            lo, hi = np.asarray(lo, np.float64), np.asarray(hi, np.float64)
+            t0 = (lo[None, :] - o[None, :]) / d
+            t1 = (hi[None, :] - o[None, :]) / d
+            tn = np.max(np.minimum(t0, t1), axis=1)
+            tf = np.min(np.maximum(t0, t1), axis=1)
+            take(tn, tn <= tf)
+        for cx, cy, r, h in layout["cylinders"]:
+            ox, oy = o[0] - cx, o[1] - cy
+            a = d[:, 0] ** 2 + d[:, 1] ** 2
+            b = 2 * (ox * d[:, 0] + oy * d[:, 1])
+            c = ox * ox + oy * oy - r * r
+            disc = b * b - 4 * a * c
+            t = (-b - np.sqrt(np.maximum(disc, 0.0))) / (2 * a)
+            z = o[2] + t * d[:, 2]
+            take(t, (disc >= 0) & (z >= 0) & (z <= h))
+            t = (h - o[2]) / d[:, 2]
+            px, py = o[0] + t * d[:, 0] - cx, o[1] + t * d[:, 1] - cy
+            take(t, px * px + py * py <= r * r)
+    t = best + sigma * Stream(seed + 4, P_NOISE).normal(len(d))
+    return (o[None, :] + t[:, None] * d).astype(np.float32)
 
 
 # --------------------------------------------------------------------------------------
