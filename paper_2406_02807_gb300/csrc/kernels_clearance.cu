@@ -11,10 +11,11 @@
 //     blocks in L1); passes of 128 consecutive spheres (4 per lane, three 16-byte
 //     loads): a sphere farther than r_max from the cloud's bounding box is farther than
 //     r_max from every point, so it gets d = r_max, argmin = -1 at once; the others are
-//     queued.  No block barrier: a warp leaves as soon as its range is done.  Rounds of 32 queued spheres: descent and leaf box test against r_max;
-//     each set of a sphere that passes is scanned in full by the whole warp in packed
-//     FP32x2 arithmetic, every lane keeping a running minimum of (d^2, slot) keys,
-//     reduced by one butterfly per set.
+//     queued.  No block barrier: a warp leaves as soon as its range is done.  Rounds
+//     of 32 queued spheres: descent and leaf box test against r_max; each set of a
+//     sphere that passes is scanned in full by the whole warp in packed FP32x2
+//     arithmetic, every lane keeping a running minimum of (d^2, slot) keys, reduced by
+//     one butterfly per set.
 //  2. Costs (k_clearance_cost): one warp per trajectory sums each waypoint's terms in a
 //     fixed order (lane-strided, then a butterfly) and adds the waypoints in order, so
 //     the cost is bitwise reproducible whatever the launch configuration.
