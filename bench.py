@@ -176,6 +176,20 @@ def host_filter_ms(capt, raw, r, reps=3):
     return statistics.median(ts)
 
 
+def frame_to_tree_ms(capt, d_points, rf, r_min, r_max, reps=3):
+    """Median wall time of capt_build_frame_device (filter + gather + build in one call,
+    points already on the device), after one untimed call."""
+    import torch
+    capt.capt_build_frame_device(d_points, rf, r_min, r_max)
+    ts = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        capt.capt_build_frame_device(d_points, rf, r_min, r_max)
+        ts.append((time.perf_counter() - t0) * 1e3)
+    return statistics.median(ts)
+
+
 def device_filter_ms(capt, raw, r, reps=5):
     """Median wall time of sfc_filter_device (points already on the device; the call
     returns with the kept count on the host), after one untimed call."""
@@ -498,6 +512,7 @@ def extra_workloads(capt, torch, dev, stream, pts, arm, args):
                      "host_build_ms": hb, "device_filter_ms": device_filter_ms(capt, frame, rf, reps=3),
                      "device_build_ms": device_build_ms(capt, frame[kept], 0.015, 0.08, reps=3),
                      "device_filter_equals_host": same,
+                     "device_frame_to_tree_ms": frame_to_tree_ms(capt, df, rf, 0.015, 0.08),
                      "total_afforded": int(capt.capt_stats(tr_h)["total_afforded"])})
     res["depth_frame_to_tree"] = {"points": int(len(frame)), "rows": rows}
     # uniform 2k cloud, 100,000 spheres

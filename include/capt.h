@@ -186,6 +186,17 @@ int capt_upload(capt_tree* t, int device, void* stream);
  *         CAPT_E_NONFINITE, CAPT_E_NOMEM, CAPT_E_CUDA. */
 int capt_build_device(const float* d_points, size_t n, float r_min, float r_max, void* stream, capt_tree** out);
 
+/* A raw cloud (e.g. one depth frame) to an uploaded tree on the current device in one
+ * call: sfc_filter_device at r_filter (Alg. 2), the kept points gathered in the filter's
+ * output order, then capt_build_device on them (Alg. 1).  The tree is the one capt_build
+ * makes from points[kept] on the host.  d_points: device float[n][3]; d_kept: device
+ * uint32[n] (caller-owned) receiving the kept indices (the tree's point i is input point
+ * d_kept[i]), or NULL when not wanted; *n_kept (host) their count.  Temporary device
+ * memory is allocated and freed inside; the call returns when the tree is complete.
+ * Errors: those of sfc_filter_device and capt_build_device. */
+int capt_build_frame_device(const float* d_points, size_t n, float r_filter, float r_min, float r_max,
+                            uint32_t* d_kept, size_t* n_kept, void* stream, capt_tree** out);
+
 /* One flag per sphere (Alg. 3).  d_centers: device float[m][3]; d_radii: device
  * float[m]; d_flags: device uint8[m] receives 1 = collides, 0 = free.  m = 0 is a
  * no-op.  Errors: CAPT_E_ARG, CAPT_E_STATE, CAPT_E_CUDA. */

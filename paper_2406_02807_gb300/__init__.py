@@ -24,7 +24,7 @@ __all__ = [
     "capt_clearance_bwd", "capt_free", "capt_last_error", "make_arm", "CaptTree", "EdgePlan",
     "capt_validate_edges_static", "CAPT_STATIC_MAX_EDGES", "capt_build_device", "capt_query_joint_configs",
     "capt_autotune_joint_configs", "CAPT_KERNEL_JOINTS", "sfc_filter_device", "capt_autotune_spheres",
-    "capt_morton_order", "STATUS", "CAPT_STAGE_GLOBAL", "CAPT_STAGE_SMEM", "CAPT_KERNEL_SPHERES", "CAPT_KERNEL_CONFIGS",
+    "capt_morton_order", "capt_build_frame_device", "STATUS", "CAPT_STAGE_GLOBAL", "CAPT_STAGE_SMEM", "CAPT_KERNEL_SPHERES", "CAPT_KERNEL_CONFIGS",
     "CAPT_KERNEL_EDGES", "CAPT_KERNEL_CLEARANCE", "CAPT_EDGES_PERSISTENT", "CAPT_EDGES_PER_EDGE",
     "EXPORTED_SYMBOLS",
 ]
@@ -44,7 +44,7 @@ EXPORTED_SYMBOLS = [
     "capt_autotune_configs", "capt_validate_edges", "capt_edge_plan_create", "capt_edge_plan_launch",
     "capt_edge_plan_info", "capt_edge_plan_free", "capt_clearance_fwd", "capt_clearance_bwd",
     "capt_validate_edges_static", "capt_build_device", "capt_query_joint_configs", "capt_autotune_joint_configs",
-    "sfc_filter_device", "capt_autotune_spheres", "capt_morton_order",
+    "sfc_filter_device", "capt_autotune_spheres", "capt_morton_order", "capt_build_frame_device",
 ]
 CAPT_STATIC_MAX_EDGES = 65536
 
@@ -96,6 +96,7 @@ def _load():
         "capt_export": [P, P, P, P, P],
         "capt_upload": [P, I, P],
         "capt_build_device": [P, SZ, F, F, P, C.POINTER(P)],
+        "capt_build_frame_device": [P, SZ, F, F, F, P, C.POINTER(SZ), P, C.POINTER(P)],
         "capt_query_spheres": [P, P, P, SZ, P, P],
         "capt_query_configs": [P, P, P, SZ, I, P, P],
         "capt_query_configs_host": [P, P, P, SZ, I, P, P],
@@ -274,6 +275,24 @@ def capt_build_device(points, r_min: float, r_max: float, stream=None) -> CaptTr
     _check(_load().capt_build_device(p, points.shape[0], float(r_min), float(r_max), _stream(stream), C.byref(h)),
            "capt_build_device")
     return CaptTree(h)
+
+
+def capt_build_frame_device(points, r_filter: float, r_min: float, r_max: float, stream=None):
+    """Filter (Alg. 2) and build (Alg. 1) on the GPU in one call from a float32 CUDA
+    tensor [n, 3]; returns (tree, kept) with kept the int32 indices of the points the tree
+    holds, in its order."""
+    import torch
+    if points.dim() != 2 or points.shape[1] != 3:
+        raise ValueError("points must be [n, 3]")
+    n = points.shape[0]
+    kept = torch.empty(max(n, 1), dtype=torch.int32, device=points.device)
+    p = _dev(points, torch.float32, "points") if n else C.c_void_p(0)
+    h = C.c_void_p()
+    m = C.c_size_t(0)
+    _check(_load().capt_build_frame_device(p, n, float(r_filter), float(r_min), float(r_max),
+                                           _dev(kept, torch.int32, "kept"), C.byref(m), _stream(stream), C.byref(h)),
+           "capt_build_frame_device")
+    return CaptTree(h), kept[: m.value]
 
 
 def capt_upload(tree: CaptTree, device: int = 0, stream=None):

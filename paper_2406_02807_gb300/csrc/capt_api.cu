@@ -376,6 +376,41 @@ int capt_build_device(const float* d_points, size_t n, float r_min, float r_max,
     return CAPT_OK;
 }
 
+int capt_build_frame_device(const float* d_points, size_t n, float r_filter, float r_min, float r_max,
+                            uint32_t* d_kept, size_t* n_kept, void* stream, capt_tree** out) {
+    if (!out || !n_kept) return fail(CAPT_E_ARG, "NULL argument");
+    *out = nullptr;
+    *n_kept = 0;
+    if (n && !d_points) return fail(CAPT_E_ARG, "points is NULL");
+    if (!(r_min >= 0.f) || !(r_max >= r_min) || !std::isfinite(r_max)) return fail(CAPT_E_RANGE, "need 0 <= r_min <= r_max < inf");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::string err;
+    uint32_t* kept = d_kept;
+    float* pts = nullptr;
+    int rc = CAPT_OK;
+    if (n && !kept && cudaMalloc((void**)&kept, n * sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CAPT_E_NOMEM, "cudaMalloc of the kept indices failed");
+    }
+    size_t m = 0;
+    rc = capt::device_sfc_filter(d_points, n, r_filter, kept, &m, st, err);
+    if (!rc && m && cudaMalloc((void**)&pts, m * 3 * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        rc = CAPT_E_NOMEM;
+        err = "cudaMalloc of the filtered points failed";
+    }
+    if (!rc) rc = capt::launch_gather_points(d_points, kept, m, pts, st, err);
+    if (!rc) {
+        rc = capt_build_device(pts, m, r_min, r_max, stream, out);   // synchronises the stream
+        if (rc) err = g_err;
+    }
+    if (pts) cudaFree(pts);
+    if (kept != d_kept && kept) cudaFree(kept);
+    if (rc) return fail(rc, err);
+    *n_kept = m;
+    return CAPT_OK;
+}
+
 int sfc_filter(const float* points, size_t n, float min_spacing, uint32_t* kept_idx, size_t* n_out) {
     std::string err;
     int rc = capt::host_sfc_filter(points, n, min_spacing, kept_idx, n_out, err);

@@ -475,6 +475,29 @@ int make_plan(FilterPlan& pl, int dev, size_t n, float r, std::string& err) {
 
 }  // namespace
 
+namespace {
+
+__global__ void k_gather_points(const float* __restrict__ pts, const uint32_t* __restrict__ idx, uint32_t m,
+                                float* __restrict__ out) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const float* p = pts + 3 * (size_t)idx[i];
+    out[3 * (size_t)i] = p[0];
+    out[3 * (size_t)i + 1] = p[1];
+    out[3 * (size_t)i + 2] = p[2];
+}
+
+}  // namespace
+
+int launch_gather_points(const float* pts, const uint32_t* idx, size_t m, float* out, cudaStream_t st,
+                         std::string& err) {
+    if (m == 0) return CAPT_OK;
+    k_gather_points<<<blocks_of(m, 256), 256, 0, st>>>(pts, idx, (uint32_t)m, out);
+    const cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) { err = std::string("gather launch: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
+    return CAPT_OK;
+}
+
 int device_sfc_filter(const float* d_points, size_t n, float r, uint32_t* d_kept, size_t* n_out, cudaStream_t st,
                       std::string& err) {
     if (!n_out || (n && (!d_points || !d_kept))) { err = "NULL argument"; return CAPT_E_ARG; }

@@ -51,6 +51,10 @@ int launch_joint_configs(const DevArgs& t, const capt_arm& arm, const float* q, 
 int device_sfc_filter(const float* d_points, size_t n, float r, uint32_t* d_kept, size_t* n_out, cudaStream_t st,
                       std::string& err);
 
+// out[i] = pts[idx[i]] for i < m (points [.][3]).
+int launch_gather_points(const float* pts, const uint32_t* idx, size_t m, float* out, cudaStream_t st,
+                         std::string& err);
+
 // Number of SMs of the current device (cached per device).
 int sm_count();
 

@@ -108,3 +108,30 @@ def test_filter_then_device_build(orc, capt_lib, torch_):
     ex = capt_lib.capt_export(tree)
     assert np.array_equal(ex["T"].view(np.uint32), ref["T"].view(np.uint32))
     assert np.array_equal(ex["set_idx"], ref["set_idx"])
+
+
+@pytest.mark.parametrize("rf", [0.015, 0.02])
+def test_frame_to_tree_in_one_call(orc, capt_lib, torch_, rf):
+    """capt_build_frame_device on a 307,200-point depth frame: the kept indices are the
+    oracle's Alg. 2 output and the tree is the oracle's Alg. 1 on those points."""
+    frame = W.depth_frame()
+    tree, kept = capt_lib.capt_build_frame_device(torch_.from_numpy(frame).cuda(), rf, 0.015, 0.08)
+    ref_kept = orc.sfc_filter(frame, rf)
+    assert np.array_equal(kept.cpu().numpy().astype(np.uint32), ref_kept)
+    ref = orc.PlainCAPT(frame[ref_kept], 0.015, 0.08).export()
+    ex = capt_lib.capt_export(tree)
+    assert np.array_equal(ex["T"].view(np.uint32), ref["T"].view(np.uint32))
+    assert np.array_equal(ex["set_begin"].astype(np.int64), ref["set_begin"])
+    assert np.array_equal(ex["set_idx"], ref["set_idx"])
+    # and it answers queries at once
+    c, r = W.cube_queries(20000, 9)
+    c = (c * np.float32([1.2, 0.8, 0.3]) + np.float32([0.0, -0.4, 0.0])).astype(np.float32)
+    r = np.clip(r, 0.015, 0.08).astype(np.float32)
+    f = capt_lib.capt_query_spheres(tree, torch_.from_numpy(c).cuda(), torch_.from_numpy(r).cuda()).cpu().numpy()
+    assert np.array_equal(f, orc.brute_flags(frame[ref_kept], c, r))
+
+
+def test_frame_to_tree_empty(capt_lib, torch_):
+    tree, kept = capt_lib.capt_build_frame_device(torch_.empty((0, 3), dtype=torch_.float32, device="cuda"),
+                                                  0.01, 0.015, 0.08)
+    assert kept.numel() == 0 and capt_lib.capt_stats(tree)["n_points"] == 0
