@@ -12,6 +12,7 @@
 
 #include "../../include/capt.h"
 #include "capt_internal.h"
+#include "host_internal.h"
 #include "device_build.h"
 #include "kernels.h"
 

@@ -82,10 +82,4 @@ struct DevArgs {
     float hi[3] = {-1.f, -1.f, -1.f};
 };
 
-int build_host_tree(const float* points, size_t n, float r_min, float r_max, int threads, HostTree& out,
-                    std::string& err);
-void flatten(const HostTree& t, Layout& out);
-int host_sfc_filter(const float* points, size_t n, float r, uint32_t* kept, size_t* n_out, std::string& err);
-int host_morton_order(const float* points, size_t n, uint32_t* order, std::string& err);
-
 }  // namespace capt

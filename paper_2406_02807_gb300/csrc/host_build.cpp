@@ -19,6 +19,7 @@
 #include <thread>
 
 #include "capt_internal.h"
+#include "host_internal.h"
 
 namespace capt {
 namespace {

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "capt_internal.h"
+#include "host_internal.h"
 
 namespace capt {
 namespace {
