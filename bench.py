@@ -554,6 +554,20 @@ def extra_workloads(capt, torch, dev, stream, pts, arm, args):
                        "build_ms": bms, "device_build_ms": device_build_ms(capt, pr, 0.02, 0.10, reps=3),
                        "launch_cfg": rcfg, "tree_device_bytes": int(st["device_bytes"]),
                        "total_afforded": int(st["total_afforded"]), "max_set": int(st["max_set"])}
+    # the compact (de-duplicated) sets of the same tree, replicated sets dropped
+    capt.capt_free(ts)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    capt.capt_compact(tr, drop_full=True)
+    cms = (time.perf_counter() - t0) * 1e3
+    sc = capt.capt_stats(tr)
+    fl3 = torch.empty_like(fl)
+    ccfg, _ = capt.capt_autotune_spheres(tr, dc, dr, fl3)
+    ms_c = time_events(torch, lambda: capt.capt_query_spheres(tr, dc, dr, fl3), 10, stream)
+    res["room200k_compact"] = {"spheres": 1 << 22, "ms": ms_c, "sphere_queries_per_s": (1 << 22) / (ms_c / 1e3),
+                               "compact_ms": cms, "launch_cfg": ccfg, "tree_device_bytes": int(sc["device_bytes"]),
+                               "compact_entries": int(sc["compact_entries"]),
+                               "flags_equal_replicated": bool(torch.equal(fl, fl3))}
     return res
 
 

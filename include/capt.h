@@ -66,6 +66,11 @@ typedef struct capt_tree_stats {
     float r_min, r_max;
     int32_t device;           /* CUDA ordinal after upload, else -1 */
     int32_t build_threads;    /* host threads of capt_build; 0 for capt_build_device */
+    uint64_t compact_chunks;  /* capt_compact: 32-point chunks of the Z-ordered cloud (0 before) */
+    uint64_t compact_entries; /* capt_compact: sum over leaves of the chunks each lists */
+    uint64_t compact_bytes;   /* capt_compact: device bytes of the compact form */
+    int32_t full_dropped;     /* 1 if capt_compact freed the replicated device sets */
+    int32_t reserved;
 } capt_tree_stats;
 
 /* ---------------------------------------------------------------------------------
@@ -167,6 +172,26 @@ const char* capt_last_error(void);
  * Calling it again re-uploads.  Errors: CAPT_E_ARG, CAPT_E_CUDA, CAPT_E_NOMEM. */
 int capt_upload(capt_tree* t, int device, void* stream);
 
+/* De-duplicated ("compact") affordance sets: Alg. 1 copies a point into the set of
+ * every leaf cell that affords it, so the sets replicate the cloud many times over
+ * (Sec. VII names compressing or de-duplicating them as the way to larger clouds).  The
+ * compact form keeps one copy of the cloud, in Z-order (capt_morton_order) and cut into
+ * chunks of 32 consecutive points with their FP32 boxes, and gives each leaf the
+ * ascending list of the chunks that hold a point of its set; the leaf box stays the
+ * box of its set.  The listed chunks hold a superset of the set inside the cloud, so
+ * every flag is unchanged (a point found is a cloud point within r; Lemma 1 puts every
+ * such point in the set).  The queries use it with the launch configuration's scan
+ * mode CAPT_SCAN_COMPACT; the autotuners include it once it exists.
+ * Built on the tree's device from its uploaded sets (stream-ordered on `stream`, the
+ * call synchronises it); about 16 bytes per point plus 32 bytes per leaf plus 4 bytes
+ * per list entry.  drop_full = 1 then frees the replicated device sets: the plain and
+ * chunked scan modes, edges, joint-angle configurations, clearance and the work
+ * counters return CAPT_E_STATE until capt_upload runs again.  capt_upload and
+ * capt_free release the compact form.
+ * Errors: CAPT_E_ARG, CAPT_E_STATE (not uploaded, or the replicated sets already
+ *         dropped), CAPT_E_RANGE (more than 1.6M chunks), CAPT_E_NOMEM, CAPT_E_CUDA. */
+int capt_compact(capt_tree* t, int drop_full, void* stream);
+
 /* Build the CAPT on the current CUDA device (Alg. 1, Sec. IV-A/B) from points already
  * in device memory.  The tree is the one capt_build makes from the same points and
  * radii, bit for bit (splits, sets in ascending index, boxes, prune decisions), and it
@@ -264,11 +289,15 @@ typedef struct capt_launch_cfg {
     int32_t staging;           /* CAPT_STAGE_* */
     int32_t chunk;             /* edges: configurations per work item (1..1024, rounded
                                   up to a multiple of 32).  Spheres and configurations:
-                                  the affordance scan, 0 = whole sets (Alg. 3), 1 = by
-                                  chunks of 32 points, only those whose box the sphere
-                                  reaches (pays when a set's consecutive points are close
-                                  in space, as after the filter) */
+                                  the affordance scan, CAPT_SCAN_* */
 } capt_launch_cfg;
+
+/* Affordance scan of the sphere and configuration kernels (capt_launch_cfg.chunk). */
+enum { CAPT_SCAN_SETS = 0,     /* whole sets, as Alg. 3 */
+       CAPT_SCAN_CHUNKED = 1,  /* sets by chunks of 32 points, only those whose box the
+                                  sphere reaches (pays when a set's consecutive points are
+                                  close in space, as after the filter) */
+       CAPT_SCAN_COMPACT = 2   /* the compact sets of capt_compact, chunk boxes first */ };
 
 /* Set / get the launch configuration used for `kernel` on this tree.
  * Errors: CAPT_E_ARG (unsupported value). */

@@ -24,7 +24,8 @@ __all__ = [
     "capt_clearance_bwd", "capt_free", "capt_last_error", "make_arm", "CaptTree", "EdgePlan",
     "capt_validate_edges_static", "CAPT_STATIC_MAX_EDGES", "capt_build_device", "capt_query_joint_configs",
     "capt_autotune_joint_configs", "CAPT_KERNEL_JOINTS", "sfc_filter_device", "capt_autotune_spheres",
-    "capt_morton_order", "capt_build_frame_device", "STATUS", "CAPT_STAGE_GLOBAL", "CAPT_STAGE_SMEM", "CAPT_KERNEL_SPHERES", "CAPT_KERNEL_CONFIGS",
+    "capt_morton_order", "capt_build_frame_device", "capt_compact", "CAPT_SCAN_SETS", "CAPT_SCAN_CHUNKED",
+    "CAPT_SCAN_COMPACT", "STATUS", "CAPT_STAGE_GLOBAL", "CAPT_STAGE_SMEM", "CAPT_KERNEL_SPHERES", "CAPT_KERNEL_CONFIGS",
     "CAPT_KERNEL_EDGES", "CAPT_KERNEL_CLEARANCE", "CAPT_EDGES_PERSISTENT", "CAPT_EDGES_PER_EDGE",
     "EXPORTED_SYMBOLS",
 ]
@@ -32,6 +33,7 @@ __all__ = [
 STATUS = {0: "CAPT_OK", -1: "CAPT_E_ARG", -2: "CAPT_E_RANGE", -3: "CAPT_E_NONFINITE", -4: "CAPT_E_NOMEM",
           -5: "CAPT_E_CUDA", -6: "CAPT_E_TIMEOUT", -7: "CAPT_E_BOUNDS", -8: "CAPT_E_STATE"}
 CAPT_STAGE_GLOBAL, CAPT_STAGE_SMEM = 0, 1
+CAPT_SCAN_SETS, CAPT_SCAN_CHUNKED, CAPT_SCAN_COMPACT = 0, 1, 2
 CAPT_KERNEL_SPHERES, CAPT_KERNEL_CONFIGS, CAPT_KERNEL_EDGES, CAPT_KERNEL_CLEARANCE, CAPT_KERNEL_JOINTS = 0, 1, 2, 3, 4
 CAPT_EDGES_PERSISTENT, CAPT_EDGES_PER_EDGE = 0, 1
 MAX_JOINTS, MAX_SPHERES = 16, 64
@@ -44,7 +46,7 @@ EXPORTED_SYMBOLS = [
     "capt_autotune_configs", "capt_validate_edges", "capt_edge_plan_create", "capt_edge_plan_launch",
     "capt_edge_plan_info", "capt_edge_plan_free", "capt_clearance_fwd", "capt_clearance_bwd",
     "capt_validate_edges_static", "capt_build_device", "capt_query_joint_configs", "capt_autotune_joint_configs",
-    "sfc_filter_device", "capt_autotune_spheres", "capt_morton_order", "capt_build_frame_device",
+    "sfc_filter_device", "capt_autotune_spheres", "capt_morton_order", "capt_build_frame_device", "capt_compact",
 ]
 CAPT_STATIC_MAX_EDGES = 65536
 
@@ -60,7 +62,8 @@ class _Stats(C.Structure):
                 ("max_set", C.c_uint32), ("total_afforded", C.c_uint64), ("total_blocks", C.c_uint64),
                 ("pruned_leaves", C.c_uint64), ("empty_leaves", C.c_uint64), ("device_bytes", C.c_uint64),
                 ("build_ms", C.c_double), ("r_min", C.c_float), ("r_max", C.c_float), ("device", C.c_int32),
-                ("build_threads", C.c_int32)]
+                ("build_threads", C.c_int32), ("compact_chunks", C.c_uint64), ("compact_entries", C.c_uint64),
+                ("compact_bytes", C.c_uint64), ("full_dropped", C.c_int32), ("reserved", C.c_int32)]
 
 
 class _LaunchCfg(C.Structure):
@@ -95,6 +98,7 @@ def _load():
         "capt_stats": [P, C.POINTER(_Stats)],
         "capt_export": [P, P, P, P, P],
         "capt_upload": [P, I, P],
+        "capt_compact": [P, I, P],
         "capt_build_device": [P, SZ, F, F, P, C.POINTER(P)],
         "capt_build_frame_device": [P, SZ, F, F, F, P, C.POINTER(SZ), P, C.POINTER(P)],
         "capt_query_spheres": [P, P, P, SZ, P, P],
@@ -297,6 +301,12 @@ def capt_build_frame_device(points, r_filter: float, r_min: float, r_max: float,
 
 def capt_upload(tree: CaptTree, device: int = 0, stream=None):
     _check(_load().capt_upload(tree.h, int(device), _stream(stream)), "capt_upload")
+
+
+def capt_compact(tree: CaptTree, drop_full: bool = False, stream=None):
+    """Build the tree's compact (de-duplicated) sets on its device; drop_full frees the
+    replicated device sets afterwards."""
+    _check(_load().capt_compact(tree.h, 1 if drop_full else 0, _stream(stream)), "capt_compact")
 
 
 def capt_query_spheres(tree: CaptTree, centers, radii, flags=None, stream=None):

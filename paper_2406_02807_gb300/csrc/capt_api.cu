@@ -3,9 +3,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -54,9 +56,9 @@ bool valid_cfg(int kernel, const capt_launch_cfg& c) {
     if (c.warps_per_block < 1 || c.warps_per_block > 16) return false;
     if (c.staging != CAPT_STAGE_GLOBAL && c.staging != CAPT_STAGE_SMEM) return false;
     const int spl = c.spheres_per_lane;
-    if (kernel == CAPT_KERNEL_SPHERES) return (spl == 1 || spl == 2 || spl == 4 || spl == 8) && (c.chunk == 0 || c.chunk == 1);
-    if (kernel == CAPT_KERNEL_CONFIGS)
-        return (spl == 2 || spl == 4 || spl == 8 || spl == 16) && (c.chunk == 0 || c.chunk == 1);
+    const bool scan_mode = c.chunk >= CAPT_SCAN_SETS && c.chunk <= CAPT_SCAN_COMPACT;
+    if (kernel == CAPT_KERNEL_SPHERES) return (spl == 1 || spl == 2 || spl == 4 || spl == 8) && scan_mode;
+    if (kernel == CAPT_KERNEL_CONFIGS) return (spl == 2 || spl == 4 || spl == 8 || spl == 16) && scan_mode;
     if (kernel == CAPT_KERNEL_EDGES) return c.chunk >= 1 && c.chunk <= 1024;   // one configuration per lane
     if (kernel == CAPT_KERNEL_CLEARANCE) return true;
     if (kernel == CAPT_KERNEL_JOINTS) return true;   // one configuration per lane
@@ -100,6 +102,13 @@ struct capt_tree {
     void* d_set_idx = nullptr;
     void* d_set_begin = nullptr;
     void* d_pruned = nullptr;
+    // compact (de-duplicated) sets, built by capt_compact; full_dropped: the replicated
+    // device sets (blocks, ids, chunk boxes) were freed after it
+    capt::CompactSets cs;
+    bool full_dropped = false;
+    // live edge plans (their graphs hold the device pointers); shared so that a plan
+    // freed after its tree does not touch the tree
+    std::shared_ptr<std::atomic<int>> n_plans = std::make_shared<std::atomic<int>>(0);
     std::mutex mu;
 
     capt_tree() {
@@ -125,6 +134,11 @@ struct capt_tree {
         a.ids = static_cast<const uint32_t*>(d_ids);
         a.cbox = static_cast<const float*>(d_cbox);
         a.cloud = static_cast<const float*>(d_cloud);
+        a.cleaves = static_cast<const capt::LeafRec*>(cs.cleaves);
+        a.clist = static_cast<const uint32_t*>(cs.clist);
+        a.cblocks = static_cast<const float*>(cs.cblocks);
+        a.cplane = cs.n_chunks > 0 ? cs.n_chunks * capt::kChunkBlocks : 1;
+        a.ccbox = static_cast<const float*>(cs.ccbox);
         a.status = d_status;
         a.N = (uint32_t)h.N;
         a.L = h.L;
@@ -144,6 +158,8 @@ struct capt_tree {
                         (void*)d_pipe_f[0], (void*)d_pipe_f[1], (void*)d_edge_scratch, (void*)d_zc_flags, d_Tplain,
                         d_set_idx, d_set_begin, d_pruned})
             if (p) cudaFree(p);
+        cs.release();
+        full_dropped = false;
         for (auto& e : pipe_ev)
             if (e) cudaEventDestroy(e);
         if (pipe_stream) cudaStreamDestroy(pipe_stream);
@@ -186,6 +202,35 @@ int check_ready(const capt_tree* t) {
     if (cudaGetDevice(&cur) != cudaSuccess || cur != t->device)
         return fail(CAPT_E_STATE, "current CUDA device differs from the tree's device");
     return CAPT_OK;
+}
+
+// check_ready, and the replicated device sets are still there (not dropped by capt_compact).
+int check_full(const capt_tree* t) {
+    const int rc = check_ready(t);
+    if (rc) return rc;
+    if (t->full_dropped)
+        return fail(CAPT_E_STATE, "the replicated sets were dropped by capt_compact (only the compact scan remains)");
+    return CAPT_OK;
+}
+
+// The scan mode of a sphere / configuration launch has its data on the device.
+int check_scan(const capt_tree* t, const capt_launch_cfg& c) {
+    if (c.chunk == CAPT_SCAN_COMPACT && !t->cs.clist)
+        return fail(CAPT_E_STATE, "scan mode CAPT_SCAN_COMPACT needs capt_compact first");
+    if (c.chunk != CAPT_SCAN_COMPACT && t->full_dropped)
+        return fail(CAPT_E_STATE, "the replicated sets were dropped by capt_compact: use CAPT_SCAN_COMPACT");
+    return CAPT_OK;
+}
+
+// Candidate scan modes for the autotuners: those whose data is on the device.
+std::vector<int> scan_modes(const capt_tree* t) {
+    std::vector<int> m;
+    if (!t->full_dropped) {
+        m.push_back(CAPT_SCAN_SETS);
+        m.push_back(CAPT_SCAN_CHUNKED);
+    }
+    if (t->cs.clist) m.push_back(CAPT_SCAN_COMPACT);
+    return m;
 }
 
 // Two chunk buffers of `chunk` configurations of S spheres (+ slack for the radii),
@@ -463,6 +508,10 @@ int capt_stats(const capt_tree* t, capt_tree_stats* s) {
     s->r_max = h.r_max;
     s->device = t->device;
     s->build_threads = h.build_threads;
+    s->compact_chunks = t->cs.n_chunks;
+    s->compact_entries = t->cs.list_len;
+    s->compact_bytes = t->cs.bytes;
+    s->full_dropped = t->full_dropped ? 1 : 0;
     return CAPT_OK;
 }
 
@@ -574,12 +623,56 @@ int capt_upload(capt_tree* t, int device, void* stream) {
     return CAPT_OK;
 }
 
+int capt_compact(capt_tree* t, int drop_full, void* stream) {
+    int rc = check_full(t);
+    if (rc) return rc;
+    if (drop_full != 0 && drop_full != 1) return fail(CAPT_E_ARG, "drop_full must be 0 or 1");
+    std::lock_guard<std::mutex> lk(t->mu);
+    if (drop_full && *t->n_plans > 0) return fail(CAPT_E_STATE, "edge plans of this tree still use its replicated sets");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t n = t->h.n;
+    std::vector<float> pts;
+    std::vector<uint32_t> order;
+    std::string err;
+    try {
+        order.resize(n);
+        const float* hp = t->h.pts.data();
+        if (t->h.pts.size() != 3 * n) {   // built on the device: read the cloud back
+            pts.resize(3 * n);
+            if (n) CUDA_TRY(cudaMemcpyAsync(pts.data(), t->d_cloud, 3 * n * sizeof(float), cudaMemcpyDeviceToHost, st),
+                            "cloud D2H");
+            CUDA_TRY(cudaStreamSynchronize(st), "cloud D2H");
+            hp = pts.data();
+        }
+        rc = capt::host_morton_order(hp, n, order.data(), err);
+    } catch (const std::bad_alloc&) {
+        return fail(CAPT_E_NOMEM, "host allocation failed in capt_compact");
+    }
+    if (rc) return fail(rc, err);
+    t->dev_bytes -= std::min(t->dev_bytes, t->cs.bytes);
+    t->cs.release();
+    rc = capt::device_compact(t->args(), n, order.data(), st, t->cs, err);
+    if (rc) return fail(rc, err);
+    t->dev_bytes += t->cs.bytes;
+    if (drop_full) {
+        CUDA_TRY(cudaStreamSynchronize(st), "synchronize");
+        for (void* p : {t->d_blocks, t->d_ids, t->d_cbox})
+            if (p) cudaFree(p);
+        t->d_blocks = t->d_ids = t->d_cbox = nullptr;
+        const size_t full = t->total_blocks * 16 * sizeof(float) + capt::chunk_count(t->total_blocks) * 8 * sizeof(float);
+        t->dev_bytes = t->dev_bytes > full ? t->dev_bytes - full : 0;
+        t->full_dropped = true;
+    }
+    return CAPT_OK;
+}
+
 int capt_query_spheres(const capt_tree* t, const float* d_centers, const float* d_radii, size_t m, uint8_t* d_flags,
                        void* stream) {
     int rc = check_ready(t);
     if (rc) return rc;
     if (m == 0) return CAPT_OK;
     if (!d_centers || !d_radii || !d_flags) return fail(CAPT_E_ARG, "NULL device pointer");
+    if ((rc = check_scan(t, t->cfg[CAPT_KERNEL_SPHERES]))) return rc;
     std::string err;
     rc = capt::launch_query(t->args(), capt::kModeSpheres, d_centers, d_radii, m, 1, d_flags,
                             t->cfg[CAPT_KERNEL_SPHERES], static_cast<cudaStream_t>(stream), err);
@@ -593,6 +686,7 @@ int capt_query_configs(const capt_tree* t, const float* d_centers, const float* 
     if (S < 1 || S > CAPT_MAX_SPHERES) return fail(CAPT_E_ARG, "S must be in [1, 64]");
     if (C == 0) return CAPT_OK;
     if (!d_centers || !d_radii || !d_flags) return fail(CAPT_E_ARG, "NULL device pointer");
+    if ((rc = check_scan(t, t->cfg[CAPT_KERNEL_CONFIGS]))) return rc;
     std::string err;
     rc = capt::launch_query(t->args(), capt::kModeConfigs, d_centers, d_radii, C, S, d_flags,
                             t->cfg[CAPT_KERNEL_CONFIGS], static_cast<cudaStream_t>(stream), err);
@@ -606,6 +700,7 @@ int capt_query_configs_host(capt_tree* t, const float* h_centers, const float* h
     if (S < 1 || S > CAPT_MAX_SPHERES) return fail(CAPT_E_ARG, "S must be in [1, 64]");
     if (C == 0) return CAPT_OK;
     if (!h_centers || !h_radii || !h_flags) return fail(CAPT_E_ARG, "NULL host pointer");
+    if ((rc = check_scan(t, t->cfg[CAPT_KERNEL_CONFIGS]))) return rc;
     std::lock_guard<std::mutex> lk(t->mu);
     cudaStream_t user = static_cast<cudaStream_t>(stream);
     std::string err;
@@ -667,7 +762,7 @@ int capt_query_configs_host(capt_tree* t, const float* h_centers, const float* h
 
 int capt_count_config_work(const capt_tree* t, const float* d_centers, const float* d_radii, size_t C, int S,
                            uint64_t* d_counts, void* stream) {
-    int rc = check_ready(t);
+    int rc = check_full(t);
     if (rc) return rc;
     if (S < 1 || S > CAPT_MAX_SPHERES) return fail(CAPT_E_ARG, "S must be in [1, 64]");
     if (C == 0) return CAPT_OK;
@@ -764,7 +859,7 @@ int capt_autotune_configs(capt_tree* t, const float* d_centers, const float* d_r
     for (int warps : {4, 8, 16})
         for (int spl : {2, 4, 8, 16})
             for (int stage : {CAPT_STAGE_GLOBAL, CAPT_STAGE_SMEM})
-                for (int chunked : {0, 1}) cands.push_back({warps, spl, stage, chunked});
+                for (int mode : scan_modes(t)) cands.push_back({warps, spl, stage, mode});
     return autotune_query(t, CAPT_KERNEL_CONFIGS, cands, d_centers, d_radii, C, S, d_flags,
                           static_cast<cudaStream_t>(stream), best, best_ms);
 }
@@ -779,7 +874,7 @@ int capt_autotune_spheres(capt_tree* t, const float* d_centers, const float* d_r
     for (int warps : {4, 8, 16})
         for (int spl : {1, 2, 4, 8})
             for (int stage : {CAPT_STAGE_GLOBAL, CAPT_STAGE_SMEM})
-                for (int chunked : {0, 1}) cands.push_back({warps, spl, stage, chunked});
+                for (int mode : scan_modes(t)) cands.push_back({warps, spl, stage, mode});
     return autotune_query(t, CAPT_KERNEL_SPHERES, cands, d_centers, d_radii, m, 1, d_flags,
                           static_cast<cudaStream_t>(stream), best, best_ms);
 }
@@ -821,6 +916,7 @@ int check_arm(const capt_arm* arm) {
 
 struct capt_edge_plan {
     capt_tree* tree = nullptr;
+    std::shared_ptr<std::atomic<int>> tree_plans;
     int device = -1;
     uint32_t* d_scratch = nullptr;
     cudaGraph_t graph = nullptr;
@@ -925,6 +1021,7 @@ int capt_autotune_joint_configs(capt_tree* t, const capt_arm* arm, const float* 
 
 void capt_edge_plan_free(capt_edge_plan* p) {
     if (!p) return;
+    if (p->tree_plans) --*p->tree_plans;
     DeviceGuard g(p->device);
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
@@ -948,6 +1045,8 @@ int capt_edge_plan_create(capt_tree* t, const capt_arm* arm, const float* d_qa, 
     if (!p) return fail(CAPT_E_NOMEM, "host allocation failed");
     p->tree = t;
     p->device = t->device;
+    p->tree_plans = t->n_plans;
+    ++*p->tree_plans;
     const size_t words = capt::edge_scratch_words(E);
     if (cudaMalloc((void**)&p->d_scratch, words * sizeof(uint32_t)) != cudaSuccess) {
         cudaGetLastError();
@@ -1029,7 +1128,7 @@ int capt_edge_plan_info(const capt_edge_plan* p, capt_launch_cfg* cfg, float* tu
 
 int capt_clearance_fwd(const capt_tree* t, const float* d_centers, const float* d_radii, size_t T, int W, int S,
                        float margin, float* d_cost, float* d_dist, int32_t* d_argmin, void* stream) {
-    int rc = check_ready(t);
+    int rc = check_full(t);
     if (rc) return rc;
     if (t->h.r_min != 0.f) return fail(CAPT_E_STATE, "clearance needs a tree built with r_min = 0 (no prune)");
     if (S < 1 || S > CAPT_MAX_SPHERES || W < 1) return fail(CAPT_E_ARG, "need 1 <= S <= 64 and W >= 1");
@@ -1045,7 +1144,7 @@ int capt_clearance_fwd(const capt_tree* t, const float* d_centers, const float* 
 int capt_clearance_bwd(const capt_tree* t, const float* d_centers, const float* d_radii, const float* d_dist,
                        const int32_t* d_argmin, const float* d_grad_cost, size_t T, int W, int S, float margin,
                        float* d_grad_centers, void* stream) {
-    int rc = check_ready(t);
+    int rc = check_full(t);
     if (rc) return rc;
     if (t->h.r_min != 0.f) return fail(CAPT_E_STATE, "clearance needs a tree built with r_min = 0 (no prune)");
     if (S < 1 || S > CAPT_MAX_SPHERES || W < 1) return fail(CAPT_E_ARG, "need 1 <= S <= 64 and W >= 1");

@@ -74,6 +74,12 @@ struct DevArgs {
     const uint32_t* ids = nullptr;   // 4 per block
     const float* cbox = nullptr;     // chunk boxes: 8 floats each {lo.xyz, 0, hi.xyz, 0}
     const float* cloud = nullptr;    // [n][3]
+    // compact (de-duplicated) sets: null until capt_compact
+    const LeafRec* cleaves = nullptr;  // N records: {lo, first list entry, hi, chunks}
+    const uint32_t* clist = nullptr;   // chunk ids of each leaf, ascending
+    const float* cblocks = nullptr;    // the cloud in Z-order, 4-point blocks in three planes
+    uint64_t cplane = 1;               // blocks per plane of cblocks
+    const float* ccbox = nullptr;      // boxes of the cloud's 32-point chunks
     int* status = nullptr;           // latched device status bits
     uint32_t N = 1;
     int L = 0;

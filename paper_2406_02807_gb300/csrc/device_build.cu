@@ -653,6 +653,13 @@ void DeviceTree::release() {
         return CAPT_E_NOMEM;                                             \
     }
 
+int launch_scan64(const uint32_t* v, uint32_t len, unsigned long long* out, cudaStream_t st, std::string& err) {
+    k_scan64<<<1, 1024, 0, st>>>(v, len, out);
+    const cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) { err = std::string("scan launch: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
+    return CAPT_OK;
+}
+
 int device_build(const float* d_points, size_t n, float r_min, float r_max, cudaStream_t st, DeviceTree& out,
                  std::string& err) {
     out = DeviceTree();

@@ -55,6 +55,26 @@ int device_sfc_filter(const float* d_points, size_t n, float r, uint32_t* d_kept
 int launch_gather_points(const float* pts, const uint32_t* idx, size_t m, float* out, cudaStream_t st,
                          std::string& err);
 
+// Exclusive scan of v[0..len) into 64-bit offsets out[0..len], out[len] = total (one block).
+int launch_scan64(const uint32_t* v, uint32_t len, unsigned long long* out, cudaStream_t st, std::string& err);
+
+// Compact (de-duplicated) affordance sets of an uploaded tree: device buffers owned by
+// the tree once built (release() frees them).
+struct CompactSets {
+    void* cleaves = nullptr;   // N leaf records {lo, first list entry, hi, number of chunks}
+    void* clist = nullptr;     // uint32 chunk ids, ascending per leaf
+    void* cblocks = nullptr;   // the Z-ordered cloud: n_chunks x 8 blocks in three planes
+    void* ccbox = nullptr;     // n_chunks boxes of 8 floats
+    uint64_t n_chunks = 0, list_len = 0;
+    size_t bytes = 0;
+    void release();
+};
+
+// Builds the compact sets from the tree's device sets (t.leaves, t.ids, t.cloud) and the
+// cloud's Z-order h_order (host uint32[n]).  Synchronises st.
+int device_compact(const DevArgs& t, size_t n, const uint32_t* h_order, cudaStream_t st, CompactSets& out,
+                   std::string& err);
+
 // Number of SMs of the current device (cached per device).
 int sm_count();
 

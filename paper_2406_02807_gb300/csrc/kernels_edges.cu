@@ -118,6 +118,7 @@ struct EdgeScratch {
 // One pass: configurations k0 + stride * i, i = 0 .. count - 1 (count <= 32), of the
 // edge with n_e configurations from qa_e to qb_e, lane i taking the i-th.  Returns true
 // as soon as one of them collides.
+template <int MODE>
 __device__ bool edge_pass(const DevArgs& t, const ArmPlan& arm, const float* __restrict__ qa_e,
                           const float* __restrict__ qb_e, int n_e, int k0, int stride, int count, const float* Ts,
                           EdgeScratch* ws) {
@@ -149,7 +150,7 @@ __device__ bool edge_pass(const DevArgs& t, const ArmPlan& arm, const float* __r
             n_near += __popc(mask);
             if (n_near >= 32) {
                 __syncwarp();
-                if (sphere_round<true>(t, Ts, &ws->re, nullptr, ws->nc[lane], 0, true, lane, lt_mask)) return true;
+                if (sphere_round<true, MODE>(t, Ts, &ws->re, nullptr, ws->nc[lane], 0, true, lane, lt_mask)) return true;
                 const uint32_t rest = n_near - 32;
                 float4 cc = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (lane < rest) cc = ws->nc[32 + lane];
@@ -171,7 +172,7 @@ __device__ bool edge_pass(const DevArgs& t, const ArmPlan& arm, const float* __r
     __syncwarp();
     const bool in_queue = lane < n_near;
     const float4 c = in_queue ? ws->nc[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-    return sphere_round<true>(t, Ts, &ws->re, nullptr, c, 0, in_queue, lane, lt_mask);
+    return sphere_round<true, MODE>(t, Ts, &ws->re, nullptr, c, 0, in_queue, lane, lt_mask);
 }
 
 __device__ __forceinline__ uint8_t load_volatile_u8(const uint8_t* p) {
@@ -216,7 +217,7 @@ __global__ void k_edges_setup(const int32_t* __restrict__ ns, uint32_t E, uint32
     }
 }
 
-template <bool STAGE>
+template <bool STAGE, int MODE>
 __global__ void __launch_bounds__(512, 2) k_edges_persistent(DevArgs t, const __grid_constant__ ArmPlan arm,
                                                              const float* __restrict__ qa, const float* __restrict__ qb,
                                                              const int32_t* __restrict__ ns, uint32_t E, uint32_t chunk,
@@ -258,7 +259,7 @@ __global__ void __launch_bounds__(512, 2) k_edges_persistent(DevArgs t, const __
         const float* qa_e = qa + (size_t)e * J;
         const float* qb_e = qb + (size_t)e * J;
         for (int j = 0; j < cnt; j += 32) {
-            if (edge_pass(t, arm, qa_e, qb_e, n_e, ci + nci * j, nci, min(32, cnt - j), Ts, ws)) {
+            if (edge_pass<MODE>(t, arm, qa_e, qb_e, n_e, ci + nci * j, nci, min(32, cnt - j), Ts, ws)) {
                 if (lane == 0) valid[e] = 0;
                 break;
             }
@@ -268,6 +269,7 @@ __global__ void __launch_bounds__(512, 2) k_edges_persistent(DevArgs t, const __
 }
 
 // One edge per launch (the per-edge baseline): warps stride over its configurations.
+template <int MODE>
 __global__ void __launch_bounds__(512, 2) k_edge_single(DevArgs t, const __grid_constant__ ArmPlan arm,
                                                         const float* __restrict__ qa_e, const float* __restrict__ qb_e,
                                                         int n_e, uint8_t* valid_e) {
@@ -277,7 +279,7 @@ __global__ void __launch_bounds__(512, 2) k_edge_single(DevArgs t, const __grid_
     const int gw = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
     for (int k = gw * 32; k < n_e; k += warps * 32) {
         if (load_volatile_u8(valid_e) == 0) break;
-        if (edge_pass(t, arm, qa_e, qb_e, n_e, k, 1, min(32, n_e - k), nullptr, ws)) {
+        if (edge_pass<MODE>(t, arm, qa_e, qb_e, n_e, k, 1, min(32, n_e - k), nullptr, ws)) {
             if (lane_id() == 0) *valid_e = 0;
             break;
         }
@@ -296,7 +298,7 @@ struct JointScratch {
     RoundEntries re;
 };
 
-template <bool STAGE>
+template <bool STAGE, int MODE>
 __global__ void __launch_bounds__(512, 2) k_joint_configs(DevArgs t, const __grid_constant__ ArmPlan arm,
                                                           const float* __restrict__ q, uint64_t C,
                                                           uint8_t* __restrict__ out) {
@@ -320,7 +322,7 @@ __global__ void __launch_bounds__(512, 2) k_joint_configs(DevArgs t, const __gri
         const bool in_queue = lane < n;
         const float4 c = in_queue ? ws->nc[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
         const uint32_t g = in_queue ? ws->ng[lane] : 0u;
-        sphere_round<false>(t, Ts, &ws->re, ws->ghit, c, g, in_queue, lane, lt_mask);
+        sphere_round<false, MODE>(t, Ts, &ws->re, ws->ghit, c, g, in_queue, lane, lt_mask);
     };
     for (uint64_t pass = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); pass < passes;
          pass += nwarps) {
@@ -395,7 +397,9 @@ int launch_joint_configs(const DevArgs& t, const capt_arm& arm, const float* q, 
                          const capt_launch_cfg& cfg, cudaStream_t st, std::string& err) {
     if (C == 0) return CAPT_OK;
     const bool stage = cfg.staging == CAPT_STAGE_SMEM && t.stage_floats > 0;
-    auto fn = stage ? k_joint_configs<true> : k_joint_configs<false>;
+    // the chunked scan, or the compact one once the replicated sets are dropped
+    auto fn = t.blocks ? (stage ? k_joint_configs<true, kScanChunked> : k_joint_configs<false, kScanChunked>)
+                       : (stage ? k_joint_configs<true, kScanCompact> : k_joint_configs<false, kScanCompact>);
     const int warps = std::max(1, std::min(16, (int)cfg.warps_per_block));
     const size_t smem = (stage ? stage_offset(t) : 0u) + sizeof(JointScratch) * (size_t)warps;
     cudaError_t ce = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -434,7 +438,8 @@ int launch_edges_persistent(const DevArgs& t, const capt_arm& arm, const float* 
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) { err = std::string("edge setup launch: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
     const bool stage = cfg.staging == CAPT_STAGE_SMEM && t.stage_floats > 0;
-    auto fn = stage ? k_edges_persistent<true> : k_edges_persistent<false>;
+    auto fn = t.blocks ? (stage ? k_edges_persistent<true, kScanChunked> : k_edges_persistent<false, kScanChunked>)
+                       : (stage ? k_edges_persistent<true, kScanCompact> : k_edges_persistent<false, kScanCompact>);
     const int warps = std::max(1, std::min(16, (int)cfg.warps_per_block));
     const size_t smem = (stage ? stage_offset(t) : 0u) + sizeof(EdgeScratch) * (size_t)warps;
     ce = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -456,7 +461,8 @@ int launch_edges_per_edge(const DevArgs& t, const capt_arm& arm, const float* qa
     if (ce != cudaSuccess) { err = std::string("memset: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
     const int warps = std::max(1, std::min(16, (int)cfg.warps_per_block));
     const size_t smem = sizeof(EdgeScratch) * (size_t)warps;
-    ce = cudaFuncSetAttribute((const void*)k_edge_single, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto fn = t.blocks ? k_edge_single<kScanChunked> : k_edge_single<kScanCompact>;
+    ce = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (ce != cudaSuccess) { err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
     const ArmPlan plan = make_plan(arm);
     const int J = arm.n_joints;
@@ -465,7 +471,7 @@ int launch_edges_per_edge(const DevArgs& t, const capt_arm& arm, const float* qa
         if (n <= 0) continue;
         const int warps_needed = (n + 31) / 32;
         const int blocks = (warps_needed + warps - 1) / warps;
-        k_edge_single<<<blocks, warps * 32, smem, st>>>(t, plan, qa + e * J, qb + e * J, n, valid + e);
+        fn<<<blocks, warps * 32, smem, st>>>(t, plan, qa + e * J, qb + e * J, n, valid + e);
     }
     ce = cudaGetLastError();
     if (ce != cudaSuccess) { err = std::string("per-edge launch: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }

@@ -48,7 +48,7 @@ __device__ __forceinline__ void bulk_copy(float* dst, const float* src, uint32_t
                  : "memory");
 }
 
-template <int SPL, bool STAGE, bool CHUNKED>
+template <int SPL, bool STAGE, int MODE>
 __global__ void __launch_bounds__(512, 2)
     k_spheres(DevArgs t, const float* __restrict__ centers, const float* __restrict__ radii, uint64_t m,
               uint8_t* __restrict__ out) {
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(512, 2)
                 const float r = in[3 * E + j];
                 c = make_float4(in[3 * j], in[3 * j + 1], in[3 * j + 2], __fmul_rn(r, r));
             }
-            sphere_round<false, CHUNKED>(t, Ts, &ws->re, ws->ghit, c, j, live, lane, lt_mask);
+            sphere_round<false, MODE>(t, Ts, &ws->re, ws->ghit, c, j, live, lane, lt_mask);
         }
         __syncwarp();
 #pragma unroll
@@ -204,7 +204,7 @@ struct CfgScratch {
 #define CFG_MIN_BLOCKS 2
 #endif
 
-template <int CPT, bool STAGE, bool CHUNKED>
+template <int CPT, bool STAGE, int MODE>
 __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs(DevArgs t, const float* __restrict__ centers,
                                                                  const float* __restrict__ radii, uint64_t C, int S,
                                                                  uint8_t* __restrict__ out) {
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs(DevArgs t, cons
         const bool live = lane < n;
         const float4 c = live ? ws->nc[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
         const uint32_t g = live ? ws->ng[lane] : 0u;
-        sphere_round<false, CHUNKED>(t, Ts, &ws->re, ws->ghit, c, g, live, lane, lt_mask);
+        sphere_round<false, MODE>(t, Ts, &ws->re, ws->ghit, c, g, live, lane, lt_mask);
     };
 
     for (uint64_t tile = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp; tile < n_tiles; tile += nwarps) {
@@ -443,18 +443,22 @@ namespace {
 
 using SphereKernel = void (*)(DevArgs, const float*, const float*, uint64_t, uint8_t*);
 
-template <int SPL>
-SphereKernel pick_spheres_spl(bool stage, bool chunked) {
-    if (stage) return chunked ? k_spheres<SPL, true, true> : k_spheres<SPL, true, false>;
-    return chunked ? k_spheres<SPL, false, true> : k_spheres<SPL, false, false>;
+template <int SPL, bool STAGE>
+SphereKernel pick_spheres_mode(int mode) {
+    switch (mode) {
+        case kScanPlain: return k_spheres<SPL, STAGE, kScanPlain>;
+        case kScanChunked: return k_spheres<SPL, STAGE, kScanChunked>;
+        case kScanCompact: return k_spheres<SPL, STAGE, kScanCompact>;
+        default: return nullptr;
+    }
 }
 
-SphereKernel pick_spheres(int spl, bool stage, bool chunked) {
+SphereKernel pick_spheres(int spl, bool stage, int mode) {
     switch (spl) {
-        case 1: return pick_spheres_spl<1>(stage, chunked);
-        case 2: return pick_spheres_spl<2>(stage, chunked);
-        case 4: return pick_spheres_spl<4>(stage, chunked);
-        case 8: return pick_spheres_spl<8>(stage, chunked);
+        case 1: return stage ? pick_spheres_mode<1, true>(mode) : pick_spheres_mode<1, false>(mode);
+        case 2: return stage ? pick_spheres_mode<2, true>(mode) : pick_spheres_mode<2, false>(mode);
+        case 4: return stage ? pick_spheres_mode<4, true>(mode) : pick_spheres_mode<4, false>(mode);
+        case 8: return stage ? pick_spheres_mode<8, true>(mode) : pick_spheres_mode<8, false>(mode);
         default: return nullptr;
     }
 }
@@ -489,18 +493,22 @@ int occupancy(const void* fn, int threads, size_t smem) {
 
 using ConfigKernel = void (*)(DevArgs, const float*, const float*, uint64_t, int, uint8_t*);
 
-template <int CPT>
-ConfigKernel pick_configs_cpt(bool stage, bool chunked) {
-    if (stage) return chunked ? k_configs<CPT, true, true> : k_configs<CPT, true, false>;
-    return chunked ? k_configs<CPT, false, true> : k_configs<CPT, false, false>;
+template <int CPT, bool STAGE>
+ConfigKernel pick_configs_mode(int mode) {
+    switch (mode) {
+        case kScanPlain: return k_configs<CPT, STAGE, kScanPlain>;
+        case kScanChunked: return k_configs<CPT, STAGE, kScanChunked>;
+        case kScanCompact: return k_configs<CPT, STAGE, kScanCompact>;
+        default: return nullptr;
+    }
 }
 
-ConfigKernel pick_configs(int spl, bool stage, bool chunked) {
+ConfigKernel pick_configs(int spl, bool stage, int mode) {
     switch (spl) {
-        case 2: return pick_configs_cpt<4>(stage, chunked);
-        case 4: return pick_configs_cpt<8>(stage, chunked);
-        case 8: return pick_configs_cpt<16>(stage, chunked);
-        case 16: return pick_configs_cpt<32>(stage, chunked);
+        case 2: return stage ? pick_configs_mode<4, true>(mode) : pick_configs_mode<4, false>(mode);
+        case 4: return stage ? pick_configs_mode<8, true>(mode) : pick_configs_mode<8, false>(mode);
+        case 8: return stage ? pick_configs_mode<16, true>(mode) : pick_configs_mode<16, false>(mode);
+        case 16: return stage ? pick_configs_mode<32, true>(mode) : pick_configs_mode<32, false>(mode);
         default: return nullptr;
     }
 }
@@ -508,7 +516,7 @@ ConfigKernel pick_configs(int spl, bool stage, bool chunked) {
 int launch_configs(const DevArgs& t, const float* centers, const float* radii, uint64_t C, int S, uint8_t* out,
                    const capt_launch_cfg& cfg, cudaStream_t st, std::string& err) {
     const bool stage = cfg.staging == CAPT_STAGE_SMEM && t.stage_floats > 0;
-    ConfigKernel fn = pick_configs(cfg.spheres_per_lane, stage, cfg.chunk != 0);
+    ConfigKernel fn = pick_configs(cfg.spheres_per_lane, stage, cfg.chunk);
     if (!fn) { err = "configuration queries take spheres_per_lane 2, 4, 8 or 16"; return CAPT_E_ARG; }
     const int cpt = 2 * cfg.spheres_per_lane;
     const int warps = std::max(1, std::min(16, (int)cfg.warps_per_block));
@@ -531,7 +539,7 @@ int launch_query(const DevArgs& t, int mode, const float* centers, const float* 
     if (mode == kModeConfigs) return launch_configs(t, centers, radii, n_items, S, out, cfg, st, err);
     const int spl = cfg.spheres_per_lane;
     const bool stage = cfg.staging == CAPT_STAGE_SMEM && t.stage_floats > 0;
-    SphereKernel fn = pick_spheres(spl, stage, cfg.chunk != 0);
+    SphereKernel fn = pick_spheres(spl, stage, cfg.chunk);
     if (!fn) { err = "sphere queries take spheres_per_lane 1, 2, 4 or 8"; return CAPT_E_ARG; }
     const int warps = std::max(1, std::min(16, (int)cfg.warps_per_block));
     const size_t smem = (stage ? stage_offset(t) : 0u) + sphere_scratch_bytes(spl) * (size_t)warps;

@@ -97,23 +97,32 @@ struct RoundEntries {
 //     queued.
 //  3. Queued chunks are scanned 8 at a time: lane l takes block l % 8 of chunks l / 8
 //     and 4 + l / 8, within the entry's set; a hit resolves the entry's group.
-template <bool SINGLE>
+// With COMPACT the sets are the de-duplicated form (t.cleaves, t.clist): a leaf lists
+// the chunks of the Z-ordered cloud that hold a point of its set, and the walk visits
+// those chunks (whole, 32 points each; the union is a superset of the set inside the
+// cloud, so the flags are the same).
+template <bool SINGLE, bool COMPACT>
 __device__ __forceinline__ bool round_chunked(const DevArgs& t, const float* Ts, RoundEntries* re, uint32_t* ghit,
                                               float4 c, uint32_t g, bool live, uint32_t lane, uint32_t lt_mask) {
-    const float4* blocks = reinterpret_cast<const float4*>(t.blocks);
-    const float4* cbox = reinterpret_cast<const float4*>(t.cbox);
+    const float4* blocks = reinterpret_cast<const float4*>(COMPACT ? t.cblocks : t.blocks);
+    const uint64_t plane = COMPACT ? t.cplane : t.plane;
+    const float4* cbox = reinterpret_cast<const float4*>(COMPACT ? t.ccbox : t.cbox);
     bool act = false;
     uint32_t b0 = 0, b1 = 0, nch = 0;
     if (live && (SINGLE || !ghit[g])) {
         const uint32_t leaf = descend(c.x, c.y, c.z, t, Ts);
         float4 a, b;
-        load_leaf(t.leaves, leaf, a, b);
+        load_leaf(COMPACT ? t.cleaves : t.leaves, leaf, a, b);
         const uint32_t cnt = __float_as_uint(b.w);
         act = cnt > 0 && box_dist2(c.x, c.y, c.z, a, b) <= c.w;
         if (act) {
             b0 = __float_as_uint(a.w);
-            b1 = b0 + ((cnt + 3u) >> 2);
-            nch = (b1 - 1u) / kChunkBlocks - b0 / kChunkBlocks + 1u;
+            if (COMPACT) {
+                nch = cnt;   // b0: first entry of the leaf's chunk list
+            } else {
+                b1 = b0 + ((cnt + 3u) >> 2);
+                nch = (b1 - 1u) / kChunkBlocks - b0 / kChunkBlocks + 1u;
+            }
         }
     }
     const uint32_t mask = __ballot_sync(0xffffffffu, act);
@@ -133,21 +142,29 @@ __device__ __forceinline__ bool round_chunked(const DevArgs& t, const float* Ts,
     __syncwarp();
     bool found = false;
     uint32_t nq = 0;   // queued chunks (warp-uniform)
-    uint32_t ei = 0;   // this lane's entry in the chunk walk (monotone)
+    // This lane's (entry, chunk) at position p of the walk.  In the compact form the
+    // position one step ahead is looked up before the current box is tested, so that
+    // its list load overlaps the box load.
+    uint32_t ei = 0, k = 0;
+    auto locate = [&](uint32_t p) {
+        while (re->cend[ei] <= p) ei++;
+        const uint32_t j = p - (ei ? re->cend[ei - 1] : 0u);
+        k = COMPACT ? __ldg(t.clist + re->b0[ei] + j) : re->b0[ei] / kChunkBlocks + j;
+    };
+    if (COMPACT && lane < total) locate(lane);
     for (uint32_t base = 0; base < total; base += 32) {
         // ---- 2. one chunk box per lane ----
         const uint32_t p = base + lane;
+        if (!COMPACT && p < total) locate(p);
+        const uint32_t ec = ei, kc = k;
+        if (COMPACT && p + 32 < total) locate(p + 32);
         bool pass = false;
         uint2 item = make_uint2(0u, 0u);
-        if (p < total) {
-            while (re->cend[ei] <= p) ei++;
-            if (SINGLE || !ghit[re->grp[ei]]) {
-                const float4 ce = re->c[ei];
-                const uint32_t k = re->b0[ei] / kChunkBlocks + (p - (ei ? re->cend[ei - 1] : 0u));
-                const float4 lo = __ldg(cbox + 2 * (size_t)k), hi = __ldg(cbox + 2 * (size_t)k + 1);
-                pass = box_dist2(ce.x, ce.y, ce.z, lo, hi) <= ce.w;
-                item = make_uint2(ei, k);
-            }
+        if (p < total && (SINGLE || !ghit[re->grp[ec]])) {
+            const float4 ce = re->c[ec];
+            const float4 lo = __ldg(cbox + 2 * (size_t)kc), hi = __ldg(cbox + 2 * (size_t)kc + 1);
+            pass = box_dist2(ce.x, ce.y, ce.z, lo, hi) <= ce.w;
+            item = make_uint2(ec, kc);
         }
         const uint32_t pm = __ballot_sync(0xffffffffu, pass);
         if (pass) re->q[nq + __popc(pm & lt_mask)] = item;
@@ -172,9 +189,9 @@ __device__ __forceinline__ bool round_chunked(const DevArgs& t, const float* Ts,
                     const uint2 it = re->q[j];
                     const uint32_t b = it.y * kChunkBlocks + (lane & 7u);
                     gv[v] = re->grp[it.x];
-                    if (b >= re->b0[it.x] && b < re->b1[it.x] && (SINGLE || !ghit[gv[v]])) {
+                    if ((COMPACT || (b >= re->b0[it.x] && b < re->b1[it.x])) && (SINGLE || !ghit[gv[v]])) {
                         const float4 ce = re->c[it.x];
-                        block_d2(blocks, t.plane, (int64_t)b, f2_dup(ce.x), f2_dup(ce.y), f2_dup(ce.z), s01[v], s23[v]);
+                        block_d2(blocks, plane, (int64_t)b, f2_dup(ce.x), f2_dup(ce.y), f2_dup(ce.z), s01[v], s23[v]);
                         r2v[v] = ce.w;
                         v_ok[v] = true;
                     }
@@ -350,12 +367,16 @@ __device__ __forceinline__ bool round_plain(const DevArgs& t, const float* Ts, R
     return found;
 }
 
-// One round over the spheres (c, g) held by lanes < n, chunked (default) or plain.
-template <bool SINGLE, bool CHUNKED = true>
+// Scan modes of a round: whole sets, chunk boxes over the sets, or the compact
+// (de-duplicated) sets.
+enum ScanMode : int { kScanPlain = 0, kScanChunked = 1, kScanCompact = 2 };
+
+// One round over the spheres (c, g) held by lanes < n in the given scan mode.
+template <bool SINGLE, int MODE = kScanChunked>
 __device__ __forceinline__ bool sphere_round(const DevArgs& t, const float* Ts, RoundEntries* re, uint32_t* ghit,
                                              float4 c, uint32_t g, bool live, uint32_t lane, uint32_t lt_mask) {
-    if constexpr (CHUNKED) return round_chunked<SINGLE>(t, Ts, re, ghit, c, g, live, lane, lt_mask);
-    else return round_plain<SINGLE>(t, Ts, re, ghit, c, g, live, lane, lt_mask);
+    if constexpr (MODE == kScanPlain) return round_plain<SINGLE>(t, Ts, re, ghit, c, g, live, lane, lt_mask);
+    else return round_chunked<SINGLE, MODE == kScanCompact>(t, Ts, re, ghit, c, g, live, lane, lt_mask);
 }
 
 }  // namespace capt

@@ -119,6 +119,17 @@ def test_device_calls_reject_unuploaded_tree_without_gpu(capt_lib):
     assert st["device"] == -1 and st["device_bytes"] == 0
 
 
+def test_compact_rejects_unuploaded_tree_without_gpu(capt_lib):
+    """capt_compact needs the uploaded sets; its checks run before any CUDA call."""
+    t = capt_lib.capt_build(W.uniform_cloud(50, 3), 0.01, 0.08)
+    L = capt_lib._load()
+    assert L.capt_compact(t.h, 0, None) == -8                     # not uploaded
+    assert L.capt_compact(None, 0, None) == -1
+    st = capt_lib.capt_stats(t)
+    assert st["compact_chunks"] == st["compact_entries"] == st["compact_bytes"] == st["full_dropped"] == 0
+    assert ctypes.sizeof(capt_lib._Stats) == 120                  # the C struct's size
+
+
 def test_joint_and_filter_calls_reject_bad_arguments_without_gpu(capt_lib):
     """capt_query_joint_configs and sfc_filter_device check their arguments on the host
     before any CUDA call."""
