@@ -169,7 +169,8 @@ const char* capt_last_error(void);
  *          FP32 min / max of its finite coordinates {lo.xyz, 0, hi.xyz, 0}; the scan
  *          skips a chunk whose box the sphere does not reach (exact: a box holding p
  *          is never farther than p)
- * Calling it again re-uploads.  Errors: CAPT_E_ARG, CAPT_E_CUDA, CAPT_E_NOMEM. */
+ * Calling it again re-uploads (and releases any compact form of capt_compact).
+ * Errors: CAPT_E_ARG, CAPT_E_CUDA, CAPT_E_NOMEM. */
 int capt_upload(capt_tree* t, int device, void* stream);
 
 /* De-duplicated ("compact") affordance sets: Alg. 1 copies a point into the set of
