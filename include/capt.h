@@ -188,7 +188,8 @@ int capt_upload(capt_tree* t, int device, void* stream);
  * per list entry.  drop_full = 1 then frees the replicated device sets: the plain and
  * chunked scan modes, edges, joint-angle configurations, clearance and the work
  * counters return CAPT_E_STATE until capt_upload runs again.  capt_upload and
- * capt_free release the compact form.
+ * capt_free release the compact form.  With drop_full, the caller must make sure that no
+ * work queued on other streams still uses the tree (the call synchronises `stream` only).
  * Errors: CAPT_E_ARG, CAPT_E_STATE (not uploaded, or the replicated sets already
  *         dropped), CAPT_E_RANGE (more than 1.6M chunks), CAPT_E_NOMEM, CAPT_E_CUDA. */
 int capt_compact(capt_tree* t, int drop_full, void* stream);
