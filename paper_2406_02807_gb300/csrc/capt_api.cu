@@ -115,7 +115,7 @@ struct capt_tree {
         cfg[CAPT_KERNEL_SPHERES] = {8, 2, CAPT_STAGE_SMEM, 0};
         cfg[CAPT_KERNEL_CONFIGS] = {4, 8, CAPT_STAGE_GLOBAL, 1};
         cfg[CAPT_KERNEL_EDGES] = {8, 2, CAPT_STAGE_SMEM, 32};
-        cfg[CAPT_KERNEL_CLEARANCE] = {8, 2, CAPT_STAGE_SMEM, 0};
+        cfg[CAPT_KERNEL_CLEARANCE] = {16, 2, CAPT_STAGE_GLOBAL, 0};
         cfg[CAPT_KERNEL_JOINTS] = {4, 1, CAPT_STAGE_GLOBAL, 0};
     }
 

@@ -10,12 +10,13 @@
 //     contiguous range of its waypoints (close in space, so the block's warps share set
 //     blocks in L1); passes of 128 consecutive spheres (4 per lane, three 16-byte
 //     loads): a sphere farther than r_max from the cloud's bounding box is farther than
-//     r_max from every point, so it gets d = r_max, argmin = -1 at once; the others are
+//     r_max from every point, so it gets d = r_max, argmin = -1 at once (one 16-byte
+//     store per output when all four of a lane's spheres are that far); the others are
 //     queued.  No block barrier: a warp leaves as soon as its range is done.  Rounds
 //     of 32 queued spheres: descent and leaf box test against r_max; each set of a
 //     sphere that passes is scanned in full by the whole warp in packed FP32x2
 //     arithmetic, every lane keeping a running minimum of (d^2, slot) keys, reduced by
-//     one butterfly per set.
+//     two warp-wide 32-bit minimum reductions per set.
 //  2. Costs (k_clearance_cost): one warp per trajectory sums each waypoint's terms in a
 //     fixed order (lane-strided, then a butterfly) and adds the waypoints in order, so
 //     the cost is bitwise reproducible whatever the launch configuration.
@@ -38,8 +39,8 @@ struct ClearScratch {
 // One round over the first n queued spheres of the trajectory at `tbase` (sphere index
 // offset of the trajectory in dist / argmin).  Spheres passing the leaf box test are
 // scanned one at a time by the whole warp: lanes stride over the set's 4-point blocks
-// (two blocks in flight per lane) keeping a running minimum of (d^2, slot) keys, and one
-// butterfly per set reduces the 32 minima.  The lowest key is the smallest FP32 squared
+// (two blocks in flight per lane) keeping a running minimum of (d^2, slot) keys, and two
+// 32-bit warp reductions per set (d^2, then the slot) give the smallest key.  The lowest key is the smallest FP32 squared
 // distance, ties going to the lowest slot, i.e. the lowest point index.
 __device__ __forceinline__ void clearance_round(const DevArgs& t, const float* Ts, ClearScratch* ws, uint32_t n,
                                                 uint64_t tbase, float rmax, float rmax2, float* __restrict__ dist,
@@ -95,10 +96,14 @@ __device__ __forceinline__ void clearance_round(const DevArgs& t, const float* T
             fold(r + 32);
         }
         if (r < nbs) fold(r);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
-            best = other < best ? other : best;
+        // minimum key over the warp in two 32-bit reductions: the smallest d^2 (the bits
+        // of a non-negative float order as unsigned integers), then the smallest slot
+        // among the lanes that hold it
+        {
+            const uint32_t hi = (uint32_t)(best >> 32);
+            const uint32_t mhi = __reduce_min_sync(0xffffffffu, hi);
+            const uint32_t mlo = __reduce_min_sync(0xffffffffu, hi == mhi ? (uint32_t)best : 0xffffffffu);
+            best = ((unsigned long long)mhi << 32) | mlo;
         }
         if (lane == (uint32_t)src) {
             const float dd = __fsqrt_rn(__uint_as_float((uint32_t)(best >> 32)));
@@ -141,37 +146,47 @@ __global__ void __launch_bounds__(512, 2) k_clearance_dist(DevArgs t, const floa
     const uint32_t w_lo = (uint32_t)(((uint64_t)W * warp) / nw), w_hi = (uint32_t)(((uint64_t)W * (warp + 1)) / nw);
     const uint64_t tbase = traj * (uint64_t)W * (uint64_t)S;        // first sphere of the trajectory
     const uint32_t s_lo = w_lo * (uint32_t)S, s_hi = w_hi * (uint32_t)S;   // this warp's spheres
-    const float* base = centers + 3 * tbase;
     uint32_t n_q = 0;
     for (uint32_t p0 = s_lo; p0 < s_hi; p0 += 128) {
-        const uint32_t i0 = p0 + 4 * lane;
-        const uint32_t nv = i0 < s_hi ? min(4u, s_hi - i0) : 0u;
+        const uint64_t i0 = tbase + p0 + 4 * lane;
+        const uint32_t nv = p0 + 4 * lane < s_hi ? min(4u, s_hi - (p0 + 4 * lane)) : 0u;
+        const float* src = centers + 3 * i0;
         float v[12];
-        if (nv == 4 && ((reinterpret_cast<uintptr_t>(base + 3 * (size_t)i0) & 15u) == 0)) {
-            const float4* q = reinterpret_cast<const float4*>(base + 3 * (size_t)i0);
+        if (nv == 4 && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0)) {
+            const float4* q = reinterpret_cast<const float4*>(src);
             const float4 a = __ldg(q), b = __ldg(q + 1), cc = __ldg(q + 2);
             v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
             v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
             v[8] = cc.x; v[9] = cc.y; v[10] = cc.z; v[11] = cc.w;
         } else {
 #pragma unroll
-            for (int k = 0; k < 12; k++) v[k] = (uint32_t)(k / 3) < nv ? __ldg(base + 3 * (size_t)i0 + k) : 0.f;
+            for (int k = 0; k < 12; k++) v[k] = (uint32_t)(k / 3) < nv ? __ldg(src + k) : 0.f;
+        }
+        // farther than r_max from the cloud's box: farther than r_max from every point
+        bool nr[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            nr[k] = (uint32_t)k < nv && box_dist2(v[3 * k], v[3 * k + 1], v[3 * k + 2], rlo, rhi) <= rmax2;
+        // the common case, four spheres all far: one 16-byte store for each output
+        const bool all_far = nv == 4 && !(nr[0] | nr[1] | nr[2] | nr[3]) &&
+                             ((reinterpret_cast<uintptr_t>(dist + i0) | reinterpret_cast<uintptr_t>(argmin + i0)) &
+                              15u) == 0;
+        if (all_far) {
+            *reinterpret_cast<float4*>(dist + i0) = make_float4(rmax, rmax, rmax, rmax);
+            *reinterpret_cast<int4*>(argmin + i0) = make_int4(-1, -1, -1, -1);
         }
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            const float x = v[3 * k], y = v[3 * k + 1], z = v[3 * k + 2];
-            const bool valid = (uint32_t)k < nv;
-            // farther than r_max from the cloud's box: farther than r_max from every point
-            const bool near = valid && box_dist2(x, y, z, rlo, rhi) <= rmax2;
-            if (valid && !near) {
-                dist[tbase + i0 + k] = rmax;
-                argmin[tbase + i0 + k] = -1;
+            const bool near = nr[k];
+            if ((uint32_t)k < nv && !near && !all_far) {
+                dist[i0 + k] = rmax;
+                argmin[i0 + k] = -1;
             }
             const uint32_t mask = __ballot_sync(0xffffffffu, near);
             if (near) {
                 const uint32_t pos = n_q + __popc(mask & lt_mask);
-                ws->nq[pos] = make_float4(x, y, z, 0.f);
-                ws->ni[pos] = tbase + i0 + k;
+                ws->nq[pos] = make_float4(v[3 * k], v[3 * k + 1], v[3 * k + 2], 0.f);
+                ws->ni[pos] = i0 + k;
             }
             n_q += __popc(mask);
         }

@@ -409,7 +409,7 @@ def test_clearance_cost_is_reproducible(tabletop, capt_lib, torch_):
         capt_lib.capt_set_launch_cfg(tabletop["ctree"], capt_lib.CAPT_KERNEL_CLEARANCE, w, 2, w % 2)
         b = capt_lib.capt_clearance_fwd(tabletop["ctree"], cen, r, 0.01)[0].cpu().numpy()
         assert np.array_equal(a, b)
-    capt_lib.capt_set_launch_cfg(tabletop["ctree"], capt_lib.CAPT_KERNEL_CLEARANCE, 8, 2, 1)
+    capt_lib.capt_set_launch_cfg(tabletop["ctree"], capt_lib.CAPT_KERNEL_CLEARANCE, 16, 2, 0)
 
 
 def test_clearance_backward_against_oracle_and_fd(tabletop, orc, capt_lib, torch_):
