@@ -88,7 +88,6 @@ class Clocks:
     def stop(self):
         if self.proc is None:
             return None
-        time.sleep(0.25)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -112,6 +111,15 @@ class Clocks:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def keep_busy(torch, step, seconds):
+    """Run `step` back to back (untimed) for about `seconds`."""
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        for _ in range(8):
+            step()
+        torch.cuda.synchronize()
 
 
 def dist_setup(args):
@@ -337,15 +345,21 @@ def main():
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
-    if pg:
-        pg.barrier()
+    # the timed region lasts milliseconds and nvidia-smi samples every 100 ms: the same
+    # steps run untimed for a few hundred ms on both sides of it, so that every clock
+    # sample is taken under this load
     clocks = Clocks(local)
     clocks.start()
-    ms = time_events(torch, step, args.steps, stream)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
+    keep_busy(torch, step, 0.4)
     if pg:
         pg.barrier()
+    ms = time_events(torch, step, args.steps, stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    keep_busy(torch, step, 0.3)
+    clk = clocks.stop()
+    if pg:
         ms = max_over_ranks(ms, pg, dev)
     value = world * C * SPHERES / (ms / 1e3)
     collide = float(flags.float().mean().item())
