@@ -19,6 +19,7 @@
 // collide.  capt_edge_plan_create captures both launches into a CUDA graph.
 // Per-edge mode (the baseline): one kernel launch per edge.
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "device_common.cuh"
@@ -37,7 +38,12 @@ struct ArmPlan {
     int32_t sbeg[CAPT_MAX_JOINTS + 1];   // spheres of link j: [sbeg[j], sbeg[j + 1])
     float off[CAPT_MAX_SPHERES][3];      // offsets in the link frame, in that order
     float r2[CAPT_MAX_SPHERES];          // fl(r * r), in that order
+    // per link: a bounding sphere of its spheres (centre offset in the link frame) and
+    // the squared box distance beyond which none of them can reach the cloud's box
+    float cull_o[CAPT_MAX_JOINTS][3];
+    float cull_t[CAPT_MAX_JOINTS];
 };
+
 
 ArmPlan make_plan(const capt_arm& a) {
     ArmPlan p{};
@@ -59,6 +65,46 @@ ArmPlan make_plan(const capt_arm& a) {
             }
     }
     p.sbeg[a.n_joints] = n;
+    // Link culling bound.  The FP32 centre of sphere s lies within |o_s - o_b| of the
+    // FP32 centre of the bounding point o_b up to rounding (R is orthonormal to a few
+    // ulps after at most 16 rotations), so a sphere whose FP32 box test passes has its
+    // bounding point within rho = max_s(|o_s - o_b| + r_s) of the box, plus rounding;
+    // delta = 1e-4 (1 + M), with M a bound on every coordinate the chain produces, is
+    // orders of magnitude above that rounding.  A lane whose bounding point is farther
+    // than rho + delta (squared, with a relative margin) has no sphere of the link near.
+    double M = 1.0;
+    for (int d = 0; d < 3; d++) M += std::fabs((double)a.base[d]);
+    for (int j = 0; j < a.n_joints; j++)
+        M += std::fabs((double)a.link[j][0]) + std::fabs((double)a.link[j][1]) + std::fabs((double)a.link[j][2]);
+    double omax = 0.0;
+    for (int i = 0; i < n; i++)
+        omax = std::max(omax, std::fabs((double)p.off[i][0]) + std::fabs((double)p.off[i][1]) +
+                                  std::fabs((double)p.off[i][2]) + std::sqrt((double)p.r2[i]));
+    M += omax;
+    const double delta = 1e-4 * M;
+    for (int j = 0; j < a.n_joints; j++) {
+        p.cull_t[j] = INFINITY;
+        p.cull_o[j][0] = p.cull_o[j][1] = p.cull_o[j][2] = 0.f;
+        if (p.sbeg[j + 1] == p.sbeg[j]) continue;
+        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int i = p.sbeg[j]; i < p.sbeg[j + 1]; i++)
+            for (int d = 0; d < 3; d++) {
+                lo[d] = std::min(lo[d], (double)p.off[i][d]);
+                hi[d] = std::max(hi[d], (double)p.off[i][d]);
+            }
+        double ob[3];
+        for (int d = 0; d < 3; d++) {
+            p.cull_o[j][d] = (float)((lo[d] + hi[d]) / 2);
+            ob[d] = p.cull_o[j][d];
+        }
+        double rho = 0.0;
+        for (int i = p.sbeg[j]; i < p.sbeg[j + 1]; i++) {
+            const double dx = p.off[i][0] - ob[0], dy = p.off[i][1] - ob[1], dz = p.off[i][2] - ob[2];
+            rho = std::max(rho, std::sqrt(dx * dx + dy * dy + dz * dz) + std::sqrt((double)p.r2[i]));
+        }
+        const double tt = (rho + delta) * (rho + delta) * (1.0 + 1e-5);
+        p.cull_t[j] = std::isfinite(tt) ? std::nextafter((float)tt, INFINITY) : INFINITY;
+    }
     return p;
 }
 
@@ -110,6 +156,39 @@ __device__ __forceinline__ float row_dot(const float R[9], int r, float v0, floa
     return __fadd_rn(__fadd_rn(__fmul_rn(R[3 * r], v0), __fmul_rn(R[3 * r + 1], v1)), __fmul_rn(R[3 * r + 2], v2));
 }
 
+// Centres p + R o of one link's points: x and y as an FP32x2 pair (each element the
+// scalar expression p_r + ((R_r0 o_0 + R_r1 o_1) + R_r2 o_2), rounded the same way), z
+// alone.  Set up once per link from its frame.
+struct LinkXform {
+    uint64_t c0, c1, c2, p01;   // {R00, R10}, {R01, R11}, {R02, R12}, {p0, p1}
+    float r20, r21, r22, p2;
+    __device__ __forceinline__ void set(const float R[9], const float p[3]) {
+        asm("mov.b64 %0, {%1, %2};" : "=l"(c0) : "f"(R[0]), "f"(R[3]));
+        asm("mov.b64 %0, {%1, %2};" : "=l"(c1) : "f"(R[1]), "f"(R[4]));
+        asm("mov.b64 %0, {%1, %2};" : "=l"(c2) : "f"(R[2]), "f"(R[5]));
+        asm("mov.b64 %0, {%1, %2};" : "=l"(p01) : "f"(p[0]), "f"(p[1]));
+        r20 = R[6];
+        r21 = R[7];
+        r22 = R[8];
+        p2 = p[2];
+    }
+    __device__ __forceinline__ void apply(float ox, float oy, float oz, float& cx, float& cy, float& cz) const {
+        const uint64_t xy =
+            f2_add(p01, f2_add(f2_add(f2_mul(c0, f2_dup(ox)), f2_mul(c1, f2_dup(oy))), f2_mul(c2, f2_dup(oz))));
+        const float2 v = f2_split(xy);
+        cx = v.x;
+        cy = v.y;
+        cz = __fadd_rn(p2, __fadd_rn(__fadd_rn(__fmul_rn(r20, ox), __fmul_rn(r21, oy)), __fmul_rn(r22, oz)));
+    }
+};
+
+__device__ __forceinline__ void link_point(const float R[9], const float p[3], float ox, float oy, float oz, float& cx,
+                                           float& cy, float& cz) {
+    cx = __fadd_rn(p[0], row_dot(R, 0, ox, oy, oz));
+    cy = __fadd_rn(p[1], row_dot(R, 1, ox, oy, oz));
+    cz = __fadd_rn(p[2], row_dot(R, 2, ox, oy, oz));
+}
+
 struct EdgeScratch {
     float4 nc[64];   // queued near spheres (< 32 left over + 32 from one sphere step)
     RoundEntries re;
@@ -138,11 +217,20 @@ __device__ bool edge_pass(const DevArgs& t, const ArmPlan& arm, const float* __r
         float sj, cj;
         sincos_cw(q, sj, cj);
         rotate_frame(R, arm.axis[j], sj, cj);
-        for (int i = arm.sbeg[j]; i < arm.sbeg[j + 1]; i++) {
+        int i_end = arm.sbeg[j + 1];
+        if (arm.sbeg[j] < i_end) {
+            // no lane's bounding sphere of this link reaches the cloud's box: none of the
+            // link's spheres can come near it (the configurations of a pass lie on one
+            // edge, so their links are near or far together more often than not)
+            float bx, by, bz;
+            link_point(R, p, arm.cull_o[j][0], arm.cull_o[j][1], arm.cull_o[j][2], bx, by, bz);
+            const bool ln = live && box_dist2(bx, by, bz, rlo, rhi) <= arm.cull_t[j];
+            if (!__any_sync(0xffffffffu, ln)) i_end = arm.sbeg[j];
+        }
+        for (int i = arm.sbeg[j]; i < i_end; i++) {
             const float ox = arm.off[i][0], oy = arm.off[i][1], oz = arm.off[i][2];
-            const float cx = __fadd_rn(p[0], row_dot(R, 0, ox, oy, oz));
-            const float cy = __fadd_rn(p[1], row_dot(R, 1, ox, oy, oz));
-            const float cz = __fadd_rn(p[2], row_dot(R, 2, ox, oy, oz));
+            float cx, cy, cz;
+            link_point(R, p, ox, oy, oz, cx, cy, cz);
             const float r2 = arm.r2[i];
             const bool near = live && box_dist2(cx, cy, cz, rlo, rhi) <= r2;
             const uint32_t mask = __ballot_sync(0xffffffffu, near);
@@ -339,11 +427,12 @@ __global__ void __launch_bounds__(512, 2) k_joint_configs(DevArgs t, const __gri
             float sj, cj;
             sincos_cw(live ? __ldg(qk + j) : 0.f, sj, cj);
             rotate_frame(R, arm.axis[j], sj, cj);
+            LinkXform X;
+            X.set(R, p);
             for (int i = arm.sbeg[j]; i < arm.sbeg[j + 1]; i++) {
                 const float ox = arm.off[i][0], oy = arm.off[i][1], oz = arm.off[i][2];
-                const float cx = __fadd_rn(p[0], row_dot(R, 0, ox, oy, oz));
-                const float cy = __fadd_rn(p[1], row_dot(R, 1, ox, oy, oz));
-                const float cz = __fadd_rn(p[2], row_dot(R, 2, ox, oy, oz));
+                float cx, cy, cz;
+                X.apply(ox, oy, oz, cx, cy, cz);
                 const float r2 = arm.r2[i];
                 const bool near = !done && box_dist2(cx, cy, cz, rlo, rhi) <= r2;
                 const uint32_t mask = __ballot_sync(0xffffffffu, near);
