@@ -19,6 +19,12 @@
  *    is the legacy default stream).  Errors found while queueing are returned; errors
  *    found by a kernel (a bounded wait that gave up) are latched in the tree's device
  *    status word, read by capt_device_status().
+ *  - The sphere, configuration and joint-angle queries hand tiles to their warps from a
+ *    work counter of the tree (one of 64, zeroed on `stream` before the launch, once
+ *    the launch that last used it has finished, through an event the library records).
+ *    Queries on one tree may therefore run on several streams and host threads at
+ *    once.  Inside a stream capture they use a fixed tile order instead, so a captured
+ *    graph holds no hidden state and replays exactly.
  *  - Queries assume r_min <= r <= r_max (Lemma 1's hypothesis).  Outside that range
  *    the flag is unspecified (it is still computed, never faults).  Non-finite
  *    centres give unspecified flags and never fault.

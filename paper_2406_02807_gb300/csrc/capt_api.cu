@@ -67,6 +67,10 @@ bool valid_cfg(int kernel, const capt_launch_cfg& c) {
 
 }  // namespace
 
+// Device status allocation: the latched status word (first 256 bytes), then the work
+// counters of the query kernels.
+constexpr size_t kStatusBytes = 256 + 64 * sizeof(unsigned long long);
+
 struct capt_tree {
     capt::HostTree h;
     int device = -1;
@@ -109,6 +113,15 @@ struct capt_tree {
     // live edge plans (their graphs hold the device pointers); shared so that a plan
     // freed after its tree does not touch the tree
     std::shared_ptr<std::atomic<int>> n_plans = std::make_shared<std::atomic<int>>(0);
+    // work counters of the persistent query kernels (dynamic tile scheduling), in the
+    // status allocation after its first 256 bytes; a slot is zeroed for a launch only
+    // after the launch that last used it has finished (its event)
+    static constexpr int kCtrSlots = 64;
+    unsigned long long* d_ctr = nullptr;
+    mutable cudaEvent_t ctr_ev[kCtrSlots] = {};
+    mutable bool ctr_pending[kCtrSlots] = {};
+    mutable uint32_t ctr_next = 0;
+    mutable std::mutex ctr_mu;
     std::mutex mu;
 
     capt_tree() {
@@ -160,6 +173,12 @@ struct capt_tree {
             if (p) cudaFree(p);
         cs.release();
         full_dropped = false;
+        for (int i = 0; i < kCtrSlots; i++) {
+            if (ctr_ev[i]) cudaEventDestroy(ctr_ev[i]);
+            ctr_ev[i] = nullptr;
+            ctr_pending[i] = false;
+        }
+        d_ctr = nullptr;   // part of the status allocation
         for (auto& e : pipe_ev)
             if (e) cudaEventDestroy(e);
         if (pipe_stream) cudaStreamDestroy(pipe_stream);
@@ -211,6 +230,38 @@ int check_full(const capt_tree* t) {
     if (t->full_dropped)
         return fail(CAPT_E_STATE, "the replicated sets were dropped by capt_compact (only the compact scan remains)");
     return CAPT_OK;
+}
+
+// Launch a persistent query kernel with dynamic tile scheduling: it gets a counter slot
+// of the tree's pool, zeroed on `st` after the launch that last used the slot has
+// finished.  Inside a stream capture the launch keeps the static schedule (no counter,
+// no events), so a captured graph has no hidden state.
+template <class F>
+int with_counter(const capt_tree* t, cudaStream_t st, F&& launch) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (!t->d_ctr || cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return launch(nullptr);
+    }
+    std::lock_guard<std::mutex> lk(t->ctr_mu);
+    const int slot = (int)(t->ctr_next++ % capt_tree::kCtrSlots);
+    if (!t->ctr_ev[slot] && cudaEventCreateWithFlags(&t->ctr_ev[slot], cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        t->ctr_ev[slot] = nullptr;
+        return launch(nullptr);
+    }
+    cudaError_t e = cudaSuccess;
+    if (t->ctr_pending[slot]) e = cudaStreamWaitEvent(st, t->ctr_ev[slot], 0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(t->d_ctr + slot, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return cuda_fail(e, "work counter");
+    const int rc = launch(t->d_ctr + slot);
+    e = cudaEventRecord(t->ctr_ev[slot], st);
+    if (e != cudaSuccess) {
+        t->ctr_pending[slot] = false;
+        return rc ? rc : cuda_fail(e, "work counter event");
+    }
+    t->ctr_pending[slot] = true;
+    return rc;
 }
 
 // The scan mode of a sphere / configuration launch has its data on the device.
@@ -368,8 +419,8 @@ int capt_build_device(const float* d_points, size_t n, float r_min, float r_max,
     int* status = nullptr;
     void* cbox = nullptr;
     const size_t sz_cbox = capt::chunk_count(d.total_blocks) * 8 * sizeof(float);
-    cudaError_t e = cudaMalloc((void**)&status, 256);
-    if (e == cudaSuccess) e = cudaMemset(status, 0, 256);
+    cudaError_t e = cudaMalloc((void**)&status, kStatusBytes);
+    if (e == cudaSuccess) e = cudaMemset(status, 0, kStatusBytes);
     if (e == cudaSuccess) e = cudaMalloc(&cbox, sz_cbox);
     if (e == cudaSuccess) {
         const cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -400,6 +451,7 @@ int capt_build_device(const float* d_points, size_t n, float r_min, float r_max,
     t->d_cloud = d.cloud;
     t->d_cbox = cbox;
     t->d_status = status;
+    t->d_ctr = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(status) + 256);
     t->d_Tplain = d.Tplain;
     t->d_set_idx = d.set_idx;
     t->d_set_begin = d.set_begin;
@@ -415,7 +467,7 @@ int capt_build_device(const float* d_points, size_t n, float r_min, float r_max,
         t->box_lo[k] = d.box_lo[k];
         t->box_hi[k] = d.box_hi[k];
     }
-    t->dev_bytes = d.bytes + sz_cbox + 256;
+    t->dev_bytes = d.bytes + sz_cbox + kStatusBytes;
     t->host_pending = true;
     h.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     *out = t;
@@ -582,8 +634,9 @@ int capt_upload(capt_tree* t, int device, void* stream) {
     if ((rc = alloc(&t->d_T, sz_T, "T")) || (rc = alloc(&t->d_leaves, sz_leaves, "leaves")) ||
         (rc = alloc(&t->d_blocks, sz_blocks, "blocks")) || (rc = alloc(&t->d_ids, sz_ids, "ids")) ||
         (rc = alloc(&t->d_cloud, sz_cloud, "cloud")) || (rc = alloc(&t->d_cbox, sz_cbox, "chunk boxes")) ||
-        (rc = alloc((void**)&t->d_status, 256, "status")))
+        (rc = alloc((void**)&t->d_status, kStatusBytes, "status")))
         return rc;
+    t->d_ctr = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(t->d_status) + 256);
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMemcpyAsync(t->d_T, bs.data.data(), sz_T, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(t->d_leaves, lay.leaves.data(), sz_leaves, cudaMemcpyHostToDevice, st);
@@ -591,7 +644,7 @@ int capt_upload(capt_tree* t, int device, void* stream) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(t->d_ids, lay.ids.data(), sz_ids, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !h.pts.empty())
         e = cudaMemcpyAsync(t->d_cloud, h.pts.data(), h.pts.size() * sizeof(float), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(t->d_status, 0, 256, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(t->d_status, 0, kStatusBytes, st);
     if (e == cudaSuccess) {
         std::string cerr;
         if (capt::launch_chunk_boxes(static_cast<const float*>(t->d_blocks), lay.total_blocks,
@@ -619,7 +672,7 @@ int capt_upload(capt_tree* t, int device, void* stream) {
     t->Ks = bs.Ks;
     t->tail_staged = bs.tail_staged;
     t->stage_floats = bs.stage_floats;
-    t->dev_bytes = sz_T + sz_leaves + sz_blocks + sz_ids + sz_cloud + sz_cbox + 256;
+    t->dev_bytes = sz_T + sz_leaves + sz_blocks + sz_ids + sz_cloud + sz_cbox + kStatusBytes;
     return CAPT_OK;
 }
 
@@ -674,8 +727,10 @@ int capt_query_spheres(const capt_tree* t, const float* d_centers, const float* 
     if (!d_centers || !d_radii || !d_flags) return fail(CAPT_E_ARG, "NULL device pointer");
     if ((rc = check_scan(t, t->cfg[CAPT_KERNEL_SPHERES]))) return rc;
     std::string err;
-    rc = capt::launch_query(t->args(), capt::kModeSpheres, d_centers, d_radii, m, 1, d_flags,
-                            t->cfg[CAPT_KERNEL_SPHERES], static_cast<cudaStream_t>(stream), err);
+    rc = with_counter(t, static_cast<cudaStream_t>(stream), [&](unsigned long long* ctr) {
+        return capt::launch_query(t->args(), capt::kModeSpheres, d_centers, d_radii, m, 1, d_flags,
+                                  t->cfg[CAPT_KERNEL_SPHERES], ctr, static_cast<cudaStream_t>(stream), err);
+    });
     return rc ? fail(rc, err) : CAPT_OK;
 }
 
@@ -688,8 +743,10 @@ int capt_query_configs(const capt_tree* t, const float* d_centers, const float* 
     if (!d_centers || !d_radii || !d_flags) return fail(CAPT_E_ARG, "NULL device pointer");
     if ((rc = check_scan(t, t->cfg[CAPT_KERNEL_CONFIGS]))) return rc;
     std::string err;
-    rc = capt::launch_query(t->args(), capt::kModeConfigs, d_centers, d_radii, C, S, d_flags,
-                            t->cfg[CAPT_KERNEL_CONFIGS], static_cast<cudaStream_t>(stream), err);
+    rc = with_counter(t, static_cast<cudaStream_t>(stream), [&](unsigned long long* ctr) {
+        return capt::launch_query(t->args(), capt::kModeConfigs, d_centers, d_radii, C, S, d_flags,
+                                  t->cfg[CAPT_KERNEL_CONFIGS], ctr, static_cast<cudaStream_t>(stream), err);
+    });
     return rc ? fail(rc, err) : CAPT_OK;
 }
 
@@ -715,13 +772,17 @@ int capt_query_configs_host(capt_tree* t, const float* h_centers, const float* h
         CUDA_TRY(cudaMemcpyAsync(d_r, h_radii, (size_t)S * sizeof(float), cudaMemcpyHostToDevice, user), "radii H2D");
         void* df = const_cast<void*>(mapped_device_pointer(h_flags));
         if (df) {
-            rc = capt::launch_query(t->args(), capt::kModeConfigs, static_cast<const float*>(dc), d_r, C, S,
-                                    static_cast<uint8_t*>(df), t->cfg[CAPT_KERNEL_CONFIGS], user, err);
+            rc = with_counter(t, user, [&](unsigned long long* ctr) {
+                return capt::launch_query(t->args(), capt::kModeConfigs, static_cast<const float*>(dc), d_r, C, S,
+                                          static_cast<uint8_t*>(df), t->cfg[CAPT_KERNEL_CONFIGS], ctr, user, err);
+            });
             if (rc) return fail(rc, err);
         } else {
             if (!ensure_flags(t, C)) return fail(CAPT_E_NOMEM, "cudaMalloc of the flag buffer failed");
-            rc = capt::launch_query(t->args(), capt::kModeConfigs, static_cast<const float*>(dc), d_r, C, S,
-                                    t->d_zc_flags, t->cfg[CAPT_KERNEL_CONFIGS], user, err);
+            rc = with_counter(t, user, [&](unsigned long long* ctr) {
+                return capt::launch_query(t->args(), capt::kModeConfigs, static_cast<const float*>(dc), d_r, C, S,
+                                          t->d_zc_flags, t->cfg[CAPT_KERNEL_CONFIGS], ctr, user, err);
+            });
             if (rc) return fail(rc, err);
             CUDA_TRY(cudaMemcpyAsync(h_flags, t->d_zc_flags, C, cudaMemcpyDeviceToHost, user), "flags D2H");
         }
@@ -750,8 +811,10 @@ int capt_query_configs_host(capt_tree* t, const float* h_centers, const float* h
                  "centres H2D");
         CUDA_TRY(cudaEventRecord(t->pipe_ev[3], cp), "event record");
         CUDA_TRY(cudaStreamWaitEvent(user, t->pipe_ev[3], 0), "wait copy");
-        rc = capt::launch_query(t->args(), capt::kModeConfigs, t->d_pipe_c[b], d_r, cn, S, t->d_pipe_f[b],
-                                t->cfg[CAPT_KERNEL_CONFIGS], user, err);
+        rc = with_counter(t, user, [&](unsigned long long* ctr) {
+            return capt::launch_query(t->args(), capt::kModeConfigs, t->d_pipe_c[b], d_r, cn, S, t->d_pipe_f[b],
+                                      t->cfg[CAPT_KERNEL_CONFIGS], ctr, user, err);
+        });
         if (rc) return fail(rc, err);
         CUDA_TRY(cudaMemcpyAsync(h_flags + c0, t->d_pipe_f[b], cn, cudaMemcpyDeviceToHost, user), "flags D2H");
         CUDA_TRY(cudaEventRecord(t->pipe_ev[b], user), "event record");
@@ -827,7 +890,9 @@ int autotune_query(capt_tree* t, int kernel, const std::vector<capt_launch_cfg>&
         float tt = INFINITY;
         for (int rep = 0; rep < 3; rep++) {
             cudaEventRecord(e0, st);
-            rc = capt::launch_query(t->args(), mode, d_centers, d_radii, n, S, d_flags, c, st, err);
+            rc = with_counter(t, st, [&](unsigned long long* ctr) {
+                return capt::launch_query(t->args(), mode, d_centers, d_radii, n, S, d_flags, c, ctr, st, err);
+            });
             cudaEventRecord(e1, st);
             if (rc) break;
             if (cudaEventSynchronize(e1) != cudaSuccess) { rc = CAPT_E_CUDA; break; }
@@ -971,8 +1036,10 @@ int capt_query_joint_configs(const capt_tree* t, const capt_arm* arm, const floa
     if (C == 0) return CAPT_OK;
     if (!d_q || !d_flags) return fail(CAPT_E_ARG, "NULL device pointer");
     std::string err;
-    rc = capt::launch_joint_configs(t->args(), *arm, d_q, C, d_flags, t->cfg[CAPT_KERNEL_JOINTS],
-                                    static_cast<cudaStream_t>(stream), err);
+    rc = with_counter(t, static_cast<cudaStream_t>(stream), [&](unsigned long long* ctr) {
+        return capt::launch_joint_configs(t->args(), *arm, d_q, C, d_flags, t->cfg[CAPT_KERNEL_JOINTS], ctr,
+                                          static_cast<cudaStream_t>(stream), err);
+    });
     return rc ? fail(rc, err) : CAPT_OK;
 }
 
@@ -996,7 +1063,9 @@ int capt_autotune_joint_configs(capt_tree* t, const capt_arm* arm, const float* 
             float tt = INFINITY;
             for (int rep = 0; rep < 3; rep++) {
                 cudaEventRecord(e0, st);
-                rc = capt::launch_joint_configs(t->args(), *arm, d_q, C, d_flags, c, st, err);
+                rc = with_counter(t, st, [&](unsigned long long* ctr) {
+                    return capt::launch_joint_configs(t->args(), *arm, d_q, C, d_flags, c, ctr, st, err);
+                });
                 cudaEventRecord(e1, st);
                 if (rc) break;
                 if (cudaEventSynchronize(e1) != cudaSuccess) { rc = CAPT_E_CUDA; break; }

@@ -185,6 +185,22 @@ __device__ __forceinline__ float fkey_float(uint32_t k) {
 }
 
 // Inclusive warp prefix sum.
+// Work scheduling of the persistent query kernels: with a counter (zeroed before the
+// launch) a warp takes the next unclaimed tile whenever it needs one, so warps that
+// draw cheap tiles take more of them; without one, warp w of the grid takes tiles
+// w, w + warps, w + 2 warps, ...
+struct TileSched {
+    unsigned long long* ctr;
+    uint64_t stride;
+    __device__ __forceinline__ uint64_t first(uint64_t w) const { return ctr ? take() : w; }
+    __device__ __forceinline__ uint64_t next(uint64_t cur) const { return ctr ? take() : cur + stride; }
+    __device__ __forceinline__ uint64_t take() const {
+        unsigned long long v = 0;
+        if ((threadIdx.x & 31u) == 0) v = atomicAdd(ctr, 1ull);
+        return __shfl_sync(0xffffffffu, v, 0);
+    }
+};
+
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
     const uint32_t lane = lane_id();
 #pragma unroll

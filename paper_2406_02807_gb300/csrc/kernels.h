@@ -12,8 +12,11 @@ namespace capt {
 enum QueryMode { kModeSpheres = 0, kModeConfigs = 1 };
 
 // Persistent query kernel: flags per sphere (mode 0) or per configuration (mode 1).
+// ctr: a work counter zeroed on st before the launch (the warps take tiles from it), or
+// nullptr for the static schedule (warp w takes tiles w, w + warps, ...).
 int launch_query(const DevArgs& t, int mode, const float* centers, const float* radii, uint64_t n_items, int S,
-                 uint8_t* out, const capt_launch_cfg& cfg, cudaStream_t st, std::string& err);
+                 uint8_t* out, const capt_launch_cfg& cfg, unsigned long long* ctr, cudaStream_t st,
+                 std::string& err);
 
 // Sequential Alg. 3 work counters for configuration queries.
 int launch_count_configs(const DevArgs& t, const float* centers, const float* radii, uint64_t C, int S,
@@ -44,7 +47,7 @@ int launch_edges_per_edge(const DevArgs& t, const capt_arm& arm, const float* qa
 
 // Configurations given by joint angles q [C][J]: kinematics in-kernel, one flag each.
 int launch_joint_configs(const DevArgs& t, const capt_arm& arm, const float* q, uint64_t C, uint8_t* out,
-                         const capt_launch_cfg& cfg, cudaStream_t st, std::string& err);
+                         const capt_launch_cfg& cfg, unsigned long long* ctr, cudaStream_t st, std::string& err);
 
 // Alg. 2 on the device: d_points [n][3] -> kept indices (d_kept, caller-owned, n
 // entries) in the last pass's curve order, *n_out = their count.  Synchronises st.

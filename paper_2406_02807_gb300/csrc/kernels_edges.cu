@@ -389,7 +389,7 @@ struct JointScratch {
 template <bool STAGE, int MODE>
 __global__ void __launch_bounds__(512, 2) k_joint_configs(DevArgs t, const __grid_constant__ ArmPlan arm,
                                                           const float* __restrict__ q, uint64_t C,
-                                                          uint8_t* __restrict__ out) {
+                                                          uint8_t* __restrict__ out, unsigned long long* ctr) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t bar;
     const float* Ts = nullptr;
@@ -412,8 +412,9 @@ __global__ void __launch_bounds__(512, 2) k_joint_configs(DevArgs t, const __gri
         const uint32_t g = in_queue ? ws->ng[lane] : 0u;
         sphere_round<false, MODE>(t, Ts, &ws->re, ws->ghit, c, g, in_queue, lane, lt_mask);
     };
-    for (uint64_t pass = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); pass < passes;
-         pass += nwarps) {
+    const TileSched sched{ctr, nwarps};
+    for (uint64_t pass = sched.first((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)); pass < passes;
+         pass = sched.next(pass)) {
         const uint64_t k = pass * 32 + lane;
         const bool live = k < C;
         const float* qk = q + (live ? k : 0) * (uint64_t)J;
@@ -483,7 +484,7 @@ __global__ void __launch_bounds__(512, 2) k_joint_configs(DevArgs t, const __gri
 }
 
 int launch_joint_configs(const DevArgs& t, const capt_arm& arm, const float* q, uint64_t C, uint8_t* out,
-                         const capt_launch_cfg& cfg, cudaStream_t st, std::string& err) {
+                         const capt_launch_cfg& cfg, unsigned long long* ctr, cudaStream_t st, std::string& err) {
     if (C == 0) return CAPT_OK;
     const bool stage = cfg.staging == CAPT_STAGE_SMEM && t.stage_floats > 0;
     // the chunked scan, or the compact one once the replicated sets are dropped
@@ -500,7 +501,7 @@ int launch_joint_configs(const DevArgs& t, const capt_arm& arm, const float* q, 
     const uint64_t need = (passes + warps - 1) / warps;
     const uint64_t blocks = std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)sm_count() * occ, need));
     const ArmPlan plan = make_plan(arm);
-    fn<<<(unsigned)blocks, warps * 32, smem, st>>>(t, plan, q, C, out);
+    fn<<<(unsigned)blocks, warps * 32, smem, st>>>(t, plan, q, C, out, ctr);
     ce = cudaGetLastError();
     if (ce != cudaSuccess) { err = std::string("joint configuration launch: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
     return CAPT_OK;

@@ -51,7 +51,7 @@ __device__ __forceinline__ void bulk_copy(float* dst, const float* src, uint32_t
 template <int SPL, bool STAGE, int MODE>
 __global__ void __launch_bounds__(512, 2)
     k_spheres(DevArgs t, const float* __restrict__ centers, const float* __restrict__ radii, uint64_t m,
-              uint8_t* __restrict__ out) {
+              uint8_t* __restrict__ out, unsigned long long* ctr) {
     using WS = SphereScratch<SPL>;
     constexpr uint32_t E = 32 * SPL;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -103,11 +103,13 @@ __global__ void __launch_bounds__(512, 2)
         return true;
     };
 
-    uint64_t tile = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    const TileSched sched{ctr, nwarps};
+    uint64_t tile = sched.first((uint64_t)blockIdx.x * (blockDim.x >> 5) + warp);
     int buf = 0;
     bool staged = issue(tile, 0);
-    for (; tile < n_tiles; tile += nwarps, buf ^= 1) {
-        const bool next_staged = issue(tile + nwarps, buf ^ 1);
+    for (uint64_t nxt; tile < n_tiles; tile = nxt, buf ^= 1) {
+        nxt = sched.next(tile);
+        const bool next_staged = issue(nxt, buf ^ 1);
         float* in = ws->in[buf];
         bool from_smem = false;
         if (staged) {
@@ -207,7 +209,7 @@ struct CfgScratch {
 template <int CPT, bool STAGE, int MODE>
 __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs(DevArgs t, const float* __restrict__ centers,
                                                                  const float* __restrict__ radii, uint64_t C, int S,
-                                                                 uint8_t* __restrict__ out) {
+                                                                 uint8_t* __restrict__ out, unsigned long long* ctr) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t bar;
     __shared__ float r2s[64];
@@ -237,7 +239,9 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs(DevArgs t, cons
         sphere_round<false, MODE>(t, Ts, &ws->re, ws->ghit, c, g, live, lane, lt_mask);
     };
 
-    for (uint64_t tile = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp; tile < n_tiles; tile += nwarps) {
+    const TileSched sched{ctr, nwarps};
+    for (uint64_t tile = sched.first((uint64_t)blockIdx.x * (blockDim.x >> 5) + warp); tile < n_tiles;
+         tile = sched.next(tile)) {
         const uint64_t first = tile * CPT;
         const uint32_t ncfg = (uint32_t)min((uint64_t)CPT, C - first);
         const uint32_t nsph = ncfg * (uint32_t)S;
@@ -441,7 +445,7 @@ int sm_count() {
 
 namespace {
 
-using SphereKernel = void (*)(DevArgs, const float*, const float*, uint64_t, uint8_t*);
+using SphereKernel = void (*)(DevArgs, const float*, const float*, uint64_t, uint8_t*, unsigned long long*);
 
 template <int SPL, bool STAGE>
 SphereKernel pick_spheres_mode(int mode) {
@@ -491,7 +495,7 @@ int occupancy(const void* fn, int threads, size_t smem) {
 
 }  // namespace
 
-using ConfigKernel = void (*)(DevArgs, const float*, const float*, uint64_t, int, uint8_t*);
+using ConfigKernel = void (*)(DevArgs, const float*, const float*, uint64_t, int, uint8_t*, unsigned long long*);
 
 template <int CPT, bool STAGE>
 ConfigKernel pick_configs_mode(int mode) {
@@ -514,7 +518,7 @@ ConfigKernel pick_configs(int spl, bool stage, int mode) {
 }
 
 int launch_configs(const DevArgs& t, const float* centers, const float* radii, uint64_t C, int S, uint8_t* out,
-                   const capt_launch_cfg& cfg, cudaStream_t st, std::string& err) {
+                   const capt_launch_cfg& cfg, unsigned long long* ctr, cudaStream_t st, std::string& err) {
     const bool stage = cfg.staging == CAPT_STAGE_SMEM && t.stage_floats > 0;
     ConfigKernel fn = pick_configs(cfg.spheres_per_lane, stage, cfg.chunk);
     if (!fn) { err = "configuration queries take spheres_per_lane 2, 4, 8 or 16"; return CAPT_E_ARG; }
@@ -527,16 +531,17 @@ int launch_configs(const DevArgs& t, const float* centers, const float* radii, u
     const uint64_t tiles = (C + cpt - 1) / cpt;
     const uint64_t need = (tiles + warps - 1) / warps;
     const uint64_t blocks = std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)sm_count() * occ, need));
-    fn<<<(unsigned)blocks, warps * 32, smem, st>>>(t, centers, radii, C, S, out);
+    fn<<<(unsigned)blocks, warps * 32, smem, st>>>(t, centers, radii, C, S, out, ctr);
     ce = cudaGetLastError();
     if (ce != cudaSuccess) { err = std::string("configuration launch: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
     return CAPT_OK;
 }
 
 int launch_query(const DevArgs& t, int mode, const float* centers, const float* radii, uint64_t n_items, int S,
-                 uint8_t* out, const capt_launch_cfg& cfg, cudaStream_t st, std::string& err) {
+                 uint8_t* out, const capt_launch_cfg& cfg, unsigned long long* ctr, cudaStream_t st,
+                 std::string& err) {
     if (n_items == 0) return CAPT_OK;
-    if (mode == kModeConfigs) return launch_configs(t, centers, radii, n_items, S, out, cfg, st, err);
+    if (mode == kModeConfigs) return launch_configs(t, centers, radii, n_items, S, out, cfg, ctr, st, err);
     const int spl = cfg.spheres_per_lane;
     const bool stage = cfg.staging == CAPT_STAGE_SMEM && t.stage_floats > 0;
     SphereKernel fn = pick_spheres(spl, stage, cfg.chunk);
@@ -550,7 +555,7 @@ int launch_query(const DevArgs& t, int mode, const float* centers, const float* 
     const uint64_t tiles = (n_items + per_tile - 1) / per_tile;
     const uint64_t need = (tiles + warps - 1) / warps;
     const uint64_t blocks = std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)sm_count() * occ, need));
-    fn<<<(unsigned)blocks, warps * 32, smem, st>>>(t, centers, radii, n_items, out);
+    fn<<<(unsigned)blocks, warps * 32, smem, st>>>(t, centers, radii, n_items, out, ctr);
     ce = cudaGetLastError();
     if (ce != cudaSuccess) { err = std::string("query launch: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
     return CAPT_OK;
