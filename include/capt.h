@@ -356,7 +356,9 @@ enum { CAPT_EDGES_PERSISTENT = 0, /* one persistent launch over (edge, chunk) wo
  * d_qa, d_qb: device float[E][n_joints]; d_nsteps: device int32[E];
  * d_valid: device uint8[E] receives 1 = valid, 0 = collides.
  * arm: host pointer, copied.  mode: CAPT_EDGES_*.  CAPT_EDGES_PER_EDGE reads d_nsteps
- * back to the host (it synchronises `stream` once).  Uses scratch owned by the tree.
+ * back to the host (it synchronises `stream` once).  Uses scratch owned by the tree, so
+ * calls on one tree must not overlap on different streams (an edge plan, which owns
+ * its scratch, can run beside them).
  * Errors: CAPT_E_ARG, CAPT_E_STATE, CAPT_E_CUDA, CAPT_E_NOMEM. */
 int capt_validate_edges(capt_tree* t, const capt_arm* arm, const float* d_qa, const float* d_qb,
                         const int32_t* d_nsteps, size_t E, uint8_t* d_valid, int mode, void* stream);
