@@ -447,6 +447,47 @@ def test_clearance_backward_against_oracle_and_fd(tabletop, orc, capt_lib, torch
             assert abs(grad.reshape(-1, 3)[k, a] - fd) <= 1e-3 * abs(fd) + 1e-6
 
 
+@pytest.mark.slow
+def test_clearance_full_size(tabletop, orc, capt_lib, torch_):
+    """The full clearance workload (16,384 trajectories x 32 waypoints x 60 spheres) in
+    the bench's launch configuration: distances of 30,000 sampled spheres within 1e-5 of
+    the FP64 nearest distance, their argmin where the runner-up is separated, and the
+    cost and analytic gradient of 48 sampled trajectories against the FP64 oracle."""
+    import paper_2406_02807_gb300 as capt
+    T, W_ = 16384, 32
+    cen = _traj(tabletop, T, W_)
+    r = tabletop["arm"].sphere_radius
+    x = _cuda(torch_, cen).requires_grad_(True)
+    cost, d, am = capt.CaptClearance.apply(tabletop["ctree"], x, _cuda(torch_, r), 0.01)
+    cost.sum().backward()
+    d, am = d.detach().cpu().numpy().reshape(-1), am.cpu().numpy().reshape(-1)
+    rng = np.random.default_rng(3)
+    idx = rng.choice(d.size, 30000, replace=False)
+    dn, ni, d2 = orc.nearest64(tabletop["pts"], cen.reshape(-1, 3)[idx])
+    od = np.minimum(dn, 0.08)
+    assert np.abs(d[idx] - od).max() <= 1e-5
+    near = dn < 0.08 - 1e-5
+    assert near.sum() > 500
+    sep = near & (d2 - dn > 1e-5)
+    assert np.array_equal(am[idx][sep], ni[sep])
+    assert np.all(am[idx][dn >= 0.08 + 1e-5] == -1)
+    tr = rng.choice(T, 48, replace=False)
+    ocost, odist, ograd = orc.clearance64(tabletop["pts"], cen[tr], r, 0.08, 0.01)
+    c_gpu = cost.detach().cpu().numpy()[tr]
+    dd = d.reshape(T, W_, -1)[tr]
+    h = np.maximum(0.0, r[None, None, :].astype(np.float64) + 0.01 - odist)
+    bound = (2 * h * np.abs(dd - odist) + (dd - odist) ** 2).sum((1, 2)) + 1e-6 * ocost + 1e-9
+    assert np.all(np.abs(c_gpu - ocost) <= bound)
+    g = x.grad.cpu().numpy()[tr].astype(np.float64).reshape(-1, 3)
+    dn2, _, d22 = orc.nearest64(tabletop["pts"], cen[tr].reshape(-1, 3))
+    hgap = 1e-4
+    rr = np.tile(r, len(tr) * W_).astype(np.float64)
+    away = ((d22 - dn2 > 4 * hgap) & (np.abs(dn2 - 0.08) > 2 * hgap) & (np.abs(rr + 0.01 - dn2) > 2 * hgap)
+            & (dn2 > 2 * hgap))
+    og = ograd.reshape(-1, 3)
+    assert np.all(np.abs(g[away] - og[away]) <= 1e-3 * np.abs(og[away]) + 1e-6)
+
+
 def test_clearance_rejects_pruned_tree(tabletop, capt_lib, torch_):
     cen = _cuda(torch_, _traj(tabletop, 2, 2))
     with pytest.raises(capt_lib.CaptError) as e:
