@@ -189,9 +189,9 @@ int capt_upload(capt_tree* t, int device, void* stream);
  * every flag is unchanged (a point found is a cloud point within r; Lemma 1 puts every
  * such point in the set).  The queries use it with the launch configuration's scan
  * mode CAPT_SCAN_COMPACT; the autotuners include it once it exists.
- * Built on the tree's device from its uploaded sets (stream-ordered on `stream`, the
- * call synchronises it); about 16 bytes per point plus 32 bytes per leaf plus 4 bytes
- * per list entry.  drop_full = 1 then frees the replicated device sets: the plain and
+ * Built on the tree's device from its uploaded sets, the Z-order included (stream-ordered
+ * on `stream`, the call synchronises it); about 16 bytes per point plus 32 bytes per
+ * leaf plus 4 bytes per list entry.  drop_full = 1 then frees the replicated device sets: the plain and
  * chunked scan modes, edges, joint-angle configurations, clearance and the work
  * counters return CAPT_E_STATE until capt_upload runs again.  capt_upload and
  * capt_free release the compact form.  With drop_full, the caller must make sure that no

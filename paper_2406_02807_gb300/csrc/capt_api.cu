@@ -683,28 +683,10 @@ int capt_compact(capt_tree* t, int drop_full, void* stream) {
     std::lock_guard<std::mutex> lk(t->mu);
     if (drop_full && *t->n_plans > 0) return fail(CAPT_E_STATE, "edge plans of this tree still use its replicated sets");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const size_t n = t->h.n;
-    std::vector<float> pts;
-    std::vector<uint32_t> order;
     std::string err;
-    try {
-        order.resize(n);
-        const float* hp = t->h.pts.data();
-        if (t->h.pts.size() != 3 * n) {   // built on the device: read the cloud back
-            pts.resize(3 * n);
-            if (n) CUDA_TRY(cudaMemcpyAsync(pts.data(), t->d_cloud, 3 * n * sizeof(float), cudaMemcpyDeviceToHost, st),
-                            "cloud D2H");
-            CUDA_TRY(cudaStreamSynchronize(st), "cloud D2H");
-            hp = pts.data();
-        }
-        rc = capt::host_morton_order(hp, n, order.data(), err);
-    } catch (const std::bad_alloc&) {
-        return fail(CAPT_E_NOMEM, "host allocation failed in capt_compact");
-    }
-    if (rc) return fail(rc, err);
     t->dev_bytes -= std::min(t->dev_bytes, t->cs.bytes);
     t->cs.release();
-    rc = capt::device_compact(t->args(), n, order.data(), st, t->cs, err);
+    rc = capt::device_compact(t->args(), t->h.n, st, t->cs, err);
     if (rc) return fail(rc, err);
     t->dev_bytes += t->cs.bytes;
     if (drop_full) {

@@ -653,6 +653,21 @@ void DeviceTree::release() {
         return CAPT_E_NOMEM;                                             \
     }
 
+int launch_sort_pairs(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb, uint32_t n, int passes, uint32_t* hist,
+                      cudaStream_t st, std::string& err) {
+    const uint32_t nsb = grid_of(n, kSortThreads);
+    for (int pass = 0; pass < passes; pass++) {
+        k_radix_hist<<<nsb, kSortThreads, 0, st>>>(ka, n, 8 * pass, hist, nsb);
+        k_scan_exclusive<<<1, 1024, 0, st>>>(hist, 256 * nsb);
+        k_radix_scatter<<<nsb, kSortThreads, 0, st>>>(ka, va, n, 8 * pass, hist, nsb, kb, vb);
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    const cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) { err = std::string("sort launch: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
+    return CAPT_OK;
+}
+
 int launch_scan64(const uint32_t* v, uint32_t len, unsigned long long* out, cudaStream_t st, std::string& err) {
     k_scan64<<<1, 1024, 0, st>>>(v, len, out);
     const cudaError_t ce = cudaGetLastError();

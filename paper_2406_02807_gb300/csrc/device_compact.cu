@@ -27,11 +27,32 @@
 #include "capt_internal.h"
 #include "device_common.cuh"
 #include "kernels.h"
+#include "morton.cuh"
 
 namespace capt {
 namespace {
 
 constexpr uint32_t kChunkPoints = kChunkBlocks * 4;
+
+// Morton key of every point (x most significant in each bit triple, over the cloud's
+// bounding box), split in its low 32 and high 31 bits, with the point index as value.
+__global__ void kc_keys(const float* __restrict__ cloud, uint32_t n, float lx, float ly, float lz, float hx, float hy,
+                        float hz, uint32_t* __restrict__ klo, uint32_t* __restrict__ khi, uint32_t* __restrict__ idx) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float* p = cloud + 3 * (size_t)i;
+    const uint64_t k = (spread21(morton_q(p[0], lx, hx)) << 2) | (spread21(morton_q(p[1], ly, hy)) << 1) |
+                       spread21(morton_q(p[2], lz, hz));
+    klo[i] = (uint32_t)k;
+    khi[i] = (uint32_t)(k >> 32);
+    idx[i] = i;
+}
+
+__global__ void kc_gather(const uint32_t* __restrict__ src, const uint32_t* __restrict__ perm, uint32_t n,
+                          uint32_t* __restrict__ dst) {
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) dst[j] = src[perm[j]];
+}
 
 __global__ void kc_rank(const uint32_t* __restrict__ order, uint32_t n, uint32_t* __restrict__ rank) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -113,8 +134,7 @@ void CompactSets::release() {
     bytes = 0;
 }
 
-int device_compact(const DevArgs& t, size_t n, const uint32_t* h_order, cudaStream_t st, CompactSets& out,
-                   std::string& err) {
+int device_compact(const DevArgs& t, size_t n, cudaStream_t st, CompactSets& out, std::string& err) {
     out.release();
     const uint32_t N = t.N;
     const uint64_t n_chunks = std::max<uint64_t>(1, (n + kChunkPoints - 1) / kChunkPoints);
@@ -125,10 +145,12 @@ int device_compact(const DevArgs& t, size_t n, const uint32_t* h_order, cudaStre
         err = "compact sets: too many chunks for the per-warp bitmap (at most 1.6M chunks of 32 points)";
         return CAPT_E_RANGE;
     }
-    uint32_t *order = nullptr, *rank = nullptr, *counts = nullptr;
+    uint32_t *order = nullptr, *rank = nullptr, *counts = nullptr, *ka = nullptr, *kb = nullptr, *vb = nullptr,
+             *khi = nullptr, *hist = nullptr;
     unsigned long long* offsets = nullptr;
     auto cleanup = [&]() {
-        for (void* p : {(void*)order, (void*)rank, (void*)counts, (void*)offsets})
+        for (void* p : {(void*)order, (void*)rank, (void*)counts, (void*)offsets, (void*)ka, (void*)kb, (void*)vb,
+                        (void*)khi, (void*)hist})
             if (p) cudaFree(p);
     };
     auto cuda_err = [&](cudaError_t e, const char* what) {
@@ -151,8 +173,30 @@ int device_compact(const DevArgs& t, size_t n, const uint32_t* h_order, cudaStre
     DC_TRY(cudaMalloc(&out.cleaves, (size_t)N * sizeof(LeafRec)), "cudaMalloc leaf records");
     DC_TRY(cudaMalloc(&out.cblocks, n_blocks * 12 * sizeof(float)), "cudaMalloc blocks");
     DC_TRY(cudaMalloc(&out.ccbox, n_chunks * 8 * sizeof(float)), "cudaMalloc chunk boxes");
-    if (n) DC_TRY(cudaMemcpyAsync(order, h_order, n * sizeof(uint32_t), cudaMemcpyHostToDevice, st), "order upload");
-    if (n) kc_rank<<<grid_for(n, 256), 256, 0, st>>>(order, (uint32_t)n, rank);
+    if (n) {
+        // the cloud's order along its Z-order curve: a stable sort by the keys' low 32
+        // bits, then by their high 31 bits, so ties keep the point order
+        const uint32_t un = (uint32_t)n;
+        DC_TRY(cudaMalloc((void**)&ka, sz_n), "cudaMalloc keys");
+        DC_TRY(cudaMalloc((void**)&kb, sz_n), "cudaMalloc keys");
+        DC_TRY(cudaMalloc((void**)&vb, sz_n), "cudaMalloc values");
+        DC_TRY(cudaMalloc((void**)&khi, sz_n), "cudaMalloc keys");
+        DC_TRY(cudaMalloc((void**)&hist, 256 * sizeof(uint32_t) * ((n + 255) / 256)), "cudaMalloc histogram");
+        kc_keys<<<grid_for(n, 256), 256, 0, st>>>(t.cloud, un, t.lo[0], t.lo[1], t.lo[2], t.hi[0], t.hi[1], t.hi[2],
+                                                  ka, khi, order);
+        DC_TRY(cudaGetLastError(), "key launch");
+        int rc = launch_sort_pairs(ka, order, kb, vb, un, 4, hist, st, err);
+        if (rc == CAPT_OK) {
+            kc_gather<<<grid_for(n, 256), 256, 0, st>>>(khi, order, un, ka);
+            rc = launch_sort_pairs(ka, order, kb, vb, un, 4, hist, st, err);
+        }
+        if (rc != CAPT_OK) {
+            cleanup();
+            out.release();
+            return rc;
+        }
+        kc_rank<<<grid_for(n, 256), 256, 0, st>>>(order, un, rank);
+    }
     kc_blocks<<<grid_for(n_chunks * kChunkPoints, 256), 256, 0, st>>>(t.cloud, order, (uint32_t)n,
                                                                         n_chunks * kChunkPoints, n_blocks,
                                                                         static_cast<float*>(out.cblocks));

@@ -29,6 +29,7 @@
 #include "capt_internal.h"
 #include "device_common.cuh"
 #include "kernels.h"
+#include "morton.cuh"
 
 namespace capt {
 namespace {
@@ -37,17 +38,6 @@ constexpr int kFT = 256;                  // threads per block
 constexpr int kFE = 16;                   // elements per thread in the blocked kernels
 constexpr uint32_t kFTile = kFT * kFE;    // 4096 elements per block
 constexpr int kScanThreads = 1024;
-
-// Spread the low 21 bits of v so that bit b moves to bit 3b.
-__device__ __forceinline__ uint64_t spread21(uint32_t v) {
-    uint64_t x = v & 0x1fffffu;
-    x = (x | (x << 32)) & 0x1f00000000ffffull;
-    x = (x | (x << 16)) & 0x1f0000ff0000ffull;
-    x = (x | (x << 8)) & 0x100f00f00f00f00full;
-    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
-    x = (x | (x << 2)) & 0x1249249249249249ull;
-    return x;
-}
 
 // box: lo keys [0..2], hi keys [3..5], non-finite flag [6].
 __global__ void kf_bbox(const float* __restrict__ pts, uint32_t n, uint32_t* __restrict__ box) {
@@ -82,17 +72,9 @@ __global__ void kf_spread(const float* __restrict__ pts, uint32_t n, const uint3
                           uint64_t* __restrict__ sp) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    for (int a = 0; a < 3; a++) {
-        const double lo = (double)fkey_float(box[a]);
-        const double hi = (double)fkey_float(box[3 + a]);
-        const double ext = __dsub_rn(hi, lo);
-        uint32_t v = 0;
-        if (ext > 0.0) {
-            const double f = floor(__dmul_rn(__ddiv_rn(__dsub_rn((double)pts[3 * (size_t)i + a], lo), ext), 2097152.0));
-            v = f >= 2097151.0 ? 2097151u : (uint32_t)f;
-        }
-        sp[3 * (size_t)i + a] = spread21(v);
-    }
+    for (int a = 0; a < 3; a++)
+        sp[3 * (size_t)i + a] = spread21(morton_q(pts[3 * (size_t)i + a], (double)fkey_float(box[a]),
+                                                  (double)fkey_float(box[3 + a])));
 }
 
 // Block-wide exclusive prefix of one flag per thread (256 threads); returns the prefix

@@ -58,6 +58,12 @@ int device_sfc_filter(const float* d_points, size_t n, float r, uint32_t* d_kept
 int launch_gather_points(const float* pts, const uint32_t* idx, size_t m, float* out, cudaStream_t st,
                          std::string& err);
 
+// Stable LSD radix sort of n (key, value) pairs by the `passes` lowest 8-bit digits of
+// the 32-bit keys, through kb / vb; an even number of passes leaves the result in ka /
+// va.  hist: 256 * ceil(n / 256) words of scratch.
+int launch_sort_pairs(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb, uint32_t n, int passes, uint32_t* hist,
+                      cudaStream_t st, std::string& err);
+
 // Exclusive scan of v[0..len) into 64-bit offsets out[0..len], out[len] = total (one block).
 int launch_scan64(const uint32_t* v, uint32_t len, unsigned long long* out, cudaStream_t st, std::string& err);
 
@@ -73,10 +79,9 @@ struct CompactSets {
     void release();
 };
 
-// Builds the compact sets from the tree's device sets (t.leaves, t.ids, t.cloud) and the
-// cloud's Z-order h_order (host uint32[n]).  Synchronises st.
-int device_compact(const DevArgs& t, size_t n, const uint32_t* h_order, cudaStream_t st, CompactSets& out,
-                   std::string& err);
+// Builds the compact sets from the tree's device sets (t.leaves, t.ids, t.cloud), with
+// the cloud ordered along its Z-order curve on the device.  Synchronises st.
+int device_compact(const DevArgs& t, size_t n, cudaStream_t st, CompactSets& out, std::string& err);
 
 // Number of SMs of the current device (cached per device).
 int sm_count();
