@@ -178,35 +178,45 @@ __global__ void kf_keys(const uint32_t* __restrict__ asc, const uint32_t* __rest
     val[j] = i;
 }
 
-__global__ void __launch_bounds__(kFT) kf_hist(const uint32_t* __restrict__ kw, const uint32_t* __restrict__ d_m,
-                                                int shift, uint32_t* __restrict__ hist, uint32_t nblk) {
+// The radix-sort kernels take a tile of kFTile elements with kST threads, kSR rounds of
+// kST consecutive elements each (a wide block: few rounds of dependent barriers).
+constexpr int kST = 1024;
+constexpr int kSR = (int)(kFTile / kST);
+
+__global__ void __launch_bounds__(kST) kf_hist(const uint32_t* __restrict__ kw, const uint32_t* __restrict__ d_m,
+                                               int shift, uint32_t* __restrict__ hist, uint32_t nblk) {
     __shared__ uint32_t h[256];
-    h[threadIdx.x] = 0;
+    if (threadIdx.x < 256) h[threadIdx.x] = 0;
     __syncthreads();
     const uint32_t m = *d_m;
-    for (int r = 0; r < kFE; r++) {
-        const uint32_t i = blockIdx.x * kFTile + (uint32_t)r * kFT + threadIdx.x;
+    for (int r = 0; r < kSR; r++) {
+        const uint32_t i = blockIdx.x * kFTile + (uint32_t)r * kST + threadIdx.x;
         if (i < m) atomicAdd(&h[(kw[i] >> shift) & 255u], 1u);
     }
     __syncthreads();
-    hist[threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];   // digit-major
+    if (threadIdx.x < 256) hist[threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];   // digit-major
 }
 
-// Stable scatter by the digit of ka at `shift`; kb and val travel with it.
-__global__ void __launch_bounds__(kFT) kf_scatter(const uint32_t* __restrict__ ka, const uint32_t* __restrict__ kb,
-                                                   const uint32_t* __restrict__ val, const uint32_t* __restrict__ d_m,
-                                                   int shift, const uint32_t* __restrict__ off, uint32_t nblk,
-                                                   uint32_t* __restrict__ ka_o, uint32_t* __restrict__ kb_o,
-                                                   uint32_t* __restrict__ val_o) {
+// Stable scatter by the digit of ka at `shift`; kb and val travel with it.  Per round:
+// each warp counts its digits (match_any), one thread per digit turns the per-warp
+// counts into offsets (warps in order), and every element goes to base + warp offset +
+// its rank among equal digits of its warp, so the order within a digit is the input
+// order.
+__global__ void __launch_bounds__(kST) kf_scatter(const uint32_t* __restrict__ ka, const uint32_t* __restrict__ kb,
+                                                  const uint32_t* __restrict__ val, const uint32_t* __restrict__ d_m,
+                                                  int shift, const uint32_t* __restrict__ off, uint32_t nblk,
+                                                  uint32_t* __restrict__ ka_o, uint32_t* __restrict__ kb_o,
+                                                  uint32_t* __restrict__ val_o) {
+    constexpr int NW = kST / 32;
     __shared__ uint32_t base[256];
-    __shared__ uint32_t cnt[kFT / 32][256];
+    __shared__ uint32_t cnt[NW][256];
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-    base[threadIdx.x] = off[threadIdx.x * nblk + blockIdx.x];
+    if (threadIdx.x < 256) base[threadIdx.x] = off[threadIdx.x * nblk + blockIdx.x];
     const uint32_t m = *d_m;
-    for (int r = 0; r < kFE; r++) {
-        for (int w = 0; w < kFT / 32; w++) cnt[w][threadIdx.x] = 0;
+    for (int r = 0; r < kSR; r++) {
+        for (uint32_t j = threadIdx.x; j < NW * 256; j += kST) (&cnt[0][0])[j] = 0;
         __syncthreads();
-        const uint32_t i = blockIdx.x * kFTile + (uint32_t)r * kFT + threadIdx.x;
+        const uint32_t i = blockIdx.x * kFTile + (uint32_t)r * kST + threadIdx.x;
         const bool valid = i < m;
         const uint32_t a = valid ? ka[i] : 0u;
         const uint32_t d = valid ? ((a >> shift) & 255u) : 256u;
@@ -214,18 +224,23 @@ __global__ void __launch_bounds__(kFT) kf_scatter(const uint32_t* __restrict__ k
         const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
         if (valid && rank == 0) cnt[warp][d] = __popc(peers);
         __syncthreads();
+        if (threadIdx.x < 256) {
+            // exclusive prefix over the warps for this digit; the round's total moves base
+            uint32_t run = base[threadIdx.x];
+            for (int w = 0; w < NW; w++) {
+                const uint32_t c = cnt[w][threadIdx.x];
+                cnt[w][threadIdx.x] = run;
+                run += c;
+            }
+            base[threadIdx.x] = run;
+        }
+        __syncthreads();
         if (valid) {
-            uint32_t before = 0;
-            for (uint32_t w = 0; w < warp; w++) before += cnt[w][d];
-            const uint32_t pos = base[d] + before + rank;
+            const uint32_t pos = cnt[warp][d] + rank;
             ka_o[pos] = a;
             kb_o[pos] = kb[i];
             val_o[pos] = val[i];
         }
-        __syncthreads();
-        uint32_t tot = 0;
-        for (int w = 0; w < kFT / 32; w++) tot += cnt[w][threadIdx.x];
-        base[threadIdx.x] += tot;
         __syncthreads();
     }
 }
@@ -375,9 +390,9 @@ void enqueue_filter(const FilterBufs& b, uint32_t n, float r, cudaStream_t st) {
                 const uint32_t* ko = word == 0 ? kb[cur] : ka[cur];
                 uint32_t* kw_o = word == 0 ? ka[cur ^ 1] : kb[cur ^ 1];
                 uint32_t* ko_o = word == 0 ? kb[cur ^ 1] : ka[cur ^ 1];
-                kf_hist<<<nblk, kFT, 0, st>>>(kw, b.d_m, shift, b.hist, nblk);
+                kf_hist<<<nblk, kST, 0, st>>>(kw, b.d_m, shift, b.hist, nblk);
                 kf_scan<<<1, kScanThreads, 0, st>>>(b.hist, 256 * nblk, nullptr);
-                kf_scatter<<<nblk, kFT, 0, st>>>(kw, ko, vv[cur], b.d_m, shift, b.hist, nblk, kw_o, ko_o, vv[cur ^ 1]);
+                kf_scatter<<<nblk, kST, 0, st>>>(kw, ko, vv[cur], b.d_m, shift, b.hist, nblk, kw_o, ko_o, vv[cur ^ 1]);
                 cur ^= 1;
             }
         const uint32_t* val = vv[cur];
