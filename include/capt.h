@@ -191,11 +191,14 @@ int capt_upload(capt_tree* t, int device, void* stream);
  * mode CAPT_SCAN_COMPACT; the autotuners include it once it exists.
  * Built on the tree's device from its uploaded sets, the Z-order included (stream-ordered
  * on `stream`, the call synchronises it); about 16 bytes per point plus 32 bytes per
- * leaf plus 4 bytes per list entry.  drop_full = 1 then frees the replicated device sets: the plain and
- * chunked scan modes, edges, joint-angle configurations, clearance and the work
- * counters return CAPT_E_STATE until capt_upload runs again.  capt_upload and
- * capt_free release the compact form.  With drop_full, the caller must make sure that no
- * work queued on other streams still uses the tree (the call synchronises `stream` only).
+ * leaf plus 4 bytes per list entry.  drop_full = 1 then frees the replicated device
+ * sets: edge validation and joint-angle configurations switch to the compact scan by
+ * themselves, while the plain and chunked scan modes, clearance (which needs the point
+ * of every slot) and the work counters return CAPT_E_STATE until capt_upload runs
+ * again; the drop is refused while an edge plan of the tree exists.  capt_upload and
+ * capt_free release the compact form.  With drop_full, the caller must make sure that
+ * no work queued on other streams still uses the tree (the call synchronises `stream`
+ * only).
  * Errors: CAPT_E_ARG, CAPT_E_STATE (not uploaded, or the replicated sets already
  *         dropped), CAPT_E_RANGE (more than 1.6M chunks), CAPT_E_NOMEM, CAPT_E_CUDA. */
 int capt_compact(capt_tree* t, int drop_full, void* stream);
