@@ -38,7 +38,7 @@ R_MIN, R_MAX, R_FILTER = 0.02, 0.08, 0.01
 SM_MAX_MHZ = 2070.0
 # DRAM bytes (read + write) per launch of the configuration-query kernel from an ncu
 # capture, keyed by the hash of the kernel source it was taken on (null when stale).
-TRAFFIC = {"68cc194a83266fb2": 778328064 + 4323840}   # profiles/k_configs_tabletop_1M.md
+TRAFFIC = {"17cca476bcfba7d6": 778620416 + 4390656}   # profiles/k_configs_tabletop_1M.md
 HBM_FALLBACK_GBS = 6800.0   # used only when MEASURED_PEAKS.json is absent
 
 

@@ -1,6 +1,8 @@
 // Sphere and configuration queries (Alg. 3 with the early exit of Sec. IV-D).
 //
-// Design (GB300): persistent grids, one warp per tile of spheres or configurations.
+// Design (GB300): persistent grids, one warp per tile of spheres or configurations,
+// the tiles handed out by a work counter (TileSched) so that no warp is left with the
+// expensive tiles at the end.
 //  1. Root box test: every sphere is first tested against the bounding box of the
 //     whole cloud.  That box contains every affordance set, so a sphere that misses it
 //     misses every point (the same FP32 argument as the leaf box test of Alg. 3:
@@ -9,9 +11,11 @@
 //  2. Queued spheres are processed 32 at a time (sphere_round, scan.cuh): one lane
 //     each descends (fixed L steps, 3 levels per step on the blocked split array),
 //     loads its leaf's 32-byte record and applies the leaf box test; the sets of the
-//     spheres that pass are concatenated and scanned 32 blocks at a time.  The paper
-//     vectorises the scan across the points of one set; this spreads it across the
-//     points of every live set of the round, so lanes stay busy whatever the sizes.
+//     spheres that pass are then scanned by the whole warp, in the launch's scan mode:
+//     by chunks of 32 points whose boxes the sphere reaches (the default), by whole
+//     sets, or over the compact sets.  The paper vectorises the scan across the points
+//     of one set; this spreads it across the points of every live set of the round, so
+//     lanes stay busy whatever the sizes.
 //  3. A hit resolves its group (a sphere, or a configuration): later spheres and
 //     blocks of a resolved group are skipped (Sec. IV-D early termination).
 #include <algorithm>

@@ -5,8 +5,9 @@
 // the spheres that pass become entries.  In the chunked form their sets are then
 // walked chunk by chunk (kChunkBlocks blocks of 4 points): every chunk first meets its
 // FP32 bounding box, one chunk per lane, and only the chunks whose box the sphere
-// reaches are scanned, 64 blocks per warp step.  The plain form scans whole sets.  Every lane test is three 16-byte loads and four FP32
-// distance tests in packed FP32x2 arithmetic.
+// reaches are scanned, 64 blocks per warp step; the compact form walks the chunks of
+// the Z-ordered cloud that a leaf lists.  The plain form scans whole sets.  Every lane
+// test is three 16-byte loads and four FP32 distance tests in packed FP32x2 arithmetic.
 // The blocks are stored as three planes of float4 (x quads, y quads, z quads), so the
 // loads of consecutive blocks by consecutive lanes are contiguous in each plane.
 #pragma once
