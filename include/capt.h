@@ -50,7 +50,7 @@ typedef enum capt_status {
     CAPT_E_NOMEM = -4,      /* host or device allocation failed */
     CAPT_E_CUDA = -5,       /* a CUDA runtime call failed (see capt_last_error) */
     CAPT_E_TIMEOUT = -6,    /* a bounded device wait gave up (from capt_device_status) */
-    CAPT_E_BOUNDS = -7,     /* a device-side index check failed (debug builds) */
+    CAPT_E_BOUNDS = -7,     /* a device-side index or size check failed (from capt_device_status) */
     CAPT_E_STATE = -8       /* tree not uploaded, used on another device, or pruned
                                tree given to the clearance calls */
 } capt_status;
@@ -77,6 +77,9 @@ typedef struct capt_tree_stats {
     uint64_t compact_bytes;   /* capt_compact: device bytes of the compact form */
     int32_t full_dropped;     /* 1 if capt_compact freed the replicated device sets */
     int32_t reserved;
+    uint64_t scratch_bytes;   /* device scratch the tree allocated on demand (edge work items
+                                 of capt_validate_edges, buffers of capt_query_configs_host);
+                                 not part of device_bytes */
 } capt_tree_stats;
 
 /* ---------------------------------------------------------------------------------
@@ -358,10 +361,14 @@ enum { CAPT_EDGES_PERSISTENT = 0, /* one persistent launch over (edge, chunk) wo
  * checked once one configuration collides).  n_e <= 0 means no configuration: valid.
  * d_qa, d_qb: device float[E][n_joints]; d_nsteps: device int32[E];
  * d_valid: device uint8[E] receives 1 = valid, 0 = collides.
+ * Each buffer must hold E entries: the call sees only their base addresses.
  * arm: host pointer, copied.  mode: CAPT_EDGES_*.  CAPT_EDGES_PER_EDGE reads d_nsteps
  * back to the host (it synchronises `stream` once).  Uses scratch owned by the tree, so
  * calls on one tree must not overlap on different streams (an edge plan, which owns
- * its scratch, can run beside them).
+ * its scratch, can run beside them).  In persistent mode the work is counted in items
+ * of up to 32..1024 configurations; a batch of more than 2^31 items (2^36 or more
+ * configurations) is refused on the device: every edge is reported as not valid (0)
+ * and capt_device_status returns CAPT_E_BOUNDS.
  * Errors: CAPT_E_ARG, CAPT_E_STATE, CAPT_E_CUDA, CAPT_E_NOMEM. */
 int capt_validate_edges(capt_tree* t, const capt_arm* arm, const float* d_qa, const float* d_qb,
                         const int32_t* d_nsteps, size_t E, uint8_t* d_valid, int mode, void* stream);
@@ -374,10 +381,13 @@ int capt_validate_edges(capt_tree* t, const capt_arm* arm, const float* d_qa, co
  * behind its back.  The paper has no counterpart: this is a deployment variant.
  * Instead of a buffer it allocates, the call uses one fixed scratch array inside the
  * library (CAPT_STATIC_MAX_EDGES + 64 words, about 256 KB), which every device that
- * loads the library holds until the process exits.  It calls no allocator.
+ * loads the library's device code holds until its context ends.  It calls no allocator.
  *  - E must be <= CAPT_STATIC_MAX_EDGES, else CAPT_E_ARG.
- *  - The first call on a device looks the array's device address up (once per device,
- *    with that device current); make that first call before any stream capture.
+ *  - The first call on a device looks the array's device address up (once per device
+ *    and context, with that device current; again after a cudaDeviceReset replaced the
+ *    context).  With CUDA's lazy module loading that first call may also load the
+ *    library's device code, which is when the array is reserved.  Make that first call
+ *    before any stream capture.
  *  - Every call reuses the same array and re-initialises what must start at zero, so
  *    calls whose work overlaps on the GPU (other streams, other host threads) race:
  *    order them on one stream or synchronise between them.

@@ -63,7 +63,8 @@ class _Stats(C.Structure):
                 ("pruned_leaves", C.c_uint64), ("empty_leaves", C.c_uint64), ("device_bytes", C.c_uint64),
                 ("build_ms", C.c_double), ("r_min", C.c_float), ("r_max", C.c_float), ("device", C.c_int32),
                 ("build_threads", C.c_int32), ("compact_chunks", C.c_uint64), ("compact_entries", C.c_uint64),
-                ("compact_bytes", C.c_uint64), ("full_dropped", C.c_int32), ("reserved", C.c_int32)]
+                ("compact_bytes", C.c_uint64), ("full_dropped", C.c_int32), ("reserved", C.c_int32),
+                ("scratch_bytes", C.c_uint64)]
 
 
 class _LaunchCfg(C.Structure):
@@ -85,9 +86,12 @@ def _load():
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(LIB):
-        raise ImportError(f"libcapt.so is not built ({LIB}); run paper_2406_02807_gb300.build()")
-    L = C.CDLL(LIB)
+    # CAPT_LIBRARY names another build of the same library (a test variant, see
+    # _build.VARIANTS); by default the in-tree libcapt.so
+    lib = os.environ.get("CAPT_LIBRARY") or LIB
+    if not os.path.exists(lib):
+        raise ImportError(f"libcapt.so is not built ({lib}); run paper_2406_02807_gb300.build()")
+    L = C.CDLL(lib)
     P, SZ, I, F = C.c_void_p, C.c_size_t, C.c_int, C.c_float
     sig = {
         "capt_build": [P, SZ, F, F, C.POINTER(P)],
@@ -166,6 +170,13 @@ def _dev(t, dtype, name):
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     return C.c_void_p(t.data_ptr())
+
+
+def _numel(t, n, name):
+    """A caller-passed buffer must hold exactly n elements: the C ABI receives only its
+    base address, so a shorter one would be written past its end on the device."""
+    if t is not None and t.numel() != n:
+        raise ValueError(f"{name} must hold {n} elements, got {t.numel()}")
 
 
 def _stream(stream):
@@ -314,6 +325,7 @@ def capt_query_spheres(tree: CaptTree, centers, radii, flags=None, stream=None):
     m = centers.shape[0]
     if centers.dim() != 2 or centers.shape[1] != 3 or radii.shape != (m,):
         raise ValueError("centers must be [m, 3] and radii [m]")
+    _numel(flags, m, "flags")
     if flags is None:
         flags = torch.empty(m, dtype=torch.uint8, device=centers.device)
     _check(_load().capt_query_spheres(tree.h, _dev(centers, torch.float32, "centers"),
@@ -329,6 +341,7 @@ def capt_query_configs(tree: CaptTree, centers, radii, flags=None, stream=None):
     Cn, S = centers.shape[0], centers.shape[1]
     if radii.shape != (S,):
         raise ValueError("radii must be [S]")
+    _numel(flags, Cn, "flags")
     if flags is None:
         flags = torch.empty(Cn, dtype=torch.uint8, device=centers.device)
     _check(_load().capt_query_configs(tree.h, _dev(centers, torch.float32, "centers"),
@@ -350,6 +363,14 @@ def capt_query_configs_host(tree: CaptTree, centers, radii, flags=None, stream=N
         Cn, S = centers.shape[0], centers.shape[1]
         cp = _ptr(centers)
     r = np.ascontiguousarray(radii.cpu().numpy() if isinstance(radii, torch.Tensor) else radii, np.float32)
+    if centers.ndim != 3 or centers.shape[2] != 3 or r.shape != (S,):
+        raise ValueError("centers must be [C, S, 3] and radii [S]")
+    if flags is not None and (flags.size if isinstance(flags, np.ndarray) else flags.numel()) != Cn:
+        raise ValueError(f"flags must hold {Cn} elements")
+    if isinstance(flags, torch.Tensor) and (flags.is_cuda or flags.dtype != torch.uint8 or not flags.is_contiguous()):
+        raise TypeError("flags must be a contiguous uint8 CPU tensor")
+    if isinstance(flags, np.ndarray) and (flags.dtype != np.uint8 or not flags.flags.c_contiguous):
+        raise TypeError("flags must be a contiguous uint8 array")
     if flags is None:
         flags = np.zeros(Cn, np.uint8)
     fp = C.c_void_p(flags.data_ptr()) if isinstance(flags, torch.Tensor) else _ptr(flags)
@@ -359,6 +380,8 @@ def capt_query_configs_host(tree: CaptTree, centers, radii, flags=None, stream=N
 
 def capt_count_config_work(tree: CaptTree, centers, radii, stream=None):
     import torch
+    if centers.dim() != 3 or centers.shape[2] != 3 or radii.shape != (centers.shape[1],):
+        raise ValueError("centers must be [C, S, 3] and radii [S]")
     Cn, S = centers.shape[0], centers.shape[1]
     counts = torch.zeros(6, dtype=torch.int64, device=centers.device)
     _check(_load().capt_count_config_work(tree.h, _dev(centers, torch.float32, "centers"),
@@ -370,7 +393,10 @@ def capt_count_config_work(tree: CaptTree, centers, radii, stream=None):
 
 def capt_query_leaves(tree: CaptTree, centers, leaves=None, stream=None):
     import torch
+    if centers.dim() != 2 or centers.shape[1] != 3:
+        raise ValueError("centers must be [m, 3]")
     m = centers.shape[0]
+    _numel(leaves, m, "leaves")
     if leaves is None:
         leaves = torch.empty(m, dtype=torch.int32, device=centers.device)
     _check(_load().capt_query_leaves(tree.h, _dev(centers, torch.float32, "centers"), m,
@@ -397,7 +423,10 @@ def capt_get_launch_cfg(tree: CaptTree, kernel: int) -> dict:
 
 def capt_autotune_configs(tree: CaptTree, centers, radii, flags=None, stream=None):
     import torch
+    if centers.dim() != 3 or centers.shape[2] != 3 or radii.shape != (centers.shape[1],):
+        raise ValueError("centers must be [C, S, 3] and radii [S]")
     Cn, S = centers.shape[0], centers.shape[1]
+    _numel(flags, Cn, "flags")
     if flags is None:
         flags = torch.empty(Cn, dtype=torch.uint8, device=centers.device)
     c = _LaunchCfg()
@@ -412,6 +441,9 @@ def capt_autotune_configs(tree: CaptTree, centers, radii, flags=None, stream=Non
 def capt_autotune_spheres(tree: CaptTree, centers, radii, flags=None, stream=None):
     import torch
     m = centers.shape[0]
+    if centers.dim() != 2 or centers.shape[1] != 3 or radii.shape != (m,):
+        raise ValueError("centers must be [m, 3] and radii [m]")
+    _numel(flags, m, "flags")
     if flags is None:
         flags = torch.empty(m, dtype=torch.uint8, device=centers.device)
     c = _LaunchCfg()
@@ -445,12 +477,44 @@ def make_arm(arm) -> _Arm:
     return a
 
 
+def _edge_args(tree: CaptTree, a: _Arm, qa, qb, nsteps, valid):
+    """Shape and device checks of an edge batch, before any pointer crosses the C ABI
+    (which sees only base addresses and E): qa, qb [E, n_joints], nsteps [E], valid
+    with E elements, all on one CUDA device, the tree's when it is uploaded.  A shorter
+    buffer would otherwise be read or written past its end on the device."""
+    import torch
+    for name, x in (("qa", qa), ("qb", qb), ("nsteps", nsteps)):
+        if not isinstance(x, torch.Tensor):
+            raise TypeError(f"{name} must be a torch tensor")
+    if qa.dim() != 2 or qa.shape[1] != a.n_joints:
+        raise ValueError(f"qa must be [E, {a.n_joints}], got {list(qa.shape)}")
+    E = qa.shape[0]
+    if tuple(qb.shape) != tuple(qa.shape):
+        raise ValueError(f"qb must have the shape of qa {list(qa.shape)}, got {list(qb.shape)}")
+    if tuple(nsteps.shape) != (E,):
+        raise ValueError(f"nsteps must be [{E}], got {list(nsteps.shape)}")
+    if valid is not None:
+        if not isinstance(valid, torch.Tensor):
+            raise TypeError("valid must be a torch tensor")
+        if valid.numel() != E:
+            raise ValueError(f"valid must hold {E} elements, got {valid.numel()}")
+    devs = {x.device for x in (qa, qb, nsteps) + ((valid,) if valid is not None else ())}
+    if len(devs) != 1:
+        raise ValueError(f"qa, qb, nsteps and valid must be on one device, got {sorted(map(str, devs))}")
+    d = qa.device
+    if d.type == "cuda":
+        td = capt_stats(tree)["device"]
+        if td >= 0 and (d.index if d.index is not None else torch.cuda.current_device()) != td:
+            raise ValueError(f"edge buffers are on {d}, the tree on cuda:{td}")
+    return E
+
+
 def capt_validate_edges(tree: CaptTree, arm, qa, qb, nsteps, valid=None, mode=CAPT_EDGES_PERSISTENT, stream=None):
     import torch
-    E = qa.shape[0]
+    a = arm if isinstance(arm, _Arm) else make_arm(arm)
+    E = _edge_args(tree, a, qa, qb, nsteps, valid)
     if valid is None:
         valid = torch.empty(E, dtype=torch.uint8, device=qa.device)
-    a = arm if isinstance(arm, _Arm) else make_arm(arm)
     _check(_load().capt_validate_edges(tree.h, C.byref(a), _dev(qa, torch.float32, "qa"), _dev(qb, torch.float32, "qb"),
                                        _dev(nsteps, torch.int32, "nsteps"), E, _dev(valid, torch.uint8, "valid"),
                                        int(mode), _stream(stream)), "capt_validate_edges")
@@ -465,6 +529,7 @@ def capt_query_joint_configs(tree: CaptTree, arm, q, flags=None, stream=None):
     if q.dim() != 2 or q.shape[1] != a.n_joints:
         raise ValueError("q must be [C, n_joints]")
     Cn = q.shape[0]
+    _numel(flags, Cn, "flags")
     if flags is None:
         flags = torch.empty(Cn, dtype=torch.uint8, device=q.device)
     _check(_load().capt_query_joint_configs(tree.h, C.byref(a), _dev(q, torch.float32, "q"), Cn,
@@ -476,7 +541,10 @@ def capt_query_joint_configs(tree: CaptTree, arm, q, flags=None, stream=None):
 def capt_autotune_joint_configs(tree: CaptTree, arm, q, flags=None, stream=None):
     import torch
     a = arm if isinstance(arm, _Arm) else make_arm(arm)
+    if q.dim() != 2 or q.shape[1] != a.n_joints:
+        raise ValueError("q must be [C, n_joints]")
     Cn = q.shape[0]
+    _numel(flags, Cn, "flags")
     if flags is None:
         flags = torch.empty(Cn, dtype=torch.uint8, device=q.device)
     c = _LaunchCfg()
@@ -493,10 +561,10 @@ def capt_validate_edges_static(tree: CaptTree, arm, qa, qb, nsteps, valid=None, 
     race).  For callers that must not enter the CUDA allocator, such as a planner in a
     real-time control loop or an application whose device memory another allocator owns."""
     import torch
-    E = qa.shape[0]
+    a = arm if isinstance(arm, _Arm) else make_arm(arm)
+    E = _edge_args(tree, a, qa, qb, nsteps, valid)
     if valid is None:
         valid = torch.empty(E, dtype=torch.uint8, device=qa.device)
-    a = arm if isinstance(arm, _Arm) else make_arm(arm)
     _check(_load().capt_validate_edges_static(tree.h, C.byref(a), _dev(qa, torch.float32, "qa"),
                                               _dev(qb, torch.float32, "qb"), _dev(nsteps, torch.int32, "nsteps"), E,
                                               _dev(valid, torch.uint8, "valid"), _stream(stream)),
@@ -522,8 +590,8 @@ class EdgePlan:
 
 def capt_edge_plan_create(tree: CaptTree, arm, qa, qb, nsteps, valid, cfg=None, stream=None) -> EdgePlan:
     import torch
-    E = qa.shape[0]
     a = arm if isinstance(arm, _Arm) else make_arm(arm)
+    E = _edge_args(tree, a, qa, qb, nsteps, valid)
     c = None if cfg is None else C.byref(_LaunchCfg(cfg["warps_per_block"], cfg["spheres_per_lane"], cfg["staging"],
                                                     cfg["chunk"]))
     h = C.c_void_p()
@@ -559,6 +627,11 @@ def capt_clearance_fwd(tree: CaptTree, centers, radii, margin: float, cost=None,
     if centers.dim() != 4 or centers.shape[3] != 3:
         raise ValueError("centers must be [T, W, S, 3]")
     T, W, S = centers.shape[:3]
+    if radii.shape != (S,):
+        raise ValueError("radii must be [S]")
+    _numel(cost, T, "cost")
+    _numel(dist, T * W * S, "dist")
+    _numel(argmin, T * W * S, "argmin")
     dev = centers.device
     cost = torch.empty(T, dtype=torch.float32, device=dev) if cost is None else cost
     dist = torch.empty((T, W, S), dtype=torch.float32, device=dev) if dist is None else dist
@@ -573,7 +646,15 @@ def capt_clearance_fwd(tree: CaptTree, centers, radii, margin: float, cost=None,
 def capt_clearance_bwd(tree: CaptTree, centers, radii, dist, argmin, grad_cost, margin: float, grad=None,
                        stream=None):
     import torch
+    if centers.dim() != 4 or centers.shape[3] != 3:
+        raise ValueError("centers must be [T, W, S, 3]")
     T, W, S = centers.shape[:3]
+    if radii.shape != (S,):
+        raise ValueError("radii must be [S]")
+    _numel(dist, T * W * S, "dist")
+    _numel(argmin, T * W * S, "argmin")
+    _numel(grad_cost, T, "grad_cost")
+    _numel(grad, T * W * S * 3, "grad")
     grad = torch.empty_like(centers) if grad is None else grad
     _check(_load().capt_clearance_bwd(tree.h, _dev(centers, torch.float32, "centers"),
                                       _dev(radii, torch.float32, "radii"), _dev(dist, torch.float32, "dist"),

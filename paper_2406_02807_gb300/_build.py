@@ -36,30 +36,48 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu"))) + sorted(glob.glob(os.path.join(CSRC, "*.cpp")))
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
         glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every translation unit for sm_103a and link libcapt.so next to this file."""
-    if not force and not _stale():
-        return LIB
+# Test-only variants: the same sources with extra preprocessor definitions, built into
+# their own directory and library (never loaded unless a caller names the file).
+VARIANTS = {
+    # every first wait on a bulk copy into shared memory gives up at once (the copies
+    # still complete and are drained): exercises the CAPT_E_TIMEOUT fallback paths
+    "stage_timeout": ["-DCAPT_STAGE_POLLS=0u"],
+}
+
+
+def variant_lib(name: str) -> str:
+    return os.path.join(HERE, f"libcapt_{name}.so")
+
+
+def build(force: bool = False, verbose: bool = False, variant: str | None = None) -> str:
+    """Compile every translation unit for sm_103a and link libcapt.so next to this file
+    (or, for a test variant, libcapt_<variant>.so from its own build directory)."""
+    lib = LIB if variant is None else variant_lib(variant)
+    outdir = OUTDIR if variant is None else OUTDIR + "_" + variant
+    defines = [] if variant is None else VARIANTS[variant]
+    if not force and not _stale(lib):
+        return lib
     nvcc = _nvcc()
-    os.makedirs(OUTDIR, exist_ok=True)
+    os.makedirs(outdir, exist_ok=True)
     inc = ["-I", INCLUDE, "-I", CSRC]
 
     def compile_one(src):
-        obj = os.path.join(OUTDIR, os.path.basename(src) + ".o")
+        obj = os.path.join(outdir, os.path.basename(src) + ".o")
         if src.endswith(".cu"):
             extra = os.environ.get("CAPT_NVCC_EXTRA", "").split()
-            cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, *inc, "-c", src, "-o", obj]
+            cmd = [nvcc, *ARCH, *NVCC_FLAGS, *defines, *extra, *inc, "-c", src, "-o", obj]
         else:
-            cmd = [os.environ.get("CXX", "g++"), *CXX_FLAGS, *inc, "-I", _cuda_include(nvcc), "-c", src, "-o", obj]
+            cmd = [os.environ.get("CXX", "g++"), *CXX_FLAGS, *defines, *inc, "-I", _cuda_include(nvcc), "-c", src,
+                   "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"compile failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
@@ -69,13 +87,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-lpthread", "-ldl", "-lrt"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

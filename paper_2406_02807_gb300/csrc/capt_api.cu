@@ -92,6 +92,7 @@ struct capt_tree {
     float* d_pipe_c[2] = {nullptr, nullptr};
     uint8_t* d_pipe_f[2] = {nullptr, nullptr};
     size_t pipe_cap = 0;   // floats per centre buffer
+    size_t pipe_fbytes = 0;   // bytes per flag buffer
     cudaStream_t pipe_stream = nullptr;
     cudaEvent_t pipe_ev[4] = {nullptr, nullptr, nullptr, nullptr};
     uint8_t* d_zc_flags = nullptr;  // flags of the zero-copy path when h_flags is pageable
@@ -193,6 +194,7 @@ struct capt_tree {
         for (auto& e : pipe_ev) e = nullptr;
         pipe_stream = nullptr;
         pipe_cap = 0;
+        pipe_fbytes = 0;
         edge_scratch_cap = 0;
         dev_bytes = 0;
         device = -1;
@@ -296,6 +298,7 @@ bool ensure_pipe(capt_tree* t, size_t chunk, int S) {
         t->d_pipe_f[i] = nullptr;
     }
     t->pipe_cap = 0;
+    t->pipe_fbytes = 0;
     for (int i = 0; i < 2; i++) {
         if (cudaMalloc((void**)&t->d_pipe_c[i], (cfloats + 64) * sizeof(float)) != cudaSuccess ||
             cudaMalloc((void**)&t->d_pipe_f[i], chunk + 256) != cudaSuccess) {
@@ -304,6 +307,7 @@ bool ensure_pipe(capt_tree* t, size_t chunk, int S) {
         }
     }
     t->pipe_cap = cfloats + 64;
+    t->pipe_fbytes = chunk + 256;
     if (!t->pipe_stream && cudaStreamCreateWithFlags(&t->pipe_stream, cudaStreamNonBlocking) != cudaSuccess) return false;
     for (auto& e : t->pipe_ev)
         if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return false;
@@ -563,6 +567,8 @@ int capt_stats(const capt_tree* t, capt_tree_stats* s) {
     s->compact_chunks = t->cs.n_chunks;
     s->compact_entries = t->cs.list_len;
     s->compact_bytes = t->cs.bytes;
+    s->scratch_bytes = (uint64_t)t->edge_scratch_cap * sizeof(uint32_t) +
+                       2 * ((uint64_t)t->pipe_cap * sizeof(float) + t->pipe_fbytes) + (uint64_t)t->zc_cap;
     s->full_dropped = t->full_dropped ? 1 : 0;
     return CAPT_OK;
 }
@@ -836,7 +842,7 @@ int capt_device_status(const capt_tree* t, void* stream) {
     CUDA_TRY(cudaMemsetAsync(t->d_status, 0, sizeof(int), st), "status clear");
     CUDA_TRY(cudaStreamSynchronize(st), "synchronize");
     if (word & 1) return fail(CAPT_E_TIMEOUT, "a bounded device wait gave up");
-    if (word & 2) return fail(CAPT_E_BOUNDS, "a device-side index check failed");
+    if (word & 2) return fail(CAPT_E_BOUNDS, "a device-side index or size check failed (e.g. an edge batch over 2^31 work items)");
     return CAPT_OK;
 }
 

@@ -17,6 +17,24 @@ namespace capt {
 constexpr int kStatusTimeout = 1;
 constexpr int kStatusBounds = 2;
 
+// Poll limits of the bounded mbarrier waits on bulk copies into shared memory.  A copy
+// of a few KB lands within microseconds; a wait that gives up after kStagePolls latches
+// kStatusTimeout and the kernel carries on from global memory.  Before that shared
+// memory can be reused (by the warp's own direct loads, or by the next block on the SM
+// once this one exits) the copy still in flight is waited for again, up to kDrainPolls
+// (about 2^26 polls, tenths of a second): a copy outstanding after that means the memory
+// system itself has failed, and the status word already says so.  A test build sets
+// CAPT_STAGE_POLLS to 0, which makes every first wait give up at once while the copies
+// still complete, to exercise this path.
+#ifndef CAPT_STAGE_POLLS
+#define CAPT_STAGE_POLLS (1u << 22)
+#endif
+#ifndef CAPT_DRAIN_POLLS
+#define CAPT_DRAIN_POLLS (1u << 26)
+#endif
+constexpr uint32_t kStagePolls = CAPT_STAGE_POLLS;
+constexpr uint32_t kDrainPolls = CAPT_DRAIN_POLLS;
+
 // Bytes of the blocked split prefix staged into shared memory (a multiple of 16), and
 // the offset of what follows it in dynamic shared memory (rounded up to 128).
 __host__ __device__ __forceinline__ uint32_t stage_bytes(const DevArgs& t) { return t.stage_floats * 4u; }
@@ -148,16 +166,19 @@ __device__ __forceinline__ bool stage_to_smem(void* dst, const void* src, uint32
                 : "memory");
         }
     }
-    // bounded wait: about 2^22 polls (far beyond the microseconds a 32 KB copy takes)
+    // bounded wait: kStagePolls polls (far beyond the microseconds a 32 KB copy takes)
     bool done = false;
-    for (uint32_t it = 0; it < (1u << 22); it++) {
+    for (uint32_t it = 0; it < kStagePolls; it++) {
         if (mbar_try_wait(b, 0)) { done = true; break; }
     }
     int all_done = __syncthreads_and(done ? 1 : 0);
     if (!all_done) {
         if (threadIdx.x == 0) atomicOr(status, kStatusTimeout);
-        // wait (bounded again) for the copy still in flight before the block may exit
-        for (uint32_t it = 0; it < (1u << 22); it++)
+        // the block reads T from global memory from here on and never touches the
+        // staged region; the copy still in flight is waited for (kDrainPolls) before
+        // the block goes on, so it has landed before the block can exit and hand its
+        // shared memory to the next one
+        for (uint32_t it = 0; it < kDrainPolls; it++)
             if (mbar_try_wait(b, 0)) break;
         __syncthreads();
         return false;

@@ -7,8 +7,11 @@
 // and take unbounded time), and a host application whose device memory is owned by
 // another allocator (a caching allocator, a fixed arena) cannot have raw allocations
 // appear behind its back.  capt_validate_edges_static serves them: its scratch is a
-// fixed array in the library's own device memory, reserved when the library is loaded
-// on a device and held until the process exits.
+// fixed array in the library's own device memory, reserved when the library's device
+// code is loaded into a device's context (with CUDA's lazy module loading, at the first
+// call that needs it, at the latest this entry point's first call on that device) and
+// held until the context ends.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -27,13 +30,55 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) uint32_t g_edge_scratch[CAPT_STATIC_MAX_EDGES + 64];
 
 std::mutex g_mu;
+// Per device: the array's device address and the unique ID of the context it belongs
+// to.  A reset of the device (cudaDeviceReset) ends that context and the next runtime
+// call creates a new one with a new ID, in which the array has a new address; the ID
+// tells the two apart, so a stale address is never used.
 uint32_t* g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
 
 thread_local std::string g_static_err;
 
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// The two driver calls that identify the current context, found through the runtime
+// (no link-time dependency on the driver library).
+bool ctx_fns(CtxGetCurrentFn* cur, CtxGetIdFn* id) {
+    static CtxGetCurrentFn s_cur = nullptr;
+    static CtxGetIdFn s_id = nullptr;
+    static bool s_done = false;
+    if (!s_done) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            s_cur = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            s_id = reinterpret_cast<CtxGetIdFn>(f);
+        cudaGetLastError();
+        s_done = true;
+    }
+    *cur = s_cur;
+    *id = s_id;
+    return s_cur && s_id;
+}
+
+// ID of the context current on this thread, or 0 when none is bound yet.
+unsigned long long current_ctx_id(CtxGetCurrentFn cur, CtxGetIdFn id) {
+    CUcontext c = nullptr;
+    unsigned long long v = 0;
+    if (cur(&c) != CUDA_SUCCESS || !c) return 0;
+    if (id(c, &v) != CUDA_SUCCESS) return 0;
+    return v;
+}
+
 // Device address of g_edge_scratch on the current device.  In host code the name of a
-// __device__ array is only a host-side stand-in, so the address is looked up once per
-// device with cudaGetSymbolAddress (with that device current) and cached.
+// __device__ array is only a host-side stand-in, so the address is looked up with
+// cudaGetSymbolAddress, with that device current, once per device and context (the
+// set-up), and cached.
 int scratch_for_current_device(uint32_t** out, int* dev_out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
@@ -46,14 +91,27 @@ int scratch_for_current_device(uint32_t** out, int* dev_out) {
         return CAPT_E_STATE;
     }
     std::lock_guard<std::mutex> g(g_mu);
-    if (!g_scratch_addr[dev]) {
+    CtxGetCurrentFn cur;
+    CtxGetIdFn idf;
+    if (!ctx_fns(&cur, &idf)) {
+        g_static_err = "the driver does not provide cuCtxGetCurrent / cuCtxGetId";
+        return CAPT_E_CUDA;
+    }
+    const unsigned long long ctx = current_ctx_id(cur, idf);
+    if (!g_scratch_addr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_edge_scratch);
+        e = cudaGetSymbolAddress(&p, g_edge_scratch);   // binds the device's context if needed
         if (e != cudaSuccess || !p) {
             g_static_err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
             return CAPT_E_CUDA;
         }
+        const unsigned long long now = current_ctx_id(cur, idf);
+        if (now == 0) {
+            g_static_err = "no CUDA context is current after cudaGetSymbolAddress";
+            return CAPT_E_CUDA;
+        }
         g_scratch_addr[dev] = static_cast<uint32_t*>(p);
+        g_scratch_ctx[dev] = now;
     }
     *out = g_scratch_addr[dev];
     *dev_out = dev;

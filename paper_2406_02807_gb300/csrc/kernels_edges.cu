@@ -268,40 +268,63 @@ __device__ __forceinline__ uint8_t load_volatile_u8(const uint8_t* p) {
 }
 
 // Exclusive prefix of per-edge work items; resets validity and the work counter.
-// One block; scratch = [E + 1 offsets][counter].
+// One block; scratch = [E + 1 offsets][counter].  The offsets, the total and the
+// counter are 32-bit words, so the prefix is summed in 64 bits and the batch is refused
+// on the device when its total exceeds kMaxEdgeItems (2^31 items, 2^36 or more
+// configurations): the counter then stays far from wrapping (it ends at most one take
+// per warp past the total).  A refused batch does no work, reports every edge as not
+// valid (0) and latches kStatusBounds in the status word.
+constexpr uint64_t kMaxEdgeItems = 1ull << 31;
+
+__device__ __forceinline__ unsigned long long warp_incl_scan64(unsigned long long v) {
+    const uint32_t lane = lane_id();
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= (uint32_t)o) v += u;
+    }
+    return v;
+}
+
 __global__ void k_edges_setup(const int32_t* __restrict__ ns, uint32_t E, uint32_t chunk, uint32_t* scratch,
-                              uint8_t* __restrict__ valid) {
-    __shared__ uint32_t warp_sums[32];
-    __shared__ uint32_t carry;
+                              uint8_t* __restrict__ valid, int* status) {
+    __shared__ unsigned long long warp_sums[32];
+    __shared__ unsigned long long carry;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (uint32_t base = 0; base < E; base += blockDim.x) {
         const uint32_t e = base + threadIdx.x;
-        uint32_t items = 0;
+        uint32_t items = 0;   // at most 2^26 (n_e < 2^31, chunk >= 32)
         if (e < E) {
             const int n = ns[e];
-            items = n > 0 ? ((uint32_t)n + chunk - 1) / chunk : 0u;
+            items = n > 0 ? (uint32_t)(((uint64_t)n + chunk - 1) / chunk) : 0u;
             valid[e] = 1;
         }
-        const uint32_t incl = warp_incl_scan(items);
+        const unsigned long long incl = warp_incl_scan64(items);
         if (lane == 31) warp_sums[warp] = incl;
         __syncthreads();
         if (warp == 0) {
-            uint32_t v = lane < nw ? warp_sums[lane] : 0u;
-            v = warp_incl_scan(v);
+            unsigned long long v = lane < nw ? warp_sums[lane] : 0ull;
+            v = warp_incl_scan64(v);
             if (lane < nw) warp_sums[lane] = v;
         }
         __syncthreads();
-        const uint32_t before = carry + (warp ? warp_sums[warp - 1] : 0u);
-        if (e < E) scratch[e] = before + incl - items;
+        const unsigned long long before = carry + (warp ? warp_sums[warp - 1] : 0ull);
+        // offsets past the limit are never read: the batch is refused below
+        if (e < E) scratch[e] = (uint32_t)min(before + incl - items, (unsigned long long)kMaxEdgeItems);
         __syncthreads();
         if (threadIdx.x == 0) carry += warp_sums[nw - 1];
         __syncthreads();
     }
+    const bool refuse = carry > kMaxEdgeItems;
+    if (refuse) {
+        for (uint32_t e = threadIdx.x; e < E; e += blockDim.x) valid[e] = 0;
+    }
     if (threadIdx.x == 0) {
-        scratch[E] = carry;
+        scratch[E] = refuse ? 0u : (uint32_t)carry;
         scratch[E + 1] = 0;   // work counter
+        if (refuse) atomicOr(status, kStatusBounds);
     }
 }
 
@@ -341,9 +364,9 @@ __global__ void __launch_bounds__(512, 2) k_edges_persistent(DevArgs t, const __
         // the edge's items interleave its configurations: item ci of nci takes
         // ci, ci + nci, ci + 2 nci, ..., so its first passes sample the whole edge and a
         // colliding stretch is met early wherever it lies
-        const int nci = (n_e + (int)chunk - 1) / (int)chunk;
+        const int nci = (int)(((int64_t)n_e + chunk - 1) / chunk);
         const int ci = (int)(item - __ldg(scratch + e));
-        const int cnt = (n_e - ci + nci - 1) / nci;
+        const int cnt = (int)(((int64_t)n_e - ci + nci - 1) / nci);
         const float* qa_e = qa + (size_t)e * J;
         const float* qb_e = qb + (size_t)e * J;
         for (int j = 0; j < cnt; j += 32) {
@@ -365,9 +388,9 @@ __global__ void __launch_bounds__(512, 2) k_edge_single(DevArgs t, const __grid_
     EdgeScratch* ws = reinterpret_cast<EdgeScratch*>(smem_raw) + (threadIdx.x >> 5);
     const int warps = (int)(gridDim.x * (blockDim.x >> 5));
     const int gw = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
-    for (int k = gw * 32; k < n_e; k += warps * 32) {
+    for (int64_t k = (int64_t)gw * 32; k < n_e; k += (int64_t)warps * 32) {
         if (load_volatile_u8(valid_e) == 0) break;
-        if (edge_pass<MODE>(t, arm, qa_e, qb_e, n_e, k, 1, min(32, n_e - k), nullptr, ws)) {
+        if (edge_pass<MODE>(t, arm, qa_e, qb_e, n_e, (int)k, 1, (int)min((int64_t)32, n_e - k), nullptr, ws)) {
             if (lane_id() == 0) *valid_e = 0;
             break;
         }
@@ -524,7 +547,7 @@ int launch_edges_persistent(const DevArgs& t, const capt_arm& arm, const float* 
                             const capt_launch_cfg& cfg, cudaStream_t st, std::string& err) {
     if (E == 0) return CAPT_OK;
     const uint32_t chunk = item_chunk(cfg);
-    k_edges_setup<<<1, 1024, 0, st>>>(ns, (uint32_t)E, chunk, scratch, valid);
+    k_edges_setup<<<1, 1024, 0, st>>>(ns, (uint32_t)E, chunk, scratch, valid, t.status);
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) { err = std::string("edge setup launch: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
     const bool stage = cfg.staging == CAPT_STAGE_SMEM && t.stage_floats > 0;
@@ -559,8 +582,8 @@ int launch_edges_per_edge(const DevArgs& t, const capt_arm& arm, const float* qa
     for (uint64_t e = 0; e < E; e++) {
         const int n = h_ns[e];
         if (n <= 0) continue;
-        const int warps_needed = (n + 31) / 32;
-        const int blocks = (warps_needed + warps - 1) / warps;
+        const int64_t warps_needed = ((int64_t)n + 31) / 32;
+        const unsigned blocks = (unsigned)std::min<int64_t>((warps_needed + warps - 1) / warps, (int64_t)sm_count() * 64);
         fn<<<blocks, warps * 32, smem, st>>>(t, plan, qa + e * J, qb + e * J, n, valid + e);
     }
     ce = cudaGetLastError();

@@ -77,8 +77,12 @@ __global__ void __launch_bounds__(512, 2)
 
     // Tile inputs (centres, radii) are staged per warp by the bulk copy engine,
     // double-buffered: while the warp works on one tile, the copy of its next tile is in
-    // flight.  Ragged or misaligned tiles, and every tile after a copy that did not
-    // complete in time, are loaded directly into the same buffer instead.
+    // flight.  Ragged or misaligned tiles are loaded directly into the same buffer
+    // instead (no copy is in flight into it then).  If a wait gives up (kStagePolls), the
+    // warp latches kStatusTimeout, issues no further copies and reads every later tile
+    // straight from global memory without writing either buffer, so a copy that is still
+    // landing cannot race with it; before the warp exits it waits (kDrainPolls) for every
+    // copy it issued that it has not seen complete.
     if (lane == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&ws->bar[0])) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&ws->bar[1])) : "memory");
@@ -86,7 +90,8 @@ __global__ void __launch_bounds__(512, 2)
     }
     __syncwarp();
     bool bulk_ok = true;
-    uint32_t uses0 = 0, uses1 = 0;  // completed phases of bar[0] / bar[1]
+    bool pend0 = false, pend1 = false;   // a copy into in[0] / in[1] not yet seen complete
+    uint32_t ph0 = 0, ph1 = 0;           // parity of the phase that copy completes
     auto issue = [&](uint64_t tl, int b) -> bool {
         if (tl >= n_tiles || !bulk_ok) return false;
         const uint64_t first = tl * E;
@@ -104,7 +109,22 @@ __global__ void __launch_bounds__(512, 2)
             bulk_copy(ws->in[b], c, cnt * 12u, &ws->bar[b]);
             bulk_copy(ws->in[b] + 3 * E, r, cnt * 4u, &ws->bar[b]);
         }
+        if (b) pend1 = true;
+        else pend0 = true;
         return true;
+    };
+    // bounded wait for the outstanding copy into in[b]; true once it has landed
+    auto wait_buf = [&](int b, uint32_t polls) -> bool {
+        const uint32_t bar = smem_u32(&ws->bar[b]);
+        const uint32_t parity = b ? ph1 : ph0;
+        bool done = false;
+        for (uint32_t it = 0; it < polls && !done; it++) done = mbar_try_wait(bar, parity);
+        done = __all_sync(0xffffffffu, done);
+        if (done) {
+            if (b) { pend1 = false; ph1 ^= 1u; }
+            else { pend0 = false; ph0 ^= 1u; }
+        }
+        return done;
     };
 
     const TileSched sched{ctr, nwarps};
@@ -117,19 +137,16 @@ __global__ void __launch_bounds__(512, 2)
         float* in = ws->in[buf];
         bool from_smem = false;
         if (staged) {
-            const uint32_t parity = (buf ? uses1 : uses0) & 1u;
-            bool done = false;
-            for (uint32_t it = 0; it < (1u << 22) && !done; it++) done = mbar_try_wait(smem_u32(&ws->bar[buf]), parity);
-            done = __all_sync(0xffffffffu, done);
-            if (buf) uses1++;
-            else uses0++;
-            if (done) {
+            if (wait_buf(buf, kStagePolls)) {
                 from_smem = true;
             } else {
                 if (lane == 0) atomicOr(t.status, kStatusTimeout);
                 bulk_ok = false;
             }
         }
+        // after a timeout no buffer is written again: inputs come from global memory
+        const bool direct_to_smem = !from_smem && bulk_ok;
+        const bool in_smem = from_smem || direct_to_smem;
         staged = next_staged && bulk_ok;
         const uint64_t first = tile * E;
         const uint32_t n_here = (uint32_t)min((uint64_t)E, m - first);
@@ -151,10 +168,12 @@ __global__ void __launch_bounds__(512, 2)
                     y = __ldg(centers + 3 * (first + j) + 1);
                     z = __ldg(centers + 3 * (first + j) + 2);
                     r = __ldg(radii + first + j);
-                    in[3 * j] = x;
-                    in[3 * j + 1] = y;
-                    in[3 * j + 2] = z;
-                    in[3 * E + j] = r;
+                    if (direct_to_smem) {
+                        in[3 * j] = x;
+                        in[3 * j + 1] = y;
+                        in[3 * j + 2] = z;
+                        in[3 * E + j] = r;
+                    }
                 }
                 near = box_dist2(x, y, z, rlo, rhi) <= __fmul_rn(r, r);
             }
@@ -172,8 +191,19 @@ __global__ void __launch_bounds__(512, 2)
             uint32_t j = 0;
             if (live) {
                 j = ws->nslot[q];
-                const float r = in[3 * E + j];
-                c = make_float4(in[3 * j], in[3 * j + 1], in[3 * j + 2], __fmul_rn(r, r));
+                float x, y, z, r;
+                if (in_smem) {
+                    x = in[3 * j];
+                    y = in[3 * j + 1];
+                    z = in[3 * j + 2];
+                    r = in[3 * E + j];
+                } else {
+                    x = __ldg(centers + 3 * (first + j));
+                    y = __ldg(centers + 3 * (first + j) + 1);
+                    z = __ldg(centers + 3 * (first + j) + 2);
+                    r = __ldg(radii + first + j);
+                }
+                c = make_float4(x, y, z, __fmul_rn(r, r));
             }
             sphere_round<false, MODE>(t, Ts, &ws->re, ws->ghit, c, j, live, lane, lt_mask);
         }
@@ -185,6 +215,9 @@ __global__ void __launch_bounds__(512, 2)
         }
         __syncwarp();
     }
+    // every copy this warp issued has landed before its shared memory can be handed on
+    if (pend0) wait_buf(0, kDrainPolls);
+    if (pend1) wait_buf(1, kDrainPolls);
 }
 
 // ------------------------------------------------------------------------------------

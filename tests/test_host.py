@@ -127,7 +127,7 @@ def test_compact_rejects_unuploaded_tree_without_gpu(capt_lib):
     assert L.capt_compact(None, 0, None) == -1
     st = capt_lib.capt_stats(t)
     assert st["compact_chunks"] == st["compact_entries"] == st["compact_bytes"] == st["full_dropped"] == 0
-    assert ctypes.sizeof(capt_lib._Stats) == 120                  # the C struct's size
+    assert ctypes.sizeof(capt_lib._Stats) == 128                  # the C struct's size
 
 
 def test_joint_and_filter_calls_reject_bad_arguments_without_gpu(capt_lib):
@@ -174,3 +174,79 @@ def test_depth_frame_is_a_full_deterministic_frame():
     assert np.array_equal(f, W.depth_frame())
     # the camera looks down at the table: most pixels see the table top or what is on it
     assert ((f[:, 2] > -0.01) & (f[:, 0] >= -0.01) & (f[:, 0] <= 1.21)).mean() > 0.5
+
+
+def test_edge_and_query_bindings_reject_mismatched_buffers_without_gpu(capt_lib):
+    """The C ABI receives base addresses and counts only, so the binding must refuse
+    buffers whose shapes disagree before any pointer reaches a kernel."""
+    import torch
+    pts = W.uniform_cloud(64, 7)
+    tree = capt_lib.capt_build(pts, 0.02, 0.08)
+    arm = W.arm_7dof()
+    E = 8
+    qa = torch.zeros((E, 7))
+    ns = torch.ones(E, dtype=torch.int32)
+    bad = [
+        dict(qa=torch.zeros((E, 6)), qb=torch.zeros((E, 6)), nsteps=ns, valid=None),      # wrong joint count
+        dict(qa=qa, qb=torch.zeros((E - 1, 7)), nsteps=ns, valid=None),                  # shorter qb
+        dict(qa=qa, qb=qa, nsteps=torch.ones(E - 1, dtype=torch.int32), valid=None),     # shorter nsteps
+        dict(qa=qa, qb=qa, nsteps=ns, valid=torch.ones(E - 2, dtype=torch.uint8)),       # shorter valid
+        dict(qa=torch.zeros(E * 7), qb=torch.zeros(E * 7), nsteps=ns, valid=None),        # flat qa
+    ]
+    for kw in bad:
+        with pytest.raises(ValueError):
+            capt_lib.capt_validate_edges(tree, arm, kw["qa"], kw["qb"], kw["nsteps"], kw["valid"])
+        with pytest.raises(ValueError):
+            capt_lib.capt_validate_edges_static(tree, arm, kw["qa"], kw["qb"], kw["nsteps"], kw["valid"])
+        with pytest.raises(ValueError):
+            capt_lib.capt_edge_plan_create(tree, arm, kw["qa"], kw["qb"], kw["nsteps"],
+                                           kw["valid"] if kw["valid"] is not None else torch.ones(E, dtype=torch.uint8))
+    # outputs of the other queries
+    c = torch.zeros((5, 60, 3))
+    r = torch.ones(60)
+    with pytest.raises(ValueError):
+        capt_lib.capt_query_configs(tree, c, r, torch.zeros(4, dtype=torch.uint8))
+    with pytest.raises(ValueError):
+        capt_lib.capt_query_configs(tree, c, torch.ones(59))
+    with pytest.raises(ValueError):
+        capt_lib.capt_query_spheres(tree, torch.zeros((5, 3)), torch.ones(5), torch.zeros(6, dtype=torch.uint8))
+    with pytest.raises(ValueError):
+        capt_lib.capt_query_joint_configs(tree, arm, torch.zeros((5, 7)), torch.zeros(3, dtype=torch.uint8))
+    with pytest.raises(ValueError):
+        capt_lib.capt_query_leaves(tree, torch.zeros((5, 3)), torch.zeros(4, dtype=torch.int32))
+    with pytest.raises(ValueError):
+        capt_lib.capt_query_configs_host(tree, np.zeros((5, 60, 3), np.float32), np.ones(60, np.float32),
+                                         np.zeros(4, np.uint8))
+    cc = torch.zeros((2, 3, 60, 3))
+    with pytest.raises(ValueError):
+        capt_lib.capt_clearance_fwd(tree, cc, r, 0.01, dist=torch.zeros(2 * 3 * 60 - 1))
+    with pytest.raises(ValueError):
+        capt_lib.capt_clearance_bwd(tree, cc, r, torch.zeros(360), torch.zeros(360, dtype=torch.int32),
+                                    torch.ones(3), 0.01)
+
+
+def test_binding_structs_match_the_c_header(capt_lib, tmp_path):
+    """The ctypes mirrors of the header's structs have the C compiler's sizes and field
+    offsets (a mismatch would make every call read or write the wrong bytes)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"capt_tree_stats": capt_lib._Stats, "capt_launch_cfg": capt_lib._LaunchCfg, "capt_arm": capt_lib._Arm}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "capt.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "sizes.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "sizes"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    for cname, py in structs.items():
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, f"{cname}.{f}"

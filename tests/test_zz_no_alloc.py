@@ -57,3 +57,35 @@ def test_static_edges_reject_batches_over_the_limit(capt_lib):
     with pytest.raises(capt_lib.CaptError) as e:
         capt_lib.capt_validate_edges_static(tree, arm, q, q, ns)
     assert e.value.status == -1 and "65536" in str(e.value)
+
+
+def test_static_edges_allocate_no_device_memory(capt_lib):
+    """The point of the entry point: repeated calls leave the device's free memory and the
+    tree's on-demand scratch exactly as they were.  The allocating entry point, called
+    afterwards on the same tree, does allocate its scratch (the check can see it)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    raw, _, arm = W.tabletop_scene(1001)
+    pts = raw[capt_lib.sfc_filter(raw, 0.01)]
+    tree = capt_lib.capt_build(pts, 0.02, 0.08)
+    capt_lib.capt_upload(tree, 0)
+    qa, qb, ns = W.random_edges(1024, 1008)
+    dqa, dqb, dns = (torch.from_numpy(a).cuda() for a in (qa, qb, ns))
+    outs = [torch.empty(len(ns), dtype=torch.uint8, device="cuda") for _ in range(4)]
+    # first call: the per-device set-up and the first launch of each kernel
+    capt_lib.capt_validate_edges_static(tree, arm, dqa, dqb, dns, outs[0])
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    assert capt_lib.capt_stats(tree)["scratch_bytes"] == 0
+    for o in outs[1:]:
+        capt_lib.capt_validate_edges_static(tree, arm, dqa, dqb, dns, o)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert capt_lib.capt_stats(tree)["scratch_bytes"] == 0
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+    ref = capt_lib.capt_validate_edges(tree, arm, dqa, dqb, dns)
+    torch.cuda.synchronize()
+    assert capt_lib.capt_stats(tree)["scratch_bytes"] > 0
+    assert torch.equal(ref, outs[0])
