@@ -10,6 +10,10 @@ Also reported: the same through the host-buffer entry point (e2e), edges validat
 second (4,096 edges, persistent graph launch vs one launch per edge), the roofline of
 the query kernel and the oracle timed on the host cores.
 
+Each further workload of the method (clearance forward and backward, the large room
+cloud with replicated and compact sets, the small uniform cloud) is timed in the same
+run under "workloads", with its own roofline and an oracle parity sample.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--all]
 """
 from __future__ import annotations
@@ -40,6 +44,7 @@ SM_MAX_MHZ = 2070.0
 # capture, keyed by the hash of the kernel source it was taken on (null when stale).
 TRAFFIC = {"17cca476bcfba7d6": 778620416 + 4390656}   # profiles/k_configs_tabletop_1M.md
 HBM_FALLBACK_GBS = 6800.0   # used only when MEASURED_PEAKS.json is absent
+PARITY_SAMPLE = 32768       # configurations of the timed run checked against the oracle
 
 
 def hbm_peak():
@@ -60,6 +65,8 @@ def parse():
     ap.add_argument("--configs", type=int, default=1 << 20, help="configurations per GPU")
     ap.add_argument("--all", action="store_true", help="also time the clearance and the other clouds")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the clearance, room and uniform-cloud workloads of the default run")
     ap.add_argument("--headline-only", action="store_true",
                     help="time only the configuration query (for profiling); the JSON line lacks e2e and the rest")
     return ap.parse_args()
@@ -243,12 +250,13 @@ def time_events_flushed(torch, fn, steps, stream, flush):
 
 def cpu_baseline(pts, arm, sample_cfgs):
     """The oracle as it stands: FP32 brute force on all host cores, plus its plain CAPT
-    single-threaded (the paper's setting: one CPU thread)."""
+    single-threaded (the paper's setting: one CPU thread).  Also returns the brute-force
+    flags of the sample (the first configurations of the timed workload)."""
     import oracle
     cores = oracle.default_threads()
     cen = W.fk_centers(arm, W.random_configs(sample_cfgs, 1001))
     t0 = time.perf_counter()
-    oracle.brute_config_flags(pts, cen, arm.sphere_radius, threads=cores)
+    ref_flags = oracle.brute_config_flags(pts, cen, arm.sphere_radius, threads=cores)
     dt = time.perf_counter() - t0
     ot = oracle.PlainCAPT(pts, R_MIN, R_MAX)
     n2 = 2 * sample_cfgs
@@ -261,7 +269,7 @@ def cpu_baseline(pts, arm, sample_cfgs):
                       f"of the workload, {cores} threads ({dt:.1f} s wall, {dt * cores:.0f} core-seconds)",
             "plain_capt_1thread": {"ns_per_sphere_query_examined": dt2 * 1e9 / max(int(counts[0]), 1),
                                    "sphere_queries_per_s": n2 * SPHERES / dt2,
-                                   "sample": f"{n2} configurations, 1 thread ({dt2:.1f} s)"}}
+                                   "sample": f"{n2} configurations, 1 thread ({dt2:.1f} s)"}}, ref_flags
 
 
 def run_reference(args, rank, world):
@@ -363,6 +371,7 @@ def main():
         ms = max_over_ranks(ms, pg, dev)
     value = world * C * SPHERES / (ms / 1e3)
     collide = float(flags.float().mean().item())
+    flags_host = flags[:PARITY_SAMPLE].cpu().numpy()
 
     sec = None if args.headline_only else secondary(capt, torch, dev, stream, tree, arm, q, cen_host, r_host,
                                                     flags, C, args, pg)
@@ -411,10 +420,23 @@ def main():
         }
         if sec:
             out.update(sec)
+        if not args.headline_only and not args.no_workloads:
+            # the other workloads of the paper's method, each timed on the device with its
+            # own roofline (rank 0 only; the other ranks wait at the closing barrier)
+            out["workloads"] = {
+                "clearance": bench_clearance(capt, torch, dev, stream, pts, arm, max(args.steps // 2, 5), sms),
+                "room200k": bench_room(capt, torch, dev, stream, max(args.steps // 2, 5), sms),
+                "uniform2k": bench_uniform(capt, torch, dev, stream, args.steps, sms),
+            }
         if args.all:
             out["extra"] = extra_workloads(capt, torch, dev, stream, pts, arm, args)
         if world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(pts, arm, 32768)
+            out["cpu_baseline"], ref = cpu_baseline(pts, arm, PARITY_SAMPLE)
+            # the timed run's own flags against the oracle's brute force on the sample
+            got = flags_host[:PARITY_SAMPLE]
+            out["parity_sample_equal"] = bool(np.array_equal(got, ref))
+            out["parity_sample"] = (f"flags of configurations 0..{PARITY_SAMPLE - 1} of the timed run vs the "
+                                    f"oracle's FP32 brute force over all {len(pts)} points")
         print(json.dumps(out), flush=True)
     if pg:
         pg.barrier()
@@ -492,24 +514,162 @@ def secondary(capt, torch, dev, stream, tree, arm, q, cen_host, r_host, flags, C
     }
 
 
-def extra_workloads(capt, torch, dev, stream, pts, arm, args):
-    res = {}
-    # clearance forward and forward + backward (16,384 trajectories x 32 waypoints x 60 spheres)
+def roof(ms, hbm_bytes, ops, l1_bytes, sms, note=None):
+    """Both floors of a launch (or step): DRAM bytes against the measured copy bandwidth,
+    FP32 operations against the ALU peak (no FMA on this path), the on-chip bytes
+    beside them.  `bound` names the floor that is higher, the roofline that binds."""
+    peak_gbs, peak_src = hbm_peak()
+    peak_tops = sms * 128 * SM_MAX_MHZ * 1e6 / 1e12
+    t = ms / 1e3
+    hbm = {"achieved": hbm_bytes / t / 1e9, "peak": peak_gbs, "unit": "GB/s", "frac": hbm_bytes / t / 1e9 / peak_gbs,
+           "floor_ms": hbm_bytes / (peak_gbs * 1e9) * 1e3, "bytes": int(hbm_bytes), "peak_basis": peak_src}
+    alu = {"achieved": ops / t / 1e12, "peak": peak_tops, "unit": "TFLOP/s", "frac": ops / t / 1e12 / peak_tops,
+           "floor_ms": ops / (peak_tops * 1e12) * 1e3, "ops": int(ops),
+           "peak_basis": f"{sms} SMs x 128 FP32 lanes x {SM_MAX_MHZ:.0f} MHz"}
+    out = {"bound": "hbm" if hbm["floor_ms"] >= alu["floor_ms"] else "alu"}
+    top = hbm if out["bound"] == "hbm" else alu
+    out.update({k: top[k] for k in ("achieved", "peak", "unit", "frac")})
+    out["hbm"], out["alu"] = hbm, alu
+    if l1_bytes is not None:
+        out["l1_bytes"] = int(l1_bytes)
+        out["l1_frac"] = l1_bytes / t / (sms * 128 * SM_MAX_MHZ * 1e6)
+    if note:
+        out["note"] = note
+    return out
+
+
+def sphere_ops(counts, L, chunked=True):
+    """FP32 operations and on-chip bytes of a sphere query launch from its work counts:
+    a root box test per sphere (15 ops, 16 bytes in), a descent and leaf box test per
+    near sphere (L + 15 ops, 32 + 4 L bytes), then either the chunk walk (15 ops and 32
+    bytes per chunk box, 9 ops and 12 bytes per point scanned) or Alg. 3's plain scan
+    (9 ops and 12 bytes per point)."""
+    c = [int(x) for x in counts]
+    if chunked:
+        return (c[0] * 15 + c[1] * (L + 15) + c[4] * 15 + c[5] * 9,
+                c[0] * 16 + c[1] * (32 + 4 * L) + c[4] * 32 + c[5] * 12)
+    return c[0] * 15 + c[1] * (L + 15) + c[3] * 9, c[0] * 16 + c[1] * (32 + 4 * L) + c[3] * 12
+
+
+def bench_clearance(capt, torch, dev, stream, pts, arm, steps, sms):
+    """The differentiable clearance workload: 16,384 trajectories x 32 waypoints x 60
+    spheres, forward (distances, argmin, hinge cost) and backward, inputs (377 MB of
+    centres) larger than L2."""
+    import oracle
     ctree = capt.capt_build(pts, 0.0, R_MAX)
     capt.capt_upload(ctree, dev.index)
     T, Wn = 16384, 32
     q = W.random_trajectories(T, Wn, 1003)
-    c = torch.from_numpy(W.fk_centers(arm, q.reshape(-1, 7)).reshape(T, Wn, SPHERES, 3)).to(dev)
+    c_host = W.fk_centers(arm, q.reshape(-1, 7)).reshape(T, Wn, SPHERES, 3)
+    c = torch.from_numpy(c_host).to(dev)
     r = torch.from_numpy(arm.sphere_radius.copy()).to(dev)
     g = torch.ones(T, device=dev)
     cost, d, am = capt.capt_clearance_fwd(ctree, c, r, 0.01)
-    fwd_ms = time_events(torch, lambda: capt.capt_clearance_fwd(ctree, c, r, 0.01, cost, d, am), 10, stream)
     grad = torch.empty_like(c)
-    bwd_ms = time_events(torch, lambda: capt.capt_clearance_bwd(ctree, c, r, d, am, g, 0.01, grad), 10, stream)
+    for _ in range(3):
+        capt.capt_clearance_fwd(ctree, c, r, 0.01, cost, d, am)
+        capt.capt_clearance_bwd(ctree, c, r, d, am, g, 0.01, grad)
+    fwd_ms = time_events(torch, lambda: capt.capt_clearance_fwd(ctree, c, r, 0.01, cost, d, am), steps, stream)
+    bwd_ms = time_events(torch, lambda: capt.capt_clearance_bwd(ctree, c, r, d, am, g, 0.01, grad), steps, stream)
     m = T * Wn * SPHERES
-    res["clearance"] = {"spheres": m, "fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "fwd_spheres_per_s": m / (fwd_ms / 1e3),
-                        "fwd_bwd_spheres_per_s": m / ((fwd_ms + bwd_ms) / 1e3),
-                        "bwd_hbm_GBps": m * (12 + 4 + 4 + 12 + 12) / (bwd_ms / 1e3) / 1e9}
+    counts = capt.capt_count_clearance_work(ctree, c).cpu().numpy().astype(np.int64)
+    L = capt.capt_stats(ctree)["depth"]
+    ops = int(counts[0]) * 15 + int(counts[1]) * (L + 15) + int(counts[3]) * 9
+    l1 = int(counts[0]) * 12 + int(counts[1]) * (32 + 4 * L) + int(counts[4]) * 48
+    fwd_bytes = m * (12 + 4 + 4) + T * 4          # centres in; distance and argmin out; cost
+    bwd_bytes = m * (12 + 4 + 4 + 12) + T * 4      # centres, distance, argmin in; gradient out
+    # parity sample: the first 8 trajectories against the oracle's FP64 nearest distance
+    k = 8
+    ocost, od, _ = oracle.clearance64(pts, c_host[:k], arm.sphere_radius, R_MAX, 0.01, want_grad=False)
+    derr = float(np.abs(d[:k].cpu().numpy().astype(np.float64) - od).max())
+    cerr = float(np.abs(cost[:k].cpu().numpy().astype(np.float64) - ocost).max())
+    return {"trajectories": T, "waypoints": Wn, "spheres": m, "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
+            "fwd_spheres_per_s": m / (fwd_ms / 1e3), "fwd_bwd_spheres_per_s": m / ((fwd_ms + bwd_ms) / 1e3),
+            "launch_cfg": capt.capt_get_launch_cfg(ctree, capt.CAPT_KERNEL_CLEARANCE),
+            "work": {"spheres": int(counts[0]), "near_cloud_box": int(counts[1]), "leaf_box_pass": int(counts[2]),
+                     "points_scanned": int(counts[3]), "blocks_scanned": int(counts[4]),
+                     "points_per_sphere": float(counts[3]) / m},
+            "roofline_fwd": roof(fwd_ms, fwd_bytes, ops, l1, sms),
+            "roofline_bwd": roof(bwd_ms, bwd_bytes, m * 12, None, sms),
+            "l2": "inputs larger than L2 (377 MB of centres)",
+            "parity_sample": {"trajectories": k, "max_abs_dist_err_vs_fp64": derr, "max_abs_cost_err_vs_fp64": cerr,
+                              "within_1e-5": derr <= 1e-5}}
+
+
+def bench_spheres(capt, torch, dev, stream, tree, c_host, r_host, steps, sms, parity_n, pts):
+    """One sphere-query workload on an uploaded tree: autotuned launch, device time with
+    L2 flushed before every call, work counts, roofline and an oracle parity sample."""
+    import oracle
+    m = len(c_host)
+    dc, dr = torch.from_numpy(c_host).to(dev), torch.from_numpy(r_host).to(dev)
+    fl = torch.empty(m, dtype=torch.uint8, device=dev)
+    cfg, _ = capt.capt_autotune_spheres(tree, dc, dr, fl)
+    st = capt.capt_stats(tree)
+    counts = None if st["full_dropped"] else capt.capt_count_sphere_work(tree, dc, dr).cpu().numpy()
+    flush = torch.zeros(64 << 20, dtype=torch.float32, device=dev)   # 256 MB > L2
+    for _ in range(3):
+        capt.capt_query_spheres(tree, dc, dr, fl)
+    ms = time_events_flushed(torch, lambda: capt.capt_query_spheres(tree, dc, dr, fl), steps, stream, flush)
+    del flush
+    got = fl.cpu().numpy()
+    k = min(parity_n, m)
+    ref = oracle.brute_flags(pts, c_host[:k], r_host[:k], threads=oracle.default_threads())
+    out = {"spheres": m, "ms": ms, "sphere_queries_per_s": m / (ms / 1e3), "launch_cfg": cfg,
+           "collision_fraction": float(got.mean()), "tree_device_bytes": int(st["device_bytes"]),
+           "l2": "flushed before every timed call", "parity_sample_equal": bool(np.array_equal(got[:k], ref)),
+           "parity_sample": f"first {k} spheres vs the oracle's FP32 brute force over all {len(pts)} points"}
+    if counts is not None:
+        ops, l1 = sphere_ops(counts, st["depth"], chunked=cfg["chunk"] != capt.CAPT_SCAN_SETS)
+        out["work"] = {"spheres": int(counts[0]), "near_cloud_box": int(counts[1]), "leaf_box_pass": int(counts[2]),
+                       "points_scanned_alg3": int(counts[3]), "chunk_boxes": int(counts[4]),
+                       "points_scanned_chunked": int(counts[5])}
+        out["roofline"] = roof(ms, m * 17, ops, l1, sms)
+    return out, got
+
+
+def bench_uniform(capt, torch, dev, stream, steps, sms):
+    """The small uniform workload: 2,000 points in the unit cube, 100,000 spheres."""
+    pu = W.uniform_cloud(2000, 1000)
+    cu, ru = W.cube_queries(100_000, 1000)
+    tu = capt.capt_build(pu, 0.01, 0.08)
+    capt.capt_upload(tu, dev.index)
+    out, _ = bench_spheres(capt, torch, dev, stream, tu, cu, ru, steps, sms, 100_000, pu)
+    out["roofline"]["note"] = ("one launch of ~10 us: launch and tail latency dominate; both floors are far "
+                               "below the measured time")
+    return out
+
+
+def bench_room(capt, torch, dev, stream, steps, sms):
+    """The large room cloud: 200,000 unfiltered points, 4,194,304 spheres, host build
+    timed, then the same queries on the compact (de-duplicated) sets."""
+    pr = W.room_cloud(1004)
+    t0 = time.perf_counter()
+    tr = capt.capt_build(pr, 0.02, 0.10)
+    build_ms = (time.perf_counter() - t0) * 1e3
+    st = capt.capt_stats(tr)
+    capt.capt_upload(tr, dev.index)
+    cr, rr = W.room_queries(1 << 22, 1004)
+    rep, f_rep = bench_spheres(capt, torch, dev, stream, tr, cr, rr, steps, sms, 8192, pr)
+    rep.update({"host_build_ms": build_ms, "host_build_threads": int(st["build_threads"]),
+                "total_afforded": int(st["total_afforded"]), "max_set": int(st["max_set"]),
+                "mean_set": st["total_afforded"] / st["n_leaves"]})
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    capt.capt_compact(tr, drop_full=True)
+    torch.cuda.synchronize(dev)
+    cms = (time.perf_counter() - t0) * 1e3
+    comp, f_comp = bench_spheres(capt, torch, dev, stream, tr, cr, rr, steps, sms, 8192, pr)
+    # the compact sets' scan has no work counter; the bytes floor is the same
+    comp["roofline"] = roof(comp["ms"], (1 << 22) * 17, 0, None, sms,
+                            note="HBM floor of the sphere inputs and flags only; the scan work is not counted "
+                                 "for the compact sets")
+    comp.update({"compact_ms": cms, "compact_entries": int(capt.capt_stats(tr)["compact_entries"]),
+                 "flags_equal_replicated": bool(np.array_equal(f_rep, f_comp))})
+    return {"replicated": rep, "compact": comp}
+
+
+def extra_workloads(capt, torch, dev, stream, pts, arm, args):
+    res = {}
     # depth frame -> tree, host and device (the paper's Table III setting: a 640 x 480
     # frame of 307,200 points, r_filter 1 / 1.5 / 2 cm, r_min 1.5 cm, r_max 8 cm)
     frame = W.depth_frame()
@@ -529,59 +689,18 @@ def extra_workloads(capt, torch, dev, stream, pts, arm, args):
                      "device_frame_to_tree_ms": frame_to_tree_ms(capt, df, rf, 0.015, 0.08),
                      "total_afforded": int(capt.capt_stats(tr_h)["total_afforded"])})
     res["depth_frame_to_tree"] = {"points": int(len(frame)), "rows": rows}
-    # uniform 2k cloud, 100,000 spheres
-    pu = W.uniform_cloud(2000, 1000)
-    cu, ru = W.cube_queries(100_000, 1000)
-    tu = capt.capt_build(pu, 0.01, 0.08)
-    capt.capt_upload(tu, dev.index)
-    dc, dr = torch.from_numpy(cu).to(dev), torch.from_numpy(ru).to(dev)
-    fl = torch.empty(100_000, dtype=torch.uint8, device=dev)
-    ucfg, _ = capt.capt_autotune_spheres(tu, dc, dr, fl)
-    ms = time_events(torch, lambda: capt.capt_query_spheres(tu, dc, dr, fl), 20, stream)
-    res["uniform2k"] = {"spheres": 100_000, "ms": ms, "sphere_queries_per_s": 1e5 / (ms / 1e3), "launch_cfg": ucfg}
-    # room: 200,000 points, 4,194,304 spheres
+    # room: filter at 2 cm (host and device), device build; the cloud relabelled along
+    # the Z-order curve (same point set, same flags)
     pr = W.room_cloud(1004)
     res["room_filter_2cm"] = {"points": len(pr), "host_ms": host_filter_ms(capt, pr, 0.02),
                               "device_ms": device_filter_ms(capt, pr, 0.02, reps=3)}
-    t0 = time.perf_counter()
-    tr = capt.capt_build(pr, 0.02, 0.10)
-    bms = (time.perf_counter() - t0) * 1e3
-    capt.capt_upload(tr, dev.index)
-    st = capt.capt_stats(tr)
-    cr, rr = W.room_queries(1 << 22, 1004)
-    dc, dr = torch.from_numpy(cr).to(dev), torch.from_numpy(rr).to(dev)
-    fl = torch.empty(1 << 22, dtype=torch.uint8, device=dev)
-    rcfg, _ = capt.capt_autotune_spheres(tr, dc, dr, fl)
-    ms = time_events(torch, lambda: capt.capt_query_spheres(tr, dc, dr, fl), 10, stream)
-    # the same cloud relabelled along the Z-order curve before the build (same point
-    # set, same flags): sets run along the curve and the chunked scan pays
+    res["room_device_build_ms"] = device_build_ms(capt, pr, 0.02, 0.10, reps=3)
     order = capt.capt_morton_order(pr)
     ts = capt.capt_build(pr[order], 0.02, 0.10)
     capt.capt_upload(ts, dev.index)
-    fl2 = torch.empty_like(fl)
-    scfg, _ = capt.capt_autotune_spheres(ts, dc, dr, fl2)
-    ms_sorted = time_events(torch, lambda: capt.capt_query_spheres(ts, dc, dr, fl2), 10, stream)
-    res["room200k_zorder"] = {"spheres": 1 << 22, "ms": ms_sorted,
-                              "sphere_queries_per_s": (1 << 22) / (ms_sorted / 1e3), "launch_cfg": scfg,
-                              "flags_equal_unsorted": bool(torch.equal(fl, fl2))}
-    res["room200k"] = {"spheres": 1 << 22, "ms": ms, "sphere_queries_per_s": (1 << 22) / (ms / 1e3),
-                       "build_ms": bms, "device_build_ms": device_build_ms(capt, pr, 0.02, 0.10, reps=3),
-                       "launch_cfg": rcfg, "tree_device_bytes": int(st["device_bytes"]),
-                       "total_afforded": int(st["total_afforded"]), "max_set": int(st["max_set"])}
-    # the compact (de-duplicated) sets of the same tree, replicated sets dropped
-    capt.capt_free(ts)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    capt.capt_compact(tr, drop_full=True)
-    cms = (time.perf_counter() - t0) * 1e3
-    sc = capt.capt_stats(tr)
-    fl3 = torch.empty_like(fl)
-    ccfg, _ = capt.capt_autotune_spheres(tr, dc, dr, fl3)
-    ms_c = time_events(torch, lambda: capt.capt_query_spheres(tr, dc, dr, fl3), 10, stream)
-    res["room200k_compact"] = {"spheres": 1 << 22, "ms": ms_c, "sphere_queries_per_s": (1 << 22) / (ms_c / 1e3),
-                               "compact_ms": cms, "launch_cfg": ccfg, "tree_device_bytes": int(sc["device_bytes"]),
-                               "compact_entries": int(sc["compact_entries"]),
-                               "flags_equal_replicated": bool(torch.equal(fl, fl3))}
+    cr, rr = W.room_queries(1 << 22, 1004)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    res["room200k_zorder"], _ = bench_spheres(capt, torch, dev, stream, ts, cr, rr, 10, sms, 4096, pr[order])
     return res
 
 

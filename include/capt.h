@@ -275,6 +275,12 @@ int capt_query_configs_host(capt_tree* t, const float* h_centers, const float* h
 int capt_count_config_work(const capt_tree* t, const float* d_centers, const float* d_radii, size_t C, int S,
                            uint64_t* d_counts, void* stream);
 
+/* capt_count_config_work for capt_query_spheres: m spheres with their own radii
+ * (d_radii device float[m]), each counted as a configuration of one sphere; the same six
+ * counters. */
+int capt_count_sphere_work(const capt_tree* t, const float* d_centers, const float* d_radii, size_t m,
+                           uint64_t* d_counts, void* stream);
+
 /* Leaf index i - (N - 1) reached by the descent of Alg. 3 for each centre.
  * d_centers device float[m][3]; d_leaves device uint32[m].  Diagnostics. */
 int capt_query_leaves(const capt_tree* t, const float* d_centers, size_t m, uint32_t* d_leaves, void* stream);
@@ -304,7 +310,16 @@ typedef struct capt_launch_cfg {
     int32_t chunk;             /* edges: configurations per work item (1..1024, rounded
                                   up to a multiple of 32).  Spheres and configurations:
                                   the affordance scan, CAPT_SCAN_* */
+    int32_t prefetch;          /* configurations: 0..CAPT_MAX_PREFETCH.  With k > 0 a warp
+                                  starting tile i asks the copy engine to bring tile
+                                  i + k x (warps in the grid) of the centres into L2
+                                  (cp.async.bulk.prefetch), the tile some warp takes about
+                                  k tile-times later, so the centre loads of the root box
+                                  test hit L2.  Clearance: the same per block, a
+                                  trajectory k x (resident blocks) ahead.  0 = none.  Other
+                                  kernels: must be 0. */
 } capt_launch_cfg;
+#define CAPT_MAX_PREFETCH 4
 
 /* Affordance scan of the sphere and configuration kernels (capt_launch_cfg.chunk). */
 enum { CAPT_SCAN_SETS = 0,     /* whole sets, as Alg. 3 */
@@ -449,6 +464,16 @@ int capt_clearance_fwd(const capt_tree* t, const float* d_centers, const float* 
  * h = max(0, r_s + margin - d), when h > 0, d < r_max and d > 0; else 0.
  * d_grad_cost device float[T] (g).  Other arguments as in the forward, whose d_dist and
  * d_argmin it reads.  Errors as capt_clearance_fwd. */
+/* Algorithmic work of capt_clearance_fwd on m = T x W x S sphere centres (d_centers
+ * device float[m][3]), counted sequentially per sphere, for roofline accounting:
+ * d_counts device uint64[5] receives += [spheres, spheres within r_max of the cloud's
+ * bounding box (these descend), spheres whose leaf box is within r_max (Alg. 3's box
+ * test at r_max), points of their sets (each scanned in full: the nearest point is
+ * wanted, Lemma 1 case 1), 4-point blocks of those sets].  The caller zeroes d_counts.
+ * Errors as capt_clearance_fwd. */
+int capt_count_clearance_work(const capt_tree* t, const float* d_centers, size_t m, uint64_t* d_counts,
+                              void* stream);
+
 int capt_clearance_bwd(const capt_tree* t, const float* d_centers, const float* d_radii, const float* d_dist,
                        const int32_t* d_argmin, const float* d_grad_cost, size_t T, int W, int S, float margin,
                        float* d_grad_centers, void* stream);

@@ -25,6 +25,7 @@ __all__ = [
     "capt_validate_edges_static", "CAPT_STATIC_MAX_EDGES", "capt_build_device", "capt_query_joint_configs",
     "capt_autotune_joint_configs", "CAPT_KERNEL_JOINTS", "sfc_filter_device", "capt_autotune_spheres",
     "capt_morton_order", "capt_build_frame_device", "capt_compact", "CAPT_SCAN_SETS", "CAPT_SCAN_CHUNKED",
+    "capt_count_sphere_work", "capt_count_clearance_work",
     "CAPT_SCAN_COMPACT", "STATUS", "CAPT_STAGE_GLOBAL", "CAPT_STAGE_SMEM", "CAPT_KERNEL_SPHERES", "CAPT_KERNEL_CONFIGS",
     "CAPT_KERNEL_EDGES", "CAPT_KERNEL_CLEARANCE", "CAPT_EDGES_PERSISTENT", "CAPT_EDGES_PER_EDGE",
     "EXPORTED_SYMBOLS",
@@ -47,6 +48,7 @@ EXPORTED_SYMBOLS = [
     "capt_edge_plan_info", "capt_edge_plan_free", "capt_clearance_fwd", "capt_clearance_bwd",
     "capt_validate_edges_static", "capt_build_device", "capt_query_joint_configs", "capt_autotune_joint_configs",
     "sfc_filter_device", "capt_autotune_spheres", "capt_morton_order", "capt_build_frame_device", "capt_compact",
+    "capt_count_sphere_work", "capt_count_clearance_work",
 ]
 CAPT_STATIC_MAX_EDGES = 65536
 
@@ -69,7 +71,7 @@ class _Stats(C.Structure):
 
 class _LaunchCfg(C.Structure):
     _fields_ = [("warps_per_block", C.c_int32), ("spheres_per_lane", C.c_int32), ("staging", C.c_int32),
-                ("chunk", C.c_int32)]
+                ("chunk", C.c_int32), ("prefetch", C.c_int32)]
 
 
 class _Arm(C.Structure):
@@ -109,6 +111,8 @@ def _load():
         "capt_query_configs": [P, P, P, SZ, I, P, P],
         "capt_query_configs_host": [P, P, P, SZ, I, P, P],
         "capt_count_config_work": [P, P, P, SZ, I, P, P],
+        "capt_count_sphere_work": [P, P, P, SZ, P, P],
+        "capt_count_clearance_work": [P, P, SZ, P, P],
         "capt_query_leaves": [P, P, SZ, P, P],
         "capt_device_status": [P, P],
         "capt_set_launch_cfg": [P, I, C.POINTER(_LaunchCfg)],
@@ -391,6 +395,34 @@ def capt_count_config_work(tree: CaptTree, centers, radii, stream=None):
     return counts
 
 
+def capt_count_sphere_work(tree: CaptTree, centers, radii, stream=None):
+    """The six work counters of capt_count_config_work for sphere queries [m, 3] with
+    radii [m]."""
+    import torch
+    if centers.dim() != 2 or centers.shape[1] != 3 or radii.shape != (centers.shape[0],):
+        raise ValueError("centers must be [m, 3] and radii [m]")
+    counts = torch.zeros(6, dtype=torch.int64, device=centers.device)
+    _check(_load().capt_count_sphere_work(tree.h, _dev(centers, torch.float32, "centers"),
+                                          _dev(radii, torch.float32, "radii"), centers.shape[0],
+                                          _dev(counts, torch.int64, "counts"), _stream(stream)),
+           "capt_count_sphere_work")
+    return counts
+
+
+def capt_count_clearance_work(tree: CaptTree, centers, stream=None):
+    """[spheres, near the cloud box, passing the leaf box, points scanned, blocks scanned]
+    of capt_clearance_fwd on centres [..., 3]."""
+    import torch
+    if centers.shape[-1] != 3:
+        raise ValueError("centers must end in a dimension of 3")
+    m = centers.numel() // 3
+    counts = torch.zeros(5, dtype=torch.int64, device=centers.device)
+    _check(_load().capt_count_clearance_work(tree.h, _dev(centers, torch.float32, "centers"), m,
+                                             _dev(counts, torch.int64, "counts"), _stream(stream)),
+           "capt_count_clearance_work")
+    return counts
+
+
 def capt_query_leaves(tree: CaptTree, centers, leaves=None, stream=None):
     import torch
     if centers.dim() != 2 or centers.shape[1] != 3:
@@ -410,8 +442,8 @@ def capt_device_status(tree: CaptTree, stream=None) -> int:
 
 
 def capt_set_launch_cfg(tree: CaptTree, kernel: int, warps_per_block: int, spheres_per_lane: int, staging: int,
-                        chunk: int = 0):
-    c = _LaunchCfg(warps_per_block, spheres_per_lane, staging, chunk)
+                        chunk: int = 0, prefetch: int = 0):
+    c = _LaunchCfg(warps_per_block, spheres_per_lane, staging, chunk, prefetch)
     _check(_load().capt_set_launch_cfg(tree.h, int(kernel), C.byref(c)), "capt_set_launch_cfg")
 
 
@@ -593,7 +625,7 @@ def capt_edge_plan_create(tree: CaptTree, arm, qa, qb, nsteps, valid, cfg=None, 
     a = arm if isinstance(arm, _Arm) else make_arm(arm)
     E = _edge_args(tree, a, qa, qb, nsteps, valid)
     c = None if cfg is None else C.byref(_LaunchCfg(cfg["warps_per_block"], cfg["spheres_per_lane"], cfg["staging"],
-                                                    cfg["chunk"]))
+                                                    cfg["chunk"], cfg.get("prefetch", 0)))
     h = C.c_void_p()
     _check(_load().capt_edge_plan_create(tree.h, C.byref(a), _dev(qa, torch.float32, "qa"),
                                          _dev(qb, torch.float32, "qb"), _dev(nsteps, torch.int32, "nsteps"), E,

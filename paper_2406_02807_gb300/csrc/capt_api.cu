@@ -55,6 +55,8 @@ struct DeviceGuard {
 bool valid_cfg(int kernel, const capt_launch_cfg& c) {
     if (c.warps_per_block < 1 || c.warps_per_block > 16) return false;
     if (c.staging != CAPT_STAGE_GLOBAL && c.staging != CAPT_STAGE_SMEM) return false;
+    if (c.prefetch < 0 || c.prefetch > CAPT_MAX_PREFETCH) return false;
+    if (c.prefetch != 0 && kernel != CAPT_KERNEL_CONFIGS && kernel != CAPT_KERNEL_CLEARANCE) return false;
     const int spl = c.spheres_per_lane;
     const bool scan_mode = c.chunk >= CAPT_SCAN_SETS && c.chunk <= CAPT_SCAN_COMPACT;
     if (kernel == CAPT_KERNEL_SPHERES) return (spl == 1 || spl == 2 || spl == 4 || spl == 8) && scan_mode;
@@ -819,7 +821,20 @@ int capt_count_config_work(const capt_tree* t, const float* d_centers, const flo
     if (C == 0) return CAPT_OK;
     if (!d_centers || !d_radii || !d_counts) return fail(CAPT_E_ARG, "NULL device pointer");
     std::string err;
-    rc = capt::launch_count_configs(t->args(), d_centers, d_radii, C, S, d_counts, static_cast<cudaStream_t>(stream), err);
+    rc = capt::launch_count_configs(t->args(), d_centers, d_radii, C, S, false, d_counts,
+                                    static_cast<cudaStream_t>(stream), err);
+    return rc ? fail(rc, err) : CAPT_OK;
+}
+
+int capt_count_sphere_work(const capt_tree* t, const float* d_centers, const float* d_radii, size_t m,
+                           uint64_t* d_counts, void* stream) {
+    int rc = check_full(t);
+    if (rc) return rc;
+    if (m == 0) return CAPT_OK;
+    if (!d_centers || !d_radii || !d_counts) return fail(CAPT_E_ARG, "NULL device pointer");
+    std::string err;
+    rc = capt::launch_count_configs(t->args(), d_centers, d_radii, m, 1, true, d_counts,
+                                    static_cast<cudaStream_t>(stream), err);
     return rc ? fail(rc, err) : CAPT_OK;
 }
 
@@ -912,7 +927,8 @@ int capt_autotune_configs(capt_tree* t, const float* d_centers, const float* d_r
     for (int warps : {4, 8, 16})
         for (int spl : {2, 4, 8, 16})
             for (int stage : {CAPT_STAGE_GLOBAL, CAPT_STAGE_SMEM})
-                for (int mode : scan_modes(t)) cands.push_back({warps, spl, stage, mode});
+                for (int mode : scan_modes(t))
+                    for (int pf : {0, 1, 2}) cands.push_back({warps, spl, stage, mode, pf});
     return autotune_query(t, CAPT_KERNEL_CONFIGS, cands, d_centers, d_radii, C, S, d_flags,
                           static_cast<cudaStream_t>(stream), best, best_ms);
 }
@@ -1195,6 +1211,18 @@ int capt_clearance_fwd(const capt_tree* t, const float* d_centers, const float* 
     std::string err;
     rc = capt::launch_clearance_fwd(t->args(), d_centers, d_radii, T, W, S, margin, d_cost, d_dist, d_argmin,
                                     t->cfg[CAPT_KERNEL_CLEARANCE], static_cast<cudaStream_t>(stream), err);
+    return rc ? fail(rc, err) : CAPT_OK;
+}
+
+int capt_count_clearance_work(const capt_tree* t, const float* d_centers, size_t m, uint64_t* d_counts,
+                              void* stream) {
+    int rc = check_full(t);
+    if (rc) return rc;
+    if (t->h.r_min != 0.f) return fail(CAPT_E_STATE, "clearance needs a tree built with r_min = 0 (no prune)");
+    if (m == 0) return CAPT_OK;
+    if (!d_centers || !d_counts) return fail(CAPT_E_ARG, "NULL device pointer");
+    std::string err;
+    rc = capt::launch_count_clearance(t->args(), d_centers, m, d_counts, static_cast<cudaStream_t>(stream), err);
     return rc ? fail(rc, err) : CAPT_OK;
 }
 

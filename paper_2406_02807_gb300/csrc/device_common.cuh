@@ -192,6 +192,16 @@ __device__ __forceinline__ const float* stage_splits(const DevArgs& t, void* sme
     return stage_to_smem(smem, t.T, bytes, bar, t.status) ? reinterpret_cast<const float*>(smem) : nullptr;
 }
 
+// L2 prefetch of [p, p + bytes) by the bulk copy engine (no registers or shared memory
+// held while it is in flight); the range is trimmed inward to 16-byte boundaries, as
+// the instruction requires, so it never reaches outside the buffer.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint64_t bytes) {
+    const uintptr_t a = (reinterpret_cast<uintptr_t>(p) + 15u) & ~uintptr_t(15);
+    const uintptr_t e = (reinterpret_cast<uintptr_t>(p) + bytes) & ~uintptr_t(15);
+    if (e > a)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(e - a)) : "memory");
+}
+
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
 // Order-preserving unsigned key of a float (-0 and +0 share one key, as they compare

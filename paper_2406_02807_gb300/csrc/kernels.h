@@ -19,7 +19,7 @@ int launch_query(const DevArgs& t, int mode, const float* centers, const float* 
                  std::string& err);
 
 // Sequential Alg. 3 work counters for configuration queries.
-int launch_count_configs(const DevArgs& t, const float* centers, const float* radii, uint64_t C, int S,
+int launch_count_configs(const DevArgs& t, const float* centers, const float* radii, uint64_t C, int S, bool per_sphere,
                          uint64_t* counts, cudaStream_t st, std::string& err);
 
 // Boxes of the chunks of kChunkBlocks blocks (cbox: 8 floats per chunk, chunk_count).
@@ -29,6 +29,8 @@ int launch_leaves(const DevArgs& t, const float* centers, uint64_t m, uint32_t* 
                   std::string& err);
 
 // Clearance forward / backward.
+int launch_count_clearance(const DevArgs& t, const float* centers, uint64_t m, uint64_t* counts, cudaStream_t st,
+                           std::string& err);
 int launch_clearance_fwd(const DevArgs& t, const float* centers, const float* radii, uint64_t T, int W, int S,
                          float margin, float* cost, float* dist, int32_t* argmin, const capt_launch_cfg& cfg,
                          cudaStream_t st, std::string& err);

@@ -34,14 +34,27 @@ constexpr int kClearQueue = 160;
 struct ClearScratch {
     float4 nq[kClearQueue];          // queued spheres: centre
     unsigned long long ni[kClearQueue];   // their global sphere index
+    // the round's entries (spheres whose leaf box is within r_max): centre, first block
+    // and block count of the set
+    float4 ec[32];
+    uint32_t eb0[32];
+    uint32_t enb[32];
 };
 
+// Blocks of one set scanned per lane per step: a set of up to 32 x kClearV blocks
+// (the common case) takes one step, all its loads in flight together.
+constexpr int kClearV = 3;
+
 // One round over the first n queued spheres of the trajectory at `tbase` (sphere index
-// offset of the trajectory in dist / argmin).  Spheres passing the leaf box test are
-// scanned one at a time by the whole warp: lanes stride over the set's 4-point blocks
-// (two blocks in flight per lane) keeping a running minimum of (d^2, slot) keys, and two
-// 32-bit warp reductions per set (d^2, then the slot) give the smallest key.  The lowest key is the smallest FP32 squared
-// distance, ties going to the lowest slot, i.e. the lowest point index.
+// offset of the trajectory in dist / argmin).  Each lane descends for its sphere and
+// applies the leaf box test against r_max; spheres that fail get d = r_max at once, the
+// others become entries.  Each entry's set is then scanned by the whole warp (lane l on
+// blocks l, l + 32, l + 64 per step) keeping a running minimum of (d^2, slot) keys, and
+// two 32-bit warp reductions (d^2, then the slot) give the smallest key, which lane e
+// keeps for entry e.  The lowest key is the smallest FP32 squared distance, ties going
+// to the lowest slot, i.e. the lowest point index.  Once every entry is scanned, lane e
+// turns entry e's key into its distance and point index (the index loads of all entries
+// in flight together) and writes them.
 __device__ __forceinline__ void clearance_round(const DevArgs& t, const float* Ts, ClearScratch* ws, uint32_t n,
                                                 uint64_t tbase, float rmax, float rmax2, float* __restrict__ dist,
                                                 int32_t* __restrict__ argmin, uint32_t lane, uint32_t lt_mask) {
@@ -67,66 +80,90 @@ __device__ __forceinline__ void clearance_round(const DevArgs& t, const float* T
             argmin[tbase + gi] = -1;
         }
     }
-    uint32_t mask = __ballot_sync(0xffffffffu, act);
-    while (mask) {
-        const int src = __ffs(mask) - 1;
-        mask &= mask - 1;
-        const float cx = __shfl_sync(0xffffffffu, c.x, src);
-        const float cy = __shfl_sync(0xffffffffu, c.y, src);
-        const float cz = __shfl_sync(0xffffffffu, c.z, src);
-        const uint32_t b0 = __shfl_sync(0xffffffffu, fb, src);
-        const uint32_t nbs = __shfl_sync(0xffffffffu, nb, src);
-        const uint64_t cxx = f2_dup(cx), cyy = f2_dup(cy), czz = f2_dup(cz);
+    const uint32_t mask = __ballot_sync(0xffffffffu, act);
+    if (mask == 0) return;
+    const uint32_t n_ent = __popc(mask);
+    // entries in lane order; lane e later finishes entry e, so it takes that entry's
+    // output index now
+    const uint32_t pos = __popc(mask & lt_mask);
+    __syncwarp();
+    if (act) {
+        ws->ec[pos] = c;
+        ws->eb0[pos] = fb;
+        ws->enb[pos] = nb;
+    }
+    uint32_t src_lane = 0;
+    {
+        // lane e < n_ent: the lane holding entry e is the e-th set bit of mask
+        uint32_t mm = mask;
+        for (uint32_t k = 0; k < lane && mm; k++) mm &= mm - 1;
+        src_lane = mm ? (uint32_t)(__ffs(mm) - 1) : 0u;
+    }
+    const uint64_t my_gi = __shfl_sync(0xffffffffu, gi, src_lane);
+    __syncwarp();
+    unsigned long long mine = ~0ull;   // lane e: smallest key of entry e
+    for (uint32_t e = 0; e < n_ent; e++) {
+        const float4 ce = ws->ec[e];
+        const uint32_t b0 = ws->eb0[e];
+        const uint32_t nbs = ws->enb[e];
+        const uint64_t cxx = f2_dup(ce.x), cyy = f2_dup(ce.y), czz = f2_dup(ce.z);
         unsigned long long best = ~0ull;
-        auto fold = [&](uint32_t r) {
-            uint64_t s01, s23;
-            block_d2(blocks, t.plane, (int64_t)b0 + r, cxx, cyy, czz, s01, s23);
-            const float2 d01 = f2_split(s01), d23 = f2_split(s23);
-            float bd = d01.x;
-            uint32_t bq = 0;
-            if (d01.y < bd) { bd = d01.y; bq = 1; }
-            if (d23.x < bd) { bd = d23.x; bq = 2; }
-            if (d23.y < bd) { bd = d23.y; bq = 3; }
-            const unsigned long long key = ((unsigned long long)__float_as_uint(bd) << 32) | (4u * r + bq);
-            best = key < best ? key : best;
-        };
-        uint32_t r = lane;
-        for (; r + 32 < nbs; r += 64) {
-            fold(r);
-            fold(r + 32);
+        for (uint32_t r = lane; r < nbs; r += 32 * kClearV) {
+            uint64_t s01[kClearV], s23[kClearV];
+#pragma unroll
+            for (int v = 0; v < kClearV; v++) {
+                s01[v] = s23[v] = ~0ull;
+                if (r + 32u * v < nbs) block_d2(blocks, t.plane, (int64_t)b0 + r + 32u * v, cxx, cyy, czz, s01[v], s23[v]);
+            }
+#pragma unroll
+            for (int v = 0; v < kClearV; v++) {
+                if (r + 32u * v < nbs) {
+                    const float2 d01 = f2_split(s01[v]), d23 = f2_split(s23[v]);
+                    float bd = d01.x;
+                    uint32_t bq = 0;
+                    if (d01.y < bd) { bd = d01.y; bq = 1; }
+                    if (d23.x < bd) { bd = d23.x; bq = 2; }
+                    if (d23.y < bd) { bd = d23.y; bq = 3; }
+                    const unsigned long long key =
+                        ((unsigned long long)__float_as_uint(bd) << 32) | (4u * (r + 32u * v) + bq);
+                    best = key < best ? key : best;
+                }
+            }
         }
-        if (r < nbs) fold(r);
         // minimum key over the warp in two 32-bit reductions: the smallest d^2 (the bits
         // of a non-negative float order as unsigned integers), then the smallest slot
         // among the lanes that hold it
-        {
-            const uint32_t hi = (uint32_t)(best >> 32);
-            const uint32_t mhi = __reduce_min_sync(0xffffffffu, hi);
-            const uint32_t mlo = __reduce_min_sync(0xffffffffu, hi == mhi ? (uint32_t)best : 0xffffffffu);
-            best = ((unsigned long long)mhi << 32) | mlo;
-        }
-        if (lane == (uint32_t)src) {
-            const float dd = __fsqrt_rn(__uint_as_float((uint32_t)(best >> 32)));
-            const uint64_t i = tbase + gi;
-            if (dd < rmax) {
-                dist[i] = dd;
-                argmin[i] = (int32_t)__ldg(t.ids + 4 * (size_t)b0 + (uint32_t)(best & 0xffffffffu));
-            } else {
-                dist[i] = rmax;
-                argmin[i] = -1;
-            }
+        const uint32_t hi = (uint32_t)(best >> 32);
+        const uint32_t mhi = __reduce_min_sync(0xffffffffu, hi);
+        const uint32_t mlo = __reduce_min_sync(0xffffffffu, hi == mhi ? (uint32_t)best : 0xffffffffu);
+        if (lane == e) mine = ((unsigned long long)mhi << 32) | mlo;
+    }
+    if (lane < n_ent) {
+        const float dd = __fsqrt_rn(__uint_as_float((uint32_t)(mine >> 32)));
+        const uint64_t i = tbase + my_gi;
+        if (dd < rmax) {
+            dist[i] = dd;
+            argmin[i] = (int32_t)__ldg(t.ids + 4 * (size_t)ws->eb0[lane] + (uint32_t)(mine & 0xffffffffu));
+        } else {
+            dist[i] = rmax;
+            argmin[i] = -1;
         }
     }
-    (void)lt_mask;
     __syncwarp();
 }
 
 template <bool STAGE>
 __global__ void __launch_bounds__(512, 2) k_clearance_dist(DevArgs t, const float* __restrict__ centers, int W,
                                                            int S, float* __restrict__ dist,
-                                                           int32_t* __restrict__ argmin) {
+                                                           int32_t* __restrict__ argmin, uint32_t pf_blocks) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t bar;
+    // blocks start in about index order as earlier ones finish, so trajectory
+    // blockIdx.x + pf_blocks is one that starts a few block-lifetimes from now: its
+    // centres are fetched into L2 meanwhile
+    if (pf_blocks && threadIdx.x == 0 && (uint64_t)blockIdx.x + pf_blocks < gridDim.x)
+        prefetch_l2(centers + 3 * ((uint64_t)blockIdx.x + pf_blocks) * (uint64_t)W * (uint64_t)S,
+                    (uint64_t)W * (uint64_t)S * 12u);
     const float* Ts = nullptr;
     uint32_t off = 0;
     if constexpr (STAGE) {
@@ -283,6 +320,62 @@ __global__ void k_clearance_bwd(DevArgs t, const float* __restrict__ centers, co
     }
 }
 
+// Sequential work count of the clearance forward, one thread per sphere, in the order
+// the kernel's method defines it: every sphere gets the box test against the cloud's
+// bounding box at r_max; a sphere within r_max of it descends and gets the leaf box
+// test at r_max; a sphere passing that scans its whole set (no early exit: the
+// nearest point is wanted).  counts += [spheres, spheres near the cloud box, spheres
+// passing the leaf box, points scanned, blocks scanned (4 slots each)].
+__global__ void k_count_clearance(DevArgs t, const float* __restrict__ centers, uint64_t m,
+                                  unsigned long long* counts) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long nsph = 0, nnear = 0, npass = 0, npts = 0, nblk = 0;
+    const float rmax2 = __fmul_rn(t.r_max, t.r_max);
+    const float4 rlo = make_float4(t.lo[0], t.lo[1], t.lo[2], 0.f);
+    const float4 rhi = make_float4(t.hi[0], t.hi[1], t.hi[2], 0.f);
+    if (i < m) {
+        const float x = centers[3 * i], y = centers[3 * i + 1], z = centers[3 * i + 2];
+        nsph = 1;
+        if (box_dist2(x, y, z, rlo, rhi) <= rmax2) {
+            nnear = 1;
+            const uint32_t leaf = descend(x, y, z, t, nullptr);
+            float4 a, b;
+            load_leaf(t.leaves, leaf, a, b);
+            const uint32_t cnt = __float_as_uint(b.w);
+            if (cnt > 0 && box_dist2(x, y, z, a, b) <= rmax2) {
+                npass = 1;
+                npts = cnt;
+                nblk = (cnt + 3u) / 4u;
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        nsph += __shfl_xor_sync(0xffffffffu, nsph, o);
+        nnear += __shfl_xor_sync(0xffffffffu, nnear, o);
+        npass += __shfl_xor_sync(0xffffffffu, npass, o);
+        npts += __shfl_xor_sync(0xffffffffu, npts, o);
+        nblk += __shfl_xor_sync(0xffffffffu, nblk, o);
+    }
+    if ((threadIdx.x & 31) == 0 && nsph) {
+        atomicAdd(counts, nsph);
+        atomicAdd(counts + 1, nnear);
+        atomicAdd(counts + 2, npass);
+        atomicAdd(counts + 3, npts);
+        atomicAdd(counts + 4, nblk);
+    }
+}
+
+int launch_count_clearance(const DevArgs& t, const float* centers, uint64_t m, uint64_t* counts, cudaStream_t st,
+                           std::string& err) {
+    if (m == 0) return CAPT_OK;
+    const unsigned threads = 256;
+    k_count_clearance<<<(unsigned)((m + threads - 1) / threads), threads, 0, st>>>(
+        t, centers, m, reinterpret_cast<unsigned long long*>(counts));
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) { err = std::string("clearance count launch: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
+    return CAPT_OK;
+}
+
 int launch_clearance_fwd(const DevArgs& t, const float* centers, const float* radii, uint64_t T, int W, int S,
                          float margin, float* cost, float* dist, int32_t* argmin, const capt_launch_cfg& cfg,
                          cudaStream_t st, std::string& err) {
@@ -295,7 +388,13 @@ int launch_clearance_fwd(const DevArgs& t, const float* centers, const float* ra
     const size_t smem = (stage ? stage_offset(t) : 0u) + sizeof(ClearScratch) * (size_t)warps;
     cudaError_t ce = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (ce != cudaSuccess) { err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
-    fn<<<(unsigned)T, warps * 32, smem, st>>>(t, centers, W, S, dist, argmin);
+    uint32_t pf_blocks = 0;
+    if (cfg.prefetch > 0) {
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)fn, warps * 32, smem);
+        pf_blocks = (uint32_t)std::max(1, occ) * (uint32_t)sm_count() * (uint32_t)cfg.prefetch;
+    }
+    fn<<<(unsigned)T, warps * 32, smem, st>>>(t, centers, W, S, dist, argmin, pf_blocks);
     const uint64_t cost_blocks = std::min<uint64_t>((T + 7) / 8, (uint64_t)sm_count() * 16);
     k_clearance_cost<<<(unsigned)cost_blocks, 256, 0, st>>>(radii, dist, T, W, S, margin, cost);
     ce = cudaGetLastError();

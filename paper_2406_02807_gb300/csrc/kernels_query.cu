@@ -246,7 +246,8 @@ struct CfgScratch {
 template <int CPT, bool STAGE, int MODE>
 __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs(DevArgs t, const float* __restrict__ centers,
                                                                  const float* __restrict__ radii, uint64_t C, int S,
-                                                                 uint8_t* __restrict__ out, unsigned long long* ctr) {
+                                                                 uint8_t* __restrict__ out, unsigned long long* ctr,
+                                                                 uint32_t pf) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t bar;
     __shared__ float r2s[64];
@@ -276,11 +277,19 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs(DevArgs t, cons
         sphere_round<false, MODE>(t, Ts, &ws->re, ws->ghit, c, g, live, lane, lt_mask);
     };
 
+    // tiles are taken in increasing order across the grid (from the counter, or w, w +
+    // warps, ... without one), so tile + pf x warps is the one some warp starts about pf
+    // tile-times from now: its centres are fetched into L2 meanwhile
+    const uint64_t pf_tiles = (uint64_t)pf * nwarps;
     const TileSched sched{ctr, nwarps};
     for (uint64_t tile = sched.first((uint64_t)blockIdx.x * (blockDim.x >> 5) + warp); tile < n_tiles;
          tile = sched.next(tile)) {
         const uint64_t first = tile * CPT;
         const uint32_t ncfg = (uint32_t)min((uint64_t)CPT, C - first);
+        if (pf_tiles && lane == 0 && tile + pf_tiles < n_tiles) {
+            const uint64_t pfirst = (tile + pf_tiles) * CPT;
+            prefetch_l2(centers + 3 * pfirst * (uint64_t)S, min((uint64_t)CPT, C - pfirst) * (uint64_t)S * 12u);
+        }
         const uint32_t nsph = ncfg * (uint32_t)S;
         const float* base = centers + 3 * first * (uint64_t)S;
         const bool vec = (reinterpret_cast<uintptr_t>(base) & 15u) == 0;
@@ -371,8 +380,11 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs(DevArgs t, cons
 // points scanned (Alg. 3 alone), chunk boxes tested, points scanned in the chunks whose
 // box the sphere reaches (up to the first hit)].  The first four are the plain method's
 // work; the query kernels do the first three, then the last two instead of the fourth.
+// With per_sphere, radii holds one radius per sphere (C x S of them) instead of one per
+// sphere slot of a configuration (S); sphere queries are counted as configurations of
+// one sphere with their own radii.
 __global__ void k_count_configs(DevArgs t, const float* __restrict__ centers, const float* __restrict__ radii,
-                                uint64_t C, int S, unsigned long long* counts) {
+                                uint64_t C, int S, bool per_sphere, unsigned long long* counts) {
     const uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long nsph = 0, nnear = 0, npass = 0, npts = 0, nbox = 0, ncpts = 0;
     const float4* cbox = reinterpret_cast<const float4*>(t.cbox);
@@ -381,7 +393,7 @@ __global__ void k_count_configs(DevArgs t, const float* __restrict__ centers, co
     if (c < C) {
         for (int s = 0; s < S; s++) {
             const float* x = centers + 3 * (c * (uint64_t)S + s);
-            const float r = radii[s], r2 = __fmul_rn(r, r);
+            const float r = radii[per_sphere ? c * (uint64_t)S + s : (uint64_t)s], r2 = __fmul_rn(r, r);
             nsph++;
             if (!(box_dist2(x[0], x[1], x[2], rlo, rhi) <= r2)) continue;
             nnear++;
@@ -532,7 +544,8 @@ int occupancy(const void* fn, int threads, size_t smem) {
 
 }  // namespace
 
-using ConfigKernel = void (*)(DevArgs, const float*, const float*, uint64_t, int, uint8_t*, unsigned long long*);
+using ConfigKernel = void (*)(DevArgs, const float*, const float*, uint64_t, int, uint8_t*, unsigned long long*,
+                              uint32_t);
 
 template <int CPT, bool STAGE>
 ConfigKernel pick_configs_mode(int mode) {
@@ -568,7 +581,8 @@ int launch_configs(const DevArgs& t, const float* centers, const float* radii, u
     const uint64_t tiles = (C + cpt - 1) / cpt;
     const uint64_t need = (tiles + warps - 1) / warps;
     const uint64_t blocks = std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)sm_count() * occ, need));
-    fn<<<(unsigned)blocks, warps * 32, smem, st>>>(t, centers, radii, C, S, out, ctr);
+    const uint32_t pf = (uint32_t)std::max(0, std::min(CAPT_MAX_PREFETCH, (int)cfg.prefetch));
+    fn<<<(unsigned)blocks, warps * 32, smem, st>>>(t, centers, radii, C, S, out, ctr, pf);
     ce = cudaGetLastError();
     if (ce != cudaSuccess) { err = std::string("configuration launch: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
     return CAPT_OK;
@@ -599,11 +613,11 @@ int launch_query(const DevArgs& t, int mode, const float* centers, const float* 
 }
 
 int launch_count_configs(const DevArgs& t, const float* centers, const float* radii, uint64_t C, int S,
-                         uint64_t* counts, cudaStream_t st, std::string& err) {
+                         bool per_sphere, uint64_t* counts, cudaStream_t st, std::string& err) {
     if (C == 0) return CAPT_OK;
     const unsigned threads = 256;
     k_count_configs<<<(unsigned)((C + threads - 1) / threads), threads, 0, st>>>(
-        t, centers, radii, C, S, reinterpret_cast<unsigned long long*>(counts));
+        t, centers, radii, C, S, per_sphere, reinterpret_cast<unsigned long long*>(counts));
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) { err = std::string("count launch: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
     return CAPT_OK;

@@ -199,6 +199,48 @@ def test_work_counters_match_oracle(tabletop, capt_lib, torch_):
     assert g[1] <= near.sum() and g[1] >= near[flags == 0].sum()
 
 
+def test_sphere_work_counters_match_oracle(uniform2k, orc, capt_lib, torch_):
+    """Per-sphere counts (each sphere its own radius) against the oracle's plain Alg. 3:
+    every sphere examined, a sphere passing its leaf box scans at least one point, and
+    the points scanned up to the first hit add up."""
+    ot = orc.PlainCAPT(uniform2k["pts"], 0.01, 0.08)
+    f, _, ms = ot.query(uniform2k["c"], uniform2k["r"])
+    g = capt_lib.capt_count_sphere_work(uniform2k["tree"], uniform2k["dc"], uniform2k["dr"]).cpu().numpy()
+    assert g[0] == len(ms)
+    assert g[2] == int((ms > 0).sum())
+    assert g[3] == int(ms.sum())
+    assert g[5] <= g[3] and g[4] >= g[2]
+    assert capt_lib.capt_device_status(uniform2k["tree"]) == 0
+
+
+def test_clearance_work_counters_match_oracle_tree(tabletop, orc, capt_lib, torch_):
+    """Clearance work (full-set scans within r_max) counted from the oracle's own tree:
+    its leaves (Alg. 3 descent), its leaf boxes and set sizes, the FP32 box expression."""
+    arm = tabletop["arm"]
+    q = W.random_trajectories(64, 8, 1011)
+    c = W.fk_centers(arm, q.reshape(-1, 7)).reshape(-1, 3)
+    pts = tabletop["pts"]
+    ot = orc.PlainCAPT(pts, 0.0, 0.08)
+    _, leaf, _ = ot.query(c, np.full(len(c), 0.08, np.float32))
+    ex = ot.export()
+    cnt = np.diff(ex["set_begin"].astype(np.int64))
+    aabb = ex["aabb"].reshape(-1, 6)
+
+    def box_d2(x, lo, hi):
+        g = (x - np.minimum(np.maximum(x, lo), hi)).astype(np.float32)
+        q2 = g * g
+        return (q2[:, 0] + q2[:, 1]) + q2[:, 2]
+
+    r2 = np.float32(0.08) * np.float32(0.08)
+    near = box_d2(c, pts.min(0), pts.max(0)) <= r2
+    lb = aabb[leaf]
+    ok = near & (cnt[leaf] > 0) & (box_d2(c, lb[:, :3], lb[:, 3:]) <= r2)
+    want = [len(c), int(near.sum()), int(ok.sum()), int(cnt[leaf][ok].sum()), int(((cnt[leaf][ok] + 3) // 4).sum())]
+    g = capt_lib.capt_count_clearance_work(tabletop["ctree"], _cuda(torch_, c)).cpu().numpy()
+    assert g.tolist() == want
+    assert want[2] > 0
+
+
 def _chunk_model_counts(ex, pts, cen, r, L):
     """Chunked-scan work counted sequentially in FP32 from the oracle's tree: the block
     layout (each set from a 4-point block boundary, sets in leaf order), boxes of chunks
