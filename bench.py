@@ -45,6 +45,7 @@ SM_MAX_MHZ = 2070.0
 TRAFFIC = {"17cca476bcfba7d6": 778620416 + 4390656}   # profiles/k_configs_tabletop_1M.md
 HBM_FALLBACK_GBS = 6800.0   # used only when MEASURED_PEAKS.json is absent
 PARITY_SAMPLE = 32768       # configurations of the timed run checked against the oracle
+GRID_CELLS = 1 << 24        # cells of the distance-bound grid of the tabletop tree (32 MB)
 
 
 def hbm_peak():
@@ -333,6 +334,15 @@ def main():
     r = r_host.to(dev)
     flags = torch.empty(C, dtype=torch.uint8, device=dev)
 
+    # the distance-bound grid (one-time per tree, like the upload): spheres that reach the
+    # cloud's box are decided by their cell where it can tell, the rest descend
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    capt.capt_build_grid(tree, GRID_CELLS)
+    grid_ms = (time.perf_counter() - t0) * 1e3
+    gst = capt.capt_stats(tree)
+    host["grid_build_ms"] = round(grid_ms, 3)
+    host["grid"] = {"dims": gst["grid_dims"], "cell_m": gst["grid_cell"], "bytes": 2 * int(np.prod(gst["grid_dims"]))}
     tuned, tuned_ms = capt.capt_autotune_configs(tree, cen, r, flags)
     counts = capt.capt_count_config_work(tree, cen, r).cpu().numpy().astype(np.int64)
     L = capt.capt_stats(tree)["depth"]

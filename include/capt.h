@@ -80,6 +80,8 @@ typedef struct capt_tree_stats {
     uint64_t scratch_bytes;   /* device scratch the tree allocated on demand (edge work items
                                  of capt_validate_edges, buffers of capt_query_configs_host);
                                  not part of device_bytes */
+    uint32_t grid_dims[3];    /* cells per axis of the distance-bound grid (0: none) */
+    float grid_cell;          /* its cell side (0: none) */
 } capt_tree_stats;
 
 /* ---------------------------------------------------------------------------------
@@ -181,6 +183,42 @@ const char* capt_last_error(void);
  * Calling it again re-uploads (and releases any compact form of capt_compact).
  * Errors: CAPT_E_ARG, CAPT_E_CUDA, CAPT_E_NOMEM. */
 int capt_upload(capt_tree* t, int device, void* stream);
+
+/* Distance-bound grid (this library's addition; the paper has no counterpart): a
+ * uniform grid of cubic cells over the cloud's bounding box grown by r_max, at most
+ * max_cells cells (0: 2^22), two bytes per cell: a lower and an upper bound of the
+ * distance from the cell to the cloud, computed on the device through the tree's own
+ * sets (for a point m of each cell, the nearest point of m's leaf set is the nearest
+ * cloud point whenever it is within r_max, Lemma 1) and rounded toward the safe side.
+ * Configuration queries launched with capt_launch_cfg.grid = 1 classify every sphere
+ * that reaches the cloud's bounding box by its cell before any descent: a sphere whose
+ * cell is farther than r from the cloud cannot hit, one whose cell is within r of it
+ * certainly hits (its configuration is decided at once), only the rest descend.  Both
+ * decisions reproduce the FP32 test exactly (the margins are derived in dist_grid.cu),
+ * so the flags do not change.  Needs the replicated sets (before capt_compact drops
+ * them); a grid built earlier stays valid after the drop.  Rebuilding replaces the old
+ * grid; do not call it while queries of this tree run on other streams.  Synchronises
+ * `stream`.  Errors: CAPT_E_ARG (max_cells > 2^28), CAPT_E_STATE, CAPT_E_NOMEM,
+ * CAPT_E_CUDA. */
+int capt_build_grid(capt_tree* t, uint64_t max_cells, void* stream);
+
+/* The distance-bound grid, for tests and inspection.  *info receives its shape (all
+ * zero when the tree has none); when h_cells is not NULL it receives the 2 x cells
+ * bytes (host buffer, caller-owned): cell (i, j, k) = [origin + (i, j, k) cell,
+ * origin + (i + 1, j + 1, k + 1) cell] at index (k dims[1] + j) dims[0] + i holds
+ * {lower bound, upper bound} of the distance from the cell (grown by cell / 100 on every
+ * side) to the cloud, in units of `unit` (upper bound 255: none).  The kernels locate a
+ * centre x by floor(fl(fl(x - origin) * inv_cell)) clamped to the grid.  Synchronous.
+ * Errors: CAPT_E_ARG, CAPT_E_CUDA. */
+typedef struct capt_grid_info {
+    float origin[3];
+    float cell;
+    float inv_cell;
+    float unit;
+    int32_t dims[3];
+    uint32_t cells;
+} capt_grid_info;
+int capt_grid_export(const capt_tree* t, capt_grid_info* info, uint8_t* h_cells);
 
 /* De-duplicated ("compact") affordance sets: Alg. 1 copies a point into the set of
  * every leaf cell that affords it, so the sets replicate the cloud many times over
@@ -318,6 +356,13 @@ typedef struct capt_launch_cfg {
                                   test hit L2.  Clearance: the same per block, a
                                   trajectory k x (resident blocks) ahead.  0 = none.  Other
                                   kernels: must be 0. */
+    int32_t grid;              /* configurations and spheres: 1 = test each sphere that reaches the
+                                  cloud's bounding box against the tree's distance-bound
+                                  grid (staged in shared memory) before it is queued for a
+                                  descent; exact (a cell stores a rounded-down lower bound
+                                  of the distance from the cell to the cloud), it only
+                                  removes spheres that cannot hit.  0 = descend for every
+                                  such sphere.  Other kernels: must be 0. */
 } capt_launch_cfg;
 #define CAPT_MAX_PREFETCH 4
 

@@ -25,7 +25,7 @@ __all__ = [
     "capt_validate_edges_static", "CAPT_STATIC_MAX_EDGES", "capt_build_device", "capt_query_joint_configs",
     "capt_autotune_joint_configs", "CAPT_KERNEL_JOINTS", "sfc_filter_device", "capt_autotune_spheres",
     "capt_morton_order", "capt_build_frame_device", "capt_compact", "CAPT_SCAN_SETS", "CAPT_SCAN_CHUNKED",
-    "capt_count_sphere_work", "capt_count_clearance_work",
+    "capt_count_sphere_work", "capt_count_clearance_work", "capt_build_grid", "capt_grid_export",
     "CAPT_SCAN_COMPACT", "STATUS", "CAPT_STAGE_GLOBAL", "CAPT_STAGE_SMEM", "CAPT_KERNEL_SPHERES", "CAPT_KERNEL_CONFIGS",
     "CAPT_KERNEL_EDGES", "CAPT_KERNEL_CLEARANCE", "CAPT_EDGES_PERSISTENT", "CAPT_EDGES_PER_EDGE",
     "EXPORTED_SYMBOLS",
@@ -48,7 +48,7 @@ EXPORTED_SYMBOLS = [
     "capt_edge_plan_info", "capt_edge_plan_free", "capt_clearance_fwd", "capt_clearance_bwd",
     "capt_validate_edges_static", "capt_build_device", "capt_query_joint_configs", "capt_autotune_joint_configs",
     "sfc_filter_device", "capt_autotune_spheres", "capt_morton_order", "capt_build_frame_device", "capt_compact",
-    "capt_count_sphere_work", "capt_count_clearance_work",
+    "capt_count_sphere_work", "capt_count_clearance_work", "capt_build_grid", "capt_grid_export",
 ]
 CAPT_STATIC_MAX_EDGES = 65536
 
@@ -66,12 +66,12 @@ class _Stats(C.Structure):
                 ("build_ms", C.c_double), ("r_min", C.c_float), ("r_max", C.c_float), ("device", C.c_int32),
                 ("build_threads", C.c_int32), ("compact_chunks", C.c_uint64), ("compact_entries", C.c_uint64),
                 ("compact_bytes", C.c_uint64), ("full_dropped", C.c_int32), ("reserved", C.c_int32),
-                ("scratch_bytes", C.c_uint64)]
+                ("scratch_bytes", C.c_uint64), ("grid_dims", C.c_uint32 * 3), ("grid_cell", C.c_float)]
 
 
 class _LaunchCfg(C.Structure):
     _fields_ = [("warps_per_block", C.c_int32), ("spheres_per_lane", C.c_int32), ("staging", C.c_int32),
-                ("chunk", C.c_int32), ("prefetch", C.c_int32)]
+                ("chunk", C.c_int32), ("prefetch", C.c_int32), ("grid", C.c_int32)]
 
 
 class _Arm(C.Structure):
@@ -79,6 +79,11 @@ class _Arm(C.Structure):
                 ("axis", C.c_int32 * MAX_JOINTS), ("link", (C.c_float * 3) * MAX_JOINTS),
                 ("sphere_link", C.c_int32 * MAX_SPHERES), ("sphere_offset", (C.c_float * 3) * MAX_SPHERES),
                 ("sphere_radius", C.c_float * MAX_SPHERES)]
+
+
+class _GridInfo(C.Structure):
+    _fields_ = [("origin", C.c_float * 3), ("cell", C.c_float), ("inv_cell", C.c_float), ("unit", C.c_float),
+                ("dims", C.c_int32 * 3), ("cells", C.c_uint32)]
 
 
 _lib = None
@@ -113,6 +118,8 @@ def _load():
         "capt_count_config_work": [P, P, P, SZ, I, P, P],
         "capt_count_sphere_work": [P, P, P, SZ, P, P],
         "capt_count_clearance_work": [P, P, SZ, P, P],
+        "capt_build_grid": [P, C.c_uint64, P],
+        "capt_grid_export": [P, C.POINTER(_GridInfo), P],
         "capt_query_leaves": [P, P, SZ, P, P],
         "capt_device_status": [P, P],
         "capt_set_launch_cfg": [P, I, C.POINTER(_LaunchCfg)],
@@ -261,7 +268,7 @@ def sfc_filter_device(points, min_spacing: float, stream=None):
 def capt_stats(tree: CaptTree) -> dict:
     s = _Stats()
     _check(_load().capt_stats(tree.h, C.byref(s)), "capt_stats")
-    return {k: getattr(s, k) for k, _ in _Stats._fields_}
+    return {k: (list(getattr(s, k)) if k == "grid_dims" else getattr(s, k)) for k, _ in _Stats._fields_}
 
 
 def capt_export(tree: CaptTree) -> dict:
@@ -316,6 +323,27 @@ def capt_build_frame_device(points, r_filter: float, r_min: float, r_max: float,
 
 def capt_upload(tree: CaptTree, device: int = 0, stream=None):
     _check(_load().capt_upload(tree.h, int(device), _stream(stream)), "capt_upload")
+
+
+def capt_build_grid(tree: CaptTree, max_cells: int = 0, stream=None):
+    """Build (or rebuild) the tree's distance-bound grid on its device (at most max_cells
+    cells; 0 = the library's default); configuration queries use it with grid = 1."""
+    _check(_load().capt_build_grid(tree.h, int(max_cells), _stream(stream)), "capt_build_grid")
+
+
+def capt_grid_export(tree: CaptTree):
+    """(shape dict, cells uint8 [n2, n1, n0, 2] = {lower, upper} bound) of the tree's
+    distance-bound grid, or (None, None) without one."""
+    info = _GridInfo()
+    _check(_load().capt_grid_export(tree.h, C.byref(info), None), "capt_grid_export")
+    if info.cells == 0:
+        return None, None
+    cells = np.zeros(2 * info.cells, np.uint8)
+    _check(_load().capt_grid_export(tree.h, C.byref(info), _ptr(cells)), "capt_grid_export")
+    shape = dict(origin=np.array(info.origin, np.float32), cell=np.float32(info.cell),
+                 inv_cell=np.float32(info.inv_cell), unit=np.float32(info.unit), dims=tuple(info.dims))
+    n0, n1, n2 = shape["dims"]
+    return shape, cells.reshape(n2, n1, n0, 2)
 
 
 def capt_compact(tree: CaptTree, drop_full: bool = False, stream=None):
@@ -442,8 +470,8 @@ def capt_device_status(tree: CaptTree, stream=None) -> int:
 
 
 def capt_set_launch_cfg(tree: CaptTree, kernel: int, warps_per_block: int, spheres_per_lane: int, staging: int,
-                        chunk: int = 0, prefetch: int = 0):
-    c = _LaunchCfg(warps_per_block, spheres_per_lane, staging, chunk, prefetch)
+                        chunk: int = 0, prefetch: int = 0, grid: int = 0):
+    c = _LaunchCfg(warps_per_block, spheres_per_lane, staging, chunk, prefetch, grid)
     _check(_load().capt_set_launch_cfg(tree.h, int(kernel), C.byref(c)), "capt_set_launch_cfg")
 
 
@@ -625,7 +653,7 @@ def capt_edge_plan_create(tree: CaptTree, arm, qa, qb, nsteps, valid, cfg=None, 
     a = arm if isinstance(arm, _Arm) else make_arm(arm)
     E = _edge_args(tree, a, qa, qb, nsteps, valid)
     c = None if cfg is None else C.byref(_LaunchCfg(cfg["warps_per_block"], cfg["spheres_per_lane"], cfg["staging"],
-                                                    cfg["chunk"], cfg.get("prefetch", 0)))
+                                                    cfg["chunk"], cfg.get("prefetch", 0), cfg.get("grid", 0)))
     h = C.c_void_p()
     _check(_load().capt_edge_plan_create(tree.h, C.byref(a), _dev(qa, torch.float32, "qa"),
                                          _dev(qb, torch.float32, "qb"), _dev(nsteps, torch.int32, "nsteps"), E,

@@ -57,6 +57,8 @@ bool valid_cfg(int kernel, const capt_launch_cfg& c) {
     if (c.staging != CAPT_STAGE_GLOBAL && c.staging != CAPT_STAGE_SMEM) return false;
     if (c.prefetch < 0 || c.prefetch > CAPT_MAX_PREFETCH) return false;
     if (c.prefetch != 0 && kernel != CAPT_KERNEL_CONFIGS && kernel != CAPT_KERNEL_CLEARANCE) return false;
+    if (c.grid != 0 && c.grid != 1) return false;
+    if (c.grid != 0 && kernel != CAPT_KERNEL_CONFIGS && kernel != CAPT_KERNEL_SPHERES) return false;
     const int spl = c.spheres_per_lane;
     const bool scan_mode = c.chunk >= CAPT_SCAN_SETS && c.chunk <= CAPT_SCAN_COMPACT;
     if (kernel == CAPT_KERNEL_SPHERES) return (spl == 1 || spl == 2 || spl == 4 || spl == 8) && scan_mode;
@@ -82,6 +84,8 @@ struct capt_tree {
     void* d_ids = nullptr;
     void* d_cloud = nullptr;
     void* d_cbox = nullptr;      // chunk boxes (chunk_count(total_blocks) x 8 floats)
+    uint8_t* d_grid = nullptr;   // distance-bound grid of capt_build_grid (2 bytes per cell)
+    capt::GridShape gshape;
     int* d_status = nullptr;
     uint64_t total_blocks = 0;
     size_t dev_bytes = 0;
@@ -156,6 +160,8 @@ struct capt_tree {
         a.cplane = cs.n_chunks > 0 ? cs.n_chunks * capt::kChunkBlocks : 1;
         a.ccbox = static_cast<const float*>(cs.ccbox);
         a.status = d_status;
+        a.grid = gshape.cells ? d_grid : nullptr;
+        a.g = gshape;
         a.N = (uint32_t)h.N;
         a.L = h.L;
         a.r_min = h.r_min;
@@ -171,7 +177,8 @@ struct capt_tree {
         if (device < 0) return;
         DeviceGuard g(device);
         for (void* p : {d_T, d_leaves, d_blocks, d_ids, d_cloud, d_cbox, (void*)d_status, (void*)d_pipe_c[0], (void*)d_pipe_c[1],
-                        (void*)d_pipe_f[0], (void*)d_pipe_f[1], (void*)d_edge_scratch, (void*)d_zc_flags, d_Tplain,
+                        (void*)d_pipe_f[0], (void*)d_pipe_f[1], (void*)d_edge_scratch, (void*)d_zc_flags, (void*)d_grid,
+                        d_Tplain,
                         d_set_idx, d_set_begin, d_pruned})
             if (p) cudaFree(p);
         cs.release();
@@ -186,6 +193,8 @@ struct capt_tree {
             if (e) cudaEventDestroy(e);
         if (pipe_stream) cudaStreamDestroy(pipe_stream);
         d_T = d_leaves = d_blocks = d_ids = d_cloud = d_cbox = nullptr;
+        d_grid = nullptr;
+        gshape = capt::GridShape();
         d_Tplain = d_set_idx = d_set_begin = d_pruned = nullptr;
         d_status = nullptr;
         d_pipe_c[0] = d_pipe_c[1] = nullptr;
@@ -475,6 +484,7 @@ int capt_build_device(const float* d_points, size_t n, float r_min, float r_max,
     }
     t->dev_bytes = d.bytes + sz_cbox + kStatusBytes;
     t->host_pending = true;
+
     h.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     *out = t;
     return CAPT_OK;
@@ -571,6 +581,8 @@ int capt_stats(const capt_tree* t, capt_tree_stats* s) {
     s->compact_bytes = t->cs.bytes;
     s->scratch_bytes = (uint64_t)t->edge_scratch_cap * sizeof(uint32_t) +
                        2 * ((uint64_t)t->pipe_cap * sizeof(float) + t->pipe_fbytes) + (uint64_t)t->zc_cap;
+    for (int d = 0; d < 3; d++) s->grid_dims[d] = t->gshape.cells ? (uint32_t)t->gshape.n[d] : 0u;
+    s->grid_cell = t->gshape.cells ? t->gshape.h : 0.f;
     s->full_dropped = t->full_dropped ? 1 : 0;
     return CAPT_OK;
 }
@@ -681,6 +693,66 @@ int capt_upload(capt_tree* t, int device, void* stream) {
     t->tail_staged = bs.tail_staged;
     t->stage_floats = bs.stage_floats;
     t->dev_bytes = sz_T + sz_leaves + sz_blocks + sz_ids + sz_cloud + sz_cbox + kStatusBytes;
+    return CAPT_OK;
+}
+
+int capt_build_grid(capt_tree* t, uint64_t max_cells, void* stream) {
+    int rc = check_full(t);
+    if (rc) return rc;
+    if (max_cells == 0) max_cells = capt::kGridDefaultCells;
+    if (max_cells > (1ull << 28)) return fail(CAPT_E_ARG, "max_cells must be at most 2^28");
+    std::lock_guard<std::mutex> lk(t->mu);
+    DeviceGuard g(t->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const capt::GridShape gs = capt::grid_shape(t->box_lo, t->box_hi, t->h.r_max, t->h.n, max_cells);
+    if (t->d_grid) {
+        CUDA_TRY(cudaStreamSynchronize(st), "synchronize");
+        cudaFree(t->d_grid);
+        t->dev_bytes -= std::min<size_t>(t->dev_bytes, 2 * (size_t)t->gshape.cells);
+        t->d_grid = nullptr;
+        t->gshape = capt::GridShape();
+    }
+    if (gs.cells == 0) return CAPT_OK;   // no points or r_max = 0: nothing to bound
+    const size_t bytes = 2 * (size_t)gs.cells;
+    cudaError_t e = cudaMalloc((void**)&t->d_grid, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        t->d_grid = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? CAPT_E_NOMEM : CAPT_E_CUDA, "cudaMalloc of the grid failed");
+    }
+    std::string err;
+    rc = capt::launch_dist_grid(t->args(), gs, t->d_grid, st, err);
+    if (rc == CAPT_OK) {
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { rc = CAPT_E_CUDA; err = std::string("grid: ") + cudaGetErrorString(e); }
+    }
+    if (rc) {
+        cudaFree(t->d_grid);
+        t->d_grid = nullptr;
+        return fail(rc, err);
+    }
+    t->gshape = gs;
+    t->dev_bytes += bytes;
+    return CAPT_OK;
+}
+
+int capt_grid_export(const capt_tree* t, capt_grid_info* info, uint8_t* h_cells) {
+    if (!t || !info) return fail(CAPT_E_ARG, "NULL argument");
+    std::memset(info, 0, sizeof(*info));
+    const capt::GridShape& g = t->gshape;
+    if (!t->d_grid || g.cells == 0) return CAPT_OK;
+    for (int d = 0; d < 3; d++) {
+        info->origin[d] = g.org[d];
+        info->dims[d] = g.n[d];
+    }
+    info->cell = g.h;
+    info->inv_cell = g.inv_h;
+    info->unit = g.unit;
+    info->cells = g.cells;
+    if (h_cells) {
+        DeviceGuard dg(t->device);
+        CUDA_TRY(cudaMemcpy(h_cells, t->d_grid, 2 * (size_t)g.cells, cudaMemcpyDeviceToHost), "grid D2H");
+    }
     return CAPT_OK;
 }
 
@@ -928,7 +1000,11 @@ int capt_autotune_configs(capt_tree* t, const float* d_centers, const float* d_r
         for (int spl : {2, 4, 8, 16})
             for (int stage : {CAPT_STAGE_GLOBAL, CAPT_STAGE_SMEM})
                 for (int mode : scan_modes(t))
-                    for (int pf : {0, 1, 2}) cands.push_back({warps, spl, stage, mode, pf});
+                    for (int pf : {0, 1})
+                        for (int grid : {0, 1})
+                            // the grid path has no staged variant
+                            if (!grid || (t->d_grid && stage == CAPT_STAGE_GLOBAL))
+                                cands.push_back({warps, spl, stage, mode, pf, grid});
     return autotune_query(t, CAPT_KERNEL_CONFIGS, cands, d_centers, d_radii, C, S, d_flags,
                           static_cast<cudaStream_t>(stream), best, best_ms);
 }
@@ -943,7 +1019,9 @@ int capt_autotune_spheres(capt_tree* t, const float* d_centers, const float* d_r
     for (int warps : {4, 8, 16})
         for (int spl : {1, 2, 4, 8})
             for (int stage : {CAPT_STAGE_GLOBAL, CAPT_STAGE_SMEM})
-                for (int mode : scan_modes(t)) cands.push_back({warps, spl, stage, mode});
+                for (int mode : scan_modes(t))
+                    for (int grid : {0, 1})
+                        if (!grid || t->d_grid) cands.push_back({warps, spl, stage, mode, 0, grid});
     return autotune_query(t, CAPT_KERNEL_SPHERES, cands, d_centers, d_radii, m, 1, d_flags,
                           static_cast<cudaStream_t>(stream), best, best_ms);
 }

@@ -62,6 +62,21 @@ inline uint64_t chunk_count(uint64_t total_blocks) {
     return ((total_blocks > 0 ? total_blocks : 1) + kChunkBlocks - 1) / kChunkBlocks;
 }
 
+// Distance-bound grid (dist_grid.cu): a uniform grid of cubic cells over the cloud's
+// bounding box grown by r_max, two bytes per cell (a lower and an upper bound of the
+// distance from the cell to the cloud, in units of `unit`).  Cell (i, j, k) is the box
+// [org + (i, j, k) h, org + (i + 1, j + 1, k + 1) h], computed exactly from the FP32
+// org and h, stored at (k n[1] + j) n[0] + i.
+constexpr uint64_t kGridDefaultCells = 1ull << 22;
+constexpr int kGridMaxAxis = 16384;
+struct GridShape {
+    float org[3] = {0.f, 0.f, 0.f};
+    float h = 0.f, inv_h = 0.f, unit = 0.f, pad = 0.f;
+    int n[3] = {0, 0, 0};
+    uint32_t cells = 0;   // 0: no grid
+};
+GridShape grid_shape(const float lo[3], const float hi[3], float r_max, uint64_t n_points, uint64_t max_cells);
+
 // Kernel view of an uploaded tree (raw device pointers, passed by value).
 struct DevArgs {
     const float* T = nullptr;        // blocked split array (BlockedSplits::data)
@@ -86,6 +101,8 @@ struct DevArgs {
     float r_min = 0.f, r_max = 0.f;
     float lo[3] = {0.f, 0.f, 0.f};   // bounding box of the cloud (empty cloud: lo > hi)
     float hi[3] = {-1.f, -1.f, -1.f};
+    const uint8_t* grid = nullptr;   // distance-bound grid, 2 g.cells bytes (null: none)
+    GridShape g;
 };
 
 }  // namespace capt

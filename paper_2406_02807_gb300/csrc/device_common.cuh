@@ -202,6 +202,27 @@ __device__ __forceinline__ void prefetch_l2(const void* p, uint64_t bytes) {
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(e - a)) : "memory");
 }
 
+// Distance-bound grid (dist_grid.cu): 0 when the grid proves that the sphere (x, r)
+// misses every cloud point under the FP32 test, 1 when it proves that it hits one, 2
+// when it cannot tell.
+__device__ __forceinline__ int grid_classify(const DevArgs& t, float x, float y, float z, float r) {
+    const GridShape& g = t.g;
+    const float ux = __fmul_rn(__fsub_rn(x, g.org[0]), g.inv_h);
+    const float uy = __fmul_rn(__fsub_rn(y, g.org[1]), g.inv_h);
+    const float uz = __fmul_rn(__fsub_rn(z, g.org[2]), g.inv_h);
+    // inside the grid box: the cell computed below holds x (grown by h / 100)
+    const bool inside = ux >= 0.f && uy >= 0.f && uz >= 0.f && ux < (float)g.n[0] && uy < (float)g.n[1] &&
+                        uz < (float)g.n[2];
+    const uint32_t i = (uint32_t)fminf(fmaxf(ux, 0.f), (float)(g.n[0] - 1));
+    const uint32_t j = (uint32_t)fminf(fmaxf(uy, 0.f), (float)(g.n[1] - 1));
+    const uint32_t k = (uint32_t)fminf(fmaxf(uz, 0.f), (float)(g.n[2] - 1));
+    const uint32_t c = (k * (uint32_t)g.n[1] + j) * (uint32_t)g.n[0] + i;
+    const unsigned short q = __ldg(reinterpret_cast<const unsigned short*>(t.grid) + c);
+    if (__fmul_rn((float)(q & 0xffu), g.unit) > r) return 0;
+    if (inside && (q >> 8) < 255u && __fmul_rn((float)(q >> 8), g.unit) < r) return 1;
+    return 2;
+}
+
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
 // Order-preserving unsigned key of a float (-0 and +0 share one key, as they compare

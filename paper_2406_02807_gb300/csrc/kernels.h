@@ -29,6 +29,7 @@ int launch_leaves(const DevArgs& t, const float* centers, uint64_t m, uint32_t* 
                   std::string& err);
 
 // Clearance forward / backward.
+int launch_dist_grid(const DevArgs& t, const GridShape& g, uint8_t* out, cudaStream_t st, std::string& err);
 int launch_count_clearance(const DevArgs& t, const float* centers, uint64_t m, uint64_t* counts, cudaStream_t st,
                            std::string& err);
 int launch_clearance_fwd(const DevArgs& t, const float* centers, const float* radii, uint64_t T, int W, int S,

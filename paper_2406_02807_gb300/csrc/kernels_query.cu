@@ -55,7 +55,7 @@ __device__ __forceinline__ void bulk_copy(float* dst, const float* src, uint32_t
 template <int SPL, bool STAGE, int MODE>
 __global__ void __launch_bounds__(512, 2)
     k_spheres(DevArgs t, const float* __restrict__ centers, const float* __restrict__ radii, uint64_t m,
-              uint8_t* __restrict__ out, unsigned long long* ctr) {
+              uint8_t* __restrict__ out, unsigned long long* ctr, bool use_grid) {
     using WS = SphereScratch<SPL>;
     constexpr uint32_t E = 32 * SPL;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -183,6 +183,39 @@ __global__ void __launch_bounds__(512, 2)
             n_near += __popc(mask);
         }
         __syncwarp();
+        // ---- with the distance-bound grid: near spheres it can decide are decided (a
+        // certain hit is recorded at once), the undecided ones are compacted in place ----
+        if (use_grid) {
+            uint32_t n_rest = 0;
+            for (uint32_t r0 = 0; r0 < n_near; r0 += 32) {
+                const uint32_t q = r0 + lane;
+                int cls = 0;
+                uint32_t j = 0;
+                if (q < n_near) {
+                    j = ws->nslot[q];
+                    float x, y, z, r;
+                    if (in_smem) {
+                        x = in[3 * j];
+                        y = in[3 * j + 1];
+                        z = in[3 * j + 2];
+                        r = in[3 * E + j];
+                    } else {
+                        x = __ldg(centers + 3 * (first + j));
+                        y = __ldg(centers + 3 * (first + j) + 1);
+                        z = __ldg(centers + 3 * (first + j) + 2);
+                        r = __ldg(radii + first + j);
+                    }
+                    cls = grid_classify(t, x, y, z, r);
+                    if (cls == 1) ws->ghit[j] = 1;
+                }
+                const uint32_t km = __ballot_sync(0xffffffffu, cls == 2);
+                __syncwarp();   // every read of this group precedes the writes below
+                if (cls == 2) ws->nslot[n_rest + __popc(km & lt_mask)] = j;
+                n_rest += __popc(km);
+                __syncwarp();
+            }
+            n_near = n_rest;
+        }
         // ---- rounds of 32 near spheres: descent, leaf box, scan ----
         for (uint32_t r0 = 0; r0 < n_near; r0 += 32) {
             const uint32_t q = r0 + lane;
@@ -250,13 +283,13 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs(DevArgs t, cons
                                                                  uint32_t pf) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t bar;
-    __shared__ float r2s[64];
+    __shared__ __align__(16) float r2s[64];
     for (int i = (int)threadIdx.x; i < S; i += (int)blockDim.x) r2s[i] = __fmul_rn(radii[i], radii[i]);
-    const float* Ts = nullptr;
     uint32_t off = 0;
+    if constexpr (STAGE) off = stage_offset(t);
+    const float* Ts = nullptr;
     if constexpr (STAGE) {
         Ts = stage_splits(t, smem_raw, &bar);   // contains a block barrier
-        off = stage_offset(t);
     } else {
         __syncthreads();
     }
@@ -269,6 +302,7 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs(DevArgs t, cons
     const float4 rlo = make_float4(t.lo[0], t.lo[1], t.lo[2], 0.f);
     const float4 rhi = make_float4(t.hi[0], t.hi[1], t.hi[2], 0.f);
     const uint32_t inv_s = (1u << 20) / (uint32_t)S + 1u;   // i / S = (i * inv_s) >> 20 for i < 4096
+    const bool s4 = (S & 3) == 0;
 
     auto run_round = [&](uint32_t n) {
         const bool live = lane < n;
@@ -295,6 +329,10 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs(DevArgs t, cons
         const bool vec = (reinterpret_cast<uintptr_t>(base) & 15u) == 0;
         if (lane < CPT) ws->ghit[lane] = 0;
         __syncwarp();
+        // bit g: configuration g of the tile is known to collide (warp-uniform; refreshed
+        // from ghit after every round)
+        uint32_t resolved = 0;
+        const uint32_t all_cfg = ncfg >= 32u ? 0xffffffffu : ((1u << ncfg) - 1u);
         uint32_t n_near = 0;
         for (uint32_t p0 = 0; p0 < nsph; p0 += 128) {
             // ---- root box test of 4 consecutive spheres per lane ----
@@ -313,19 +351,40 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs(DevArgs t, cons
             }
             uint32_t g = (i0 * inv_s) >> 20;
             uint32_t sidx = i0 - g * (uint32_t)S;
+            if (s4) {
+                // S a multiple of 4: the lane's four spheres are slots sidx .. sidx + 3 of
+                // configuration g, their radii one 16-byte load each
+                const float4 q2 = reinterpret_cast<const float4*>(r2s)[sidx >> 2];
+                const float r2k[4] = {q2.x, q2.y, q2.z, q2.w};
+                const bool open = nv > 0 && !((resolved >> (g & 31u)) & 1u);
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const float x = v[3 * k], y = v[3 * k + 1], z = v[3 * k + 2];
-                const float r2 = r2s[sidx];
-                const bool near = (uint32_t)k < nv && !ws->ghit[g] && box_dist2(x, y, z, rlo, rhi) <= r2;
-                const uint32_t mask = __ballot_sync(0xffffffffu, near);
-                if (near) {
-                    const uint32_t pos = n_near + __popc(mask & lt_mask);
-                    ws->nc[pos] = make_float4(x, y, z, r2);
-                    ws->ng[pos] = g;
+                for (int k = 0; k < 4; k++) {
+                    const float x = v[3 * k], y = v[3 * k + 1], z = v[3 * k + 2];
+                    const bool near = open && (uint32_t)k < nv && box_dist2(x, y, z, rlo, rhi) <= r2k[k];
+                    const uint32_t mask = __ballot_sync(0xffffffffu, near);
+                    if (near) {
+                        const uint32_t pos = n_near + __popc(mask & lt_mask);
+                        ws->nc[pos] = make_float4(x, y, z, r2k[k]);
+                        ws->ng[pos] = g;
+                    }
+                    n_near += __popc(mask);
                 }
-                n_near += __popc(mask);
-                if (++sidx == (uint32_t)S) { sidx = 0; g++; }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const float x = v[3 * k], y = v[3 * k + 1], z = v[3 * k + 2];
+                    const float r2 = r2s[sidx];
+                    const bool near = (uint32_t)k < nv && !((resolved >> (g & 31u)) & 1u) &&
+                                      box_dist2(x, y, z, rlo, rhi) <= r2;
+                    const uint32_t mask = __ballot_sync(0xffffffffu, near);
+                    if (near) {
+                        const uint32_t pos = n_near + __popc(mask & lt_mask);
+                        ws->nc[pos] = make_float4(x, y, z, r2);
+                        ws->ng[pos] = g;
+                    }
+                    n_near += __popc(mask);
+                    if (++sidx == (uint32_t)S) { sidx = 0; g++; }
+                }
             }
             // ---- rounds of 32 queued near spheres ----
             if (n_near >= 32) {
@@ -358,8 +417,9 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs(DevArgs t, cons
                 }
                 n_near = rest;
                 __syncwarp();
+                resolved = __ballot_sync(0xffffffffu, lane < ncfg && ws->ghit[lane]);
                 // every configuration of the tile resolved: nothing left to learn
-                if (__all_sync(0xffffffffu, lane >= ncfg || ws->ghit[lane])) { n_near = 0; break; }
+                if ((resolved & all_cfg) == all_cfg) { n_near = 0; break; }
             }
         }
         if (n_near) {
@@ -370,6 +430,217 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs(DevArgs t, cons
         if (lane < ncfg) out[first + lane] = (uint8_t)ws->ghit[lane];
         __syncwarp();
     }
+}
+
+// ------------------------------------------------------------------------------------
+// Configuration queries with the distance-bound grid (dist_grid.cu).  The stream and
+// its root box test are those of k_configs; the spheres that reach the cloud's box are
+// then classified 32 at a time by their grid cell (one lookup per lane): a sphere the
+// grid proves clear is dropped, one it proves colliding resolves its configuration at
+// once, and only the undecided rest go on to the descent.  Those are few (a sphere is
+// undecided only within about a cell of the distance r from the cloud), so they are
+// carried across the warp's tiles with their global configuration index and processed
+// in full rounds of 32; a hit there sets the configuration's flag directly (after the
+// tile's own write, in the warp's program order).  Whatever is left when the warp runs
+// out of tiles makes one last round.
+// ------------------------------------------------------------------------------------
+struct CfgGridScratch {
+    float4 nc[kQueue];     // spheres that reach the cloud's box, awaiting classification: centre, r
+    uint8_t ng[kQueue];    // their configuration within the tile
+    float4 c2[64];         // undecided spheres carried to a round: centre, r^2
+    uint32_t g2[64];       // their configuration (index into the flags)
+    uint32_t ghit[32];     // per configuration of the tile: 1 once it collides
+    uint32_t ghit2[32];    // per entry of a carried round: 1 once it collides
+    RoundEntries re;
+};
+
+template <int CPT, int MODE>
+__global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs_grid(DevArgs t, const float* __restrict__ centers,
+                                                                      const float* __restrict__ radii, uint64_t C,
+                                                                      int S, uint8_t* __restrict__ out,
+                                                                      unsigned long long* ctr, uint32_t pf) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(16) float r2s[64];
+    __shared__ __align__(16) float rs[64];
+    for (int i = (int)threadIdx.x; i < S; i += (int)blockDim.x) {
+        rs[i] = radii[i];
+        r2s[i] = __fmul_rn(radii[i], radii[i]);
+    }
+    __syncthreads();
+    const uint32_t lane = lane_id();
+    const uint32_t warp = threadIdx.x >> 5;
+    CfgGridScratch* ws = reinterpret_cast<CfgGridScratch*>(smem_raw) + warp;
+    const uint64_t n_tiles = (C + CPT - 1) / CPT;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const float4 rlo = make_float4(t.lo[0], t.lo[1], t.lo[2], 0.f);
+    const float4 rhi = make_float4(t.hi[0], t.hi[1], t.hi[2], 0.f);
+    const uint32_t inv_s = (1u << 20) / (uint32_t)S + 1u;   // i / S = (i * inv_s) >> 20 for i < 4096
+    const bool s4 = (S & 3) == 0;
+    const uint64_t pf_tiles = (uint64_t)pf * nwarps;
+
+    uint32_t n2 = 0;   // carried undecided spheres (warp-uniform)
+    uint64_t first = 0;
+    uint32_t ncfg = 0;   // configurations of the current tile (0: none)
+
+    // A round over the first n carried spheres; hits set their flags (and the current
+    // tile's resolution); the rest of the carried queue moves to the front.
+    auto carried_round = [&](uint32_t n) {
+        const bool live = lane < n;
+        const float4 c = live ? ws->c2[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const uint32_t gg = live ? ws->g2[lane] : 0u;
+        // an entry of the current tile whose configuration is already decided is skipped
+        const uint64_t rel = (uint64_t)gg - first;
+        ws->ghit2[lane] = (live && rel < ncfg && ws->ghit[rel]) ? 1u : 0u;
+        __syncwarp();
+        sphere_round<false, MODE>(t, nullptr, &ws->re, ws->ghit2, c, lane, live, lane, lt_mask);
+        __syncwarp();
+        if (live && ws->ghit2[lane]) {
+            out[gg] = 1;
+            if (rel < ncfg) ws->ghit[rel] = 1;
+        }
+        float4 cc = make_float4(0.f, 0.f, 0.f, 0.f);
+        uint32_t g3 = 0;
+        const bool mv = lane + n < n2;
+        if (mv) {
+            cc = ws->c2[lane + n];
+            g3 = ws->g2[lane + n];
+        }
+        __syncwarp();
+        if (mv) {
+            ws->c2[lane] = cc;
+            ws->g2[lane] = g3;
+        }
+        n2 -= n;
+        __syncwarp();
+    };
+
+    uint32_t resolved = 0;
+    uint32_t n1 = 0;
+    // Classify the first n queued spheres by their grid cell; the rest of the queue
+    // moves to the front.
+    auto classify = [&](uint32_t n) {
+        const bool live = lane < n;
+        float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+        uint32_t g = 0;
+        int cls = 0;
+        if (live) {
+            c = ws->nc[lane];
+            g = ws->ng[lane];
+            if (!((resolved >> (g & 31u)) & 1u)) cls = grid_classify(t, c.x, c.y, c.z, c.w);
+        }
+        if (cls == 1) ws->ghit[g] = 1;
+        const bool keep = cls == 2;
+        const uint32_t km = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+            const uint32_t pos = n2 + __popc(km & lt_mask);
+            ws->c2[pos] = make_float4(c.x, c.y, c.z, __fmul_rn(c.w, c.w));
+            ws->g2[pos] = (uint32_t)(first + g);
+        }
+        n2 += __popc(km);
+        // the rest of the queue (< 160 - n) to the front, 32 at a time in order
+        for (uint32_t b = 0; b < n1 - n; b += 32) {
+            const bool mv = b + lane < n1 - n;
+            float4 cc = make_float4(0.f, 0.f, 0.f, 0.f);
+            uint8_t gq = 0;
+            if (mv) {
+                cc = ws->nc[n + b + lane];
+                gq = ws->ng[n + b + lane];
+            }
+            __syncwarp();
+            if (mv) {
+                ws->nc[b + lane] = cc;
+                ws->ng[b + lane] = gq;
+            }
+            __syncwarp();
+        }
+        n1 -= n;
+        __syncwarp();
+        resolved = __ballot_sync(0xffffffffu, lane < ncfg && ws->ghit[lane]);
+        if (n2 >= 32) carried_round(32);
+        resolved = __ballot_sync(0xffffffffu, lane < ncfg && ws->ghit[lane]);
+    };
+
+    const TileSched sched{ctr, nwarps};
+    for (uint64_t tile = sched.first((uint64_t)blockIdx.x * (blockDim.x >> 5) + warp); tile < n_tiles;
+         tile = sched.next(tile)) {
+        first = tile * CPT;
+        ncfg = (uint32_t)min((uint64_t)CPT, C - first);
+        if (pf_tiles && lane == 0 && tile + pf_tiles < n_tiles) {
+            const uint64_t pfirst = (tile + pf_tiles) * CPT;
+            prefetch_l2(centers + 3 * pfirst * (uint64_t)S, min((uint64_t)CPT, C - pfirst) * (uint64_t)S * 12u);
+        }
+        const uint32_t nsph = ncfg * (uint32_t)S;
+        const float* base = centers + 3 * first * (uint64_t)S;
+        const bool vec = (reinterpret_cast<uintptr_t>(base) & 15u) == 0;
+        if (lane < CPT) ws->ghit[lane] = 0;
+        __syncwarp();
+        resolved = 0;
+        const uint32_t all_cfg = ncfg >= 32u ? 0xffffffffu : ((1u << ncfg) - 1u);
+        n1 = 0;
+        for (uint32_t p0 = 0; p0 < nsph; p0 += 128) {
+            // ---- root box test of 4 consecutive spheres per lane ----
+            const uint32_t i0 = p0 + 4 * lane;
+            const uint32_t nv = i0 < nsph ? min(4u, nsph - i0) : 0u;
+            float v[12];
+            if (vec && nv == 4) {
+                const float4* q = reinterpret_cast<const float4*>(base + 3 * (size_t)i0);
+                const float4 a = __ldg(q), b = __ldg(q + 1), cc = __ldg(q + 2);
+                v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+                v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+                v[8] = cc.x; v[9] = cc.y; v[10] = cc.z; v[11] = cc.w;
+            } else {
+#pragma unroll
+                for (int k = 0; k < 12; k++) v[k] = (uint32_t)(k / 3) < nv ? __ldg(base + 3 * (size_t)i0 + k) : 0.f;
+            }
+            uint32_t g = (i0 * inv_s) >> 20;
+            uint32_t sidx = i0 - g * (uint32_t)S;
+            if (s4) {
+                const float4 q2 = reinterpret_cast<const float4*>(r2s)[sidx >> 2];
+                const float4 qr = reinterpret_cast<const float4*>(rs)[sidx >> 2];
+                const float r2k[4] = {q2.x, q2.y, q2.z, q2.w};
+                const float rk[4] = {qr.x, qr.y, qr.z, qr.w};
+                const bool open = nv > 0 && !((resolved >> (g & 31u)) & 1u);
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const float x = v[3 * k], y = v[3 * k + 1], z = v[3 * k + 2];
+                    const bool near = open && (uint32_t)k < nv && box_dist2(x, y, z, rlo, rhi) <= r2k[k];
+                    const uint32_t mask = __ballot_sync(0xffffffffu, near);
+                    if (near) {
+                        const uint32_t pos = n1 + __popc(mask & lt_mask);
+                        ws->nc[pos] = make_float4(x, y, z, rk[k]);
+                        ws->ng[pos] = (uint8_t)g;
+                    }
+                    n1 += __popc(mask);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const float x = v[3 * k], y = v[3 * k + 1], z = v[3 * k + 2];
+                    const bool near = (uint32_t)k < nv && !((resolved >> (g & 31u)) & 1u) &&
+                                      box_dist2(x, y, z, rlo, rhi) <= r2s[sidx];
+                    const uint32_t mask = __ballot_sync(0xffffffffu, near);
+                    if (near) {
+                        const uint32_t pos = n1 + __popc(mask & lt_mask);
+                        ws->nc[pos] = make_float4(x, y, z, rs[sidx]);
+                        ws->ng[pos] = (uint8_t)g;
+                    }
+                    n1 += __popc(mask);
+                    if (++sidx == (uint32_t)S) { sidx = 0; g++; }
+                }
+            }
+            __syncwarp();
+            while (n1 >= 32) classify(32);
+            // every configuration of the tile resolved: nothing left to learn
+            if ((resolved & all_cfg) == all_cfg) { n1 = 0; break; }
+        }
+        if (n1) classify(n1);
+        __syncwarp();
+        if (lane < ncfg) out[first + lane] = (uint8_t)ws->ghit[lane];
+        __syncwarp();
+    }
+    ncfg = 0;
+    while (n2) carried_round(min(n2, 32u));
 }
 
 // Sequential work count per configuration (one thread each), in the order the query
@@ -494,7 +765,7 @@ int sm_count() {
 
 namespace {
 
-using SphereKernel = void (*)(DevArgs, const float*, const float*, uint64_t, uint8_t*, unsigned long long*);
+using SphereKernel = void (*)(DevArgs, const float*, const float*, uint64_t, uint8_t*, unsigned long long*, bool);
 
 template <int SPL, bool STAGE>
 SphereKernel pick_spheres_mode(int mode) {
@@ -567,8 +838,55 @@ ConfigKernel pick_configs(int spl, bool stage, int mode) {
     }
 }
 
+using ConfigGridKernel = void (*)(DevArgs, const float*, const float*, uint64_t, int, uint8_t*, unsigned long long*,
+                                  uint32_t);
+
+template <int CPT>
+ConfigGridKernel pick_configs_grid_mode(int mode) {
+    switch (mode) {
+        case kScanPlain: return k_configs_grid<CPT, kScanPlain>;
+        case kScanChunked: return k_configs_grid<CPT, kScanChunked>;
+        case kScanCompact: return k_configs_grid<CPT, kScanCompact>;
+        default: return nullptr;
+    }
+}
+
+ConfigGridKernel pick_configs_grid(int spl, int mode) {
+    switch (spl) {
+        case 2: return pick_configs_grid_mode<4>(mode);
+        case 4: return pick_configs_grid_mode<8>(mode);
+        case 8: return pick_configs_grid_mode<16>(mode);
+        case 16: return pick_configs_grid_mode<32>(mode);
+        default: return nullptr;
+    }
+}
+
+// The configuration query with the distance-bound grid (k_configs_grid).
+int launch_configs_grid(const DevArgs& t, const float* centers, const float* radii, uint64_t C, int S, uint8_t* out,
+                        const capt_launch_cfg& cfg, unsigned long long* ctr, cudaStream_t st, std::string& err) {
+    ConfigGridKernel fn = pick_configs_grid(cfg.spheres_per_lane, cfg.chunk);
+    if (!fn) { err = "configuration queries take spheres_per_lane 2, 4, 8 or 16"; return CAPT_E_ARG; }
+    const int cpt = 2 * cfg.spheres_per_lane;
+    const int warps = std::max(1, std::min(16, (int)cfg.warps_per_block));
+    const size_t smem = sizeof(CfgGridScratch) * (size_t)warps;
+    cudaError_t ce = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (ce != cudaSuccess) { err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
+    const int occ = std::max(1, occupancy((const void*)fn, warps * 32, smem));
+    const uint64_t tiles = (C + cpt - 1) / cpt;
+    const uint64_t need = (tiles + warps - 1) / warps;
+    const uint64_t blocks = std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)sm_count() * occ, need));
+    const uint32_t pf = (uint32_t)std::max(0, std::min(CAPT_MAX_PREFETCH, (int)cfg.prefetch));
+    fn<<<(unsigned)blocks, warps * 32, smem, st>>>(t, centers, radii, C, S, out, ctr, pf);
+    ce = cudaGetLastError();
+    if (ce != cudaSuccess) { err = std::string("configuration launch: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
+    return CAPT_OK;
+}
+
 int launch_configs(const DevArgs& t, const float* centers, const float* radii, uint64_t C, int S, uint8_t* out,
                    const capt_launch_cfg& cfg, unsigned long long* ctr, cudaStream_t st, std::string& err) {
+    // the grid path carries configuration indices in 32 bits
+    if (cfg.grid && t.grid && C < (1ull << 32))
+        return launch_configs_grid(t, centers, radii, C, S, out, cfg, ctr, st, err);
     const bool stage = cfg.staging == CAPT_STAGE_SMEM && t.stage_floats > 0;
     ConfigKernel fn = pick_configs(cfg.spheres_per_lane, stage, cfg.chunk);
     if (!fn) { err = "configuration queries take spheres_per_lane 2, 4, 8 or 16"; return CAPT_E_ARG; }
@@ -606,7 +924,7 @@ int launch_query(const DevArgs& t, int mode, const float* centers, const float* 
     const uint64_t tiles = (n_items + per_tile - 1) / per_tile;
     const uint64_t need = (tiles + warps - 1) / warps;
     const uint64_t blocks = std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)sm_count() * occ, need));
-    fn<<<(unsigned)blocks, warps * 32, smem, st>>>(t, centers, radii, n_items, out, ctr);
+    fn<<<(unsigned)blocks, warps * 32, smem, st>>>(t, centers, radii, n_items, out, ctr, cfg.grid != 0 && t.grid);
     ce = cudaGetLastError();
     if (ce != cudaSuccess) { err = std::string("query launch: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
     return CAPT_OK;

@@ -564,3 +564,10 @@ def test_room_full_size(orc, capt_lib, torch_):
     for chunked in (0, 1):
         capt_lib.capt_set_launch_cfg(ts, capt_lib.CAPT_KERNEL_SPHERES, 8, 2, 0, chunked)
         assert np.array_equal(capt_lib.capt_query_spheres(ts, _cuda(torch_, c), _cuda(torch_, r)).cpu().numpy(), ref)
+    # with the distance-bound grid most spheres are decided before any descent: the same
+    # flags, with either scan
+    capt_lib.capt_build_grid(tree)
+    for chunked in (0, 1):
+        capt_lib.capt_set_launch_cfg(tree, capt_lib.CAPT_KERNEL_SPHERES, 8, 2, 0, chunked, 0, 1)
+        assert np.array_equal(capt_lib.capt_query_spheres(tree, _cuda(torch_, c), _cuda(torch_, r)).cpu().numpy(), ref)
+    assert capt_lib.capt_device_status(tree) == 0

@@ -127,7 +127,7 @@ def test_compact_rejects_unuploaded_tree_without_gpu(capt_lib):
     assert L.capt_compact(None, 0, None) == -1
     st = capt_lib.capt_stats(t)
     assert st["compact_chunks"] == st["compact_entries"] == st["compact_bytes"] == st["full_dropped"] == 0
-    assert ctypes.sizeof(capt_lib._Stats) == 128                  # the C struct's size
+    assert ctypes.sizeof(capt_lib._Stats) == 144                  # the C struct's size
 
 
 def test_joint_and_filter_calls_reject_bad_arguments_without_gpu(capt_lib):
@@ -233,7 +233,8 @@ def test_binding_structs_match_the_c_header(capt_lib, tmp_path):
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    structs = {"capt_tree_stats": capt_lib._Stats, "capt_launch_cfg": capt_lib._LaunchCfg, "capt_arm": capt_lib._Arm}
+    structs = {"capt_tree_stats": capt_lib._Stats, "capt_launch_cfg": capt_lib._LaunchCfg, "capt_arm": capt_lib._Arm,
+               "capt_grid_info": capt_lib._GridInfo}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "capt.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
