@@ -347,13 +347,13 @@ def main():
     counts = capt.capt_count_config_work(tree, cen, r).cpu().numpy().astype(np.int64)
     L = capt.capt_stats(tree)["depth"]
     # FP32 operations per launch of the method as the kernel runs it: a root box test
-    # for every examined sphere (15), a descent and leaf box test for the near ones
+    # for every examined sphere (15), a grid lookup for the near ones when the grid is on
+    # (about 20), a descent and leaf box test for the near ones the grid leaves undecided
     # (L + 15), a box test per chunk walked (15) and 9 per point scanned in the chunks
-    # that pass; on-chip bytes likewise (12 per centre, 32 per leaf record, 4 per split,
-    # 32 per chunk box, 12 per point)
-    ops_per_launch = int(counts[0]) * 15 + int(counts[1]) * (L + 15) + int(counts[4]) * 15 + int(counts[5]) * 9
-    bytes_per_launch = (int(counts[0]) * 12 + int(counts[1]) * (32 + 4 * L) + int(counts[4]) * 32 +
-                        int(counts[5]) * 12)
+    # that pass; on-chip bytes likewise (12 per centre, 2 per grid cell, 32 per leaf
+    # record, 4 per split, 32 per chunk box, 12 per point)
+    ops_per_launch, bytes_per_launch = sphere_ops(counts, L, chunked=tuned["chunk"] != capt.CAPT_SCAN_SETS,
+                                                  in_bytes=12)
     # DRAM bytes the step must move: every centre once, the flags, the radii
     hbm_bytes = C * SPHERES * 12 + C + SPHERES * 4
 
@@ -421,7 +421,7 @@ def main():
                          "work": {"spheres_examined": int(counts[0]), "near_cloud_box": int(counts[1]),
                                   "leaf_box_pass": int(counts[2]), "chunk_boxes": int(counts[4]),
                                   "points_scanned": int(counts[5]), "points_scanned_alg3_alone": int(counts[3]),
-                                  "depth": L},
+                                  "grid_lookups": int(counts[6]), "decided_by_grid": int(counts[7]), "depth": L},
                          "l1_bytes_per_launch": bytes_per_launch,
                          "l1_frac": bytes_per_launch / (ms / 1e3) / (sms * 128 * SM_MAX_MHZ * 1e6)},
             "host": host,
@@ -548,17 +548,21 @@ def roof(ms, hbm_bytes, ops, l1_bytes, sms, note=None):
     return out
 
 
-def sphere_ops(counts, L, chunked=True):
+def sphere_ops(counts, L, chunked=True, in_bytes=16):
     """FP32 operations and on-chip bytes of a sphere query launch from its work counts:
     a root box test per sphere (15 ops, 16 bytes in), a descent and leaf box test per
     near sphere (L + 15 ops, 32 + 4 L bytes), then either the chunk walk (15 ops and 32
     bytes per chunk box, 9 ops and 12 bytes per point scanned) or Alg. 3's plain scan
     (9 ops and 12 bytes per point)."""
-    c = [int(x) for x in counts]
+    c = [int(x) for x in counts] + [0] * (8 - len(counts))
+    # with the distance-bound grid: a lookup (about 20 operations, 2 bytes) per sphere
+    # that reaches the cloud's box, and only the undecided ones descend
+    desc = c[1] - c[7]
+    ops = c[0] * 15 + c[6] * 20 + desc * (L + 15)
+    byt = c[0] * in_bytes + c[6] * 2 + desc * (32 + 4 * L)
     if chunked:
-        return (c[0] * 15 + c[1] * (L + 15) + c[4] * 15 + c[5] * 9,
-                c[0] * 16 + c[1] * (32 + 4 * L) + c[4] * 32 + c[5] * 12)
-    return c[0] * 15 + c[1] * (L + 15) + c[3] * 9, c[0] * 16 + c[1] * (32 + 4 * L) + c[3] * 12
+        return ops + c[4] * 15 + c[5] * 9, byt + c[4] * 32 + c[5] * 12
+    return ops + c[3] * 9, byt + c[3] * 12
 
 
 def bench_clearance(capt, torch, dev, stream, pts, arm, steps, sms):
@@ -582,10 +586,12 @@ def bench_clearance(capt, torch, dev, stream, pts, arm, steps, sms):
     fwd_ms = time_events(torch, lambda: capt.capt_clearance_fwd(ctree, c, r, 0.01, cost, d, am), steps, stream)
     bwd_ms = time_events(torch, lambda: capt.capt_clearance_bwd(ctree, c, r, d, am, g, 0.01, grad), steps, stream)
     m = T * Wn * SPHERES
-    counts = capt.capt_count_clearance_work(ctree, c).cpu().numpy().astype(np.int64)
+    counts = [int(x) for x in capt.capt_count_clearance_work(ctree, c).cpu().numpy()]
     L = capt.capt_stats(ctree)["depth"]
-    ops = int(counts[0]) * 15 + int(counts[1]) * (L + 15) + int(counts[3]) * 9
-    l1 = int(counts[0]) * 12 + int(counts[1]) * (32 + 4 * L) + int(counts[4]) * 48
+    # a box test per sphere, a descent and leaf box test per sphere near the cloud's box,
+    # 9 operations per point of the sets scanned in full (48 bytes per 4-point block)
+    ops = counts[0] * 15 + counts[1] * (L + 15) + counts[3] * 9
+    l1 = counts[0] * 12 + counts[1] * (32 + 4 * L) + counts[4] * 48
     fwd_bytes = m * (12 + 4 + 4) + T * 4          # centres in; distance and argmin out; cost
     bwd_bytes = m * (12 + 4 + 4 + 12) + T * 4      # centres, distance, argmin in; gradient out
     # parity sample: the first 8 trajectories against the oracle's FP64 nearest distance
@@ -596,9 +602,8 @@ def bench_clearance(capt, torch, dev, stream, pts, arm, steps, sms):
     return {"trajectories": T, "waypoints": Wn, "spheres": m, "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
             "fwd_spheres_per_s": m / (fwd_ms / 1e3), "fwd_bwd_spheres_per_s": m / ((fwd_ms + bwd_ms) / 1e3),
             "launch_cfg": capt.capt_get_launch_cfg(ctree, capt.CAPT_KERNEL_CLEARANCE),
-            "work": {"spheres": int(counts[0]), "near_cloud_box": int(counts[1]), "leaf_box_pass": int(counts[2]),
-                     "points_scanned": int(counts[3]), "blocks_scanned": int(counts[4]),
-                     "points_per_sphere": float(counts[3]) / m},
+            "work": {"spheres": counts[0], "near_cloud_box": counts[1], "leaf_box_pass": counts[2],
+                     "points_scanned": counts[3], "blocks_scanned": counts[4], "points_per_sphere": counts[3] / m},
             "roofline_fwd": roof(fwd_ms, fwd_bytes, ops, l1, sms),
             "roofline_bwd": roof(bwd_ms, bwd_bytes, m * 12, None, sms),
             "l2": "inputs larger than L2 (377 MB of centres)",
@@ -632,7 +637,8 @@ def bench_spheres(capt, torch, dev, stream, tree, c_host, r_host, steps, sms, pa
         ops, l1 = sphere_ops(counts, st["depth"], chunked=cfg["chunk"] != capt.CAPT_SCAN_SETS)
         out["work"] = {"spheres": int(counts[0]), "near_cloud_box": int(counts[1]), "leaf_box_pass": int(counts[2]),
                        "points_scanned_alg3": int(counts[3]), "chunk_boxes": int(counts[4]),
-                       "points_scanned_chunked": int(counts[5])}
+                       "points_scanned_chunked": int(counts[5]), "grid_lookups": int(counts[6]),
+                       "decided_by_grid": int(counts[7])}
         out["roofline"] = roof(ms, m * 17, ops, l1, sms)
     return out, got
 
@@ -643,6 +649,7 @@ def bench_uniform(capt, torch, dev, stream, steps, sms):
     cu, ru = W.cube_queries(100_000, 1000)
     tu = capt.capt_build(pu, 0.01, 0.08)
     capt.capt_upload(tu, dev.index)
+    capt.capt_build_grid(tu, 1 << 20)
     out, _ = bench_spheres(capt, torch, dev, stream, tu, cu, ru, steps, sms, 100_000, pu)
     out["roofline"]["note"] = ("one launch of ~10 us: launch and tail latency dominate; both floors are far "
                                "below the measured time")
@@ -658,9 +665,15 @@ def bench_room(capt, torch, dev, stream, steps, sms):
     build_ms = (time.perf_counter() - t0) * 1e3
     st = capt.capt_stats(tr)
     capt.capt_upload(tr, dev.index)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    capt.capt_build_grid(tr, GRID_CELLS)
+    grid_ms = (time.perf_counter() - t0) * 1e3
     cr, rr = W.room_queries(1 << 22, 1004)
     rep, f_rep = bench_spheres(capt, torch, dev, stream, tr, cr, rr, steps, sms, 8192, pr)
-    rep.update({"host_build_ms": build_ms, "host_build_threads": int(st["build_threads"]),
+    gst = capt.capt_stats(tr)
+    rep.update({"host_build_ms": build_ms, "host_build_threads": int(st["build_threads"]), "grid_build_ms": grid_ms,
+                "grid": {"dims": gst["grid_dims"], "cell_m": gst["grid_cell"]},
                 "total_afforded": int(st["total_afforded"]), "max_set": int(st["max_set"]),
                 "mean_set": st["total_afforded"] / st["n_leaves"]})
     torch.cuda.synchronize(dev)

@@ -301,7 +301,7 @@ int capt_query_configs_host(capt_tree* t, const float* h_centers, const float* h
                             uint8_t* h_flags, void* stream);
 
 /* Algorithmic work of capt_query_configs, counted sequentially per configuration (for
- * roofline accounting): d_counts device uint64[6] receives += [spheres examined (up to
+ * roofline accounting): d_counts (device uint64[8], below) receives += [spheres examined (up to
  * and including each configuration's first hit), spheres within reach of the cloud's
  * bounding box (these descend), spheres passing their leaf's box test (Alg. 3),
  * affordance points scanned by Alg. 3 alone (in stored order, up to and including the
@@ -309,13 +309,18 @@ int capt_query_configs_host(capt_tree* t, const float* h_centers, const float* h
  * reaches (up to and including the first hit)].  The query kernels do the work of
  * entries 0-2, 4 and 5; entry 3 is the plain method's scan for comparison.  The two
  * walks must find the same hits: a disagreement latches CAPT_E_BOUNDS in the device
- * status word.  The caller zeroes d_counts.  Errors as capt_query_configs. */
+ * status word.  When the tree's configuration launch has grid = 1 (capt_build_grid),
+ * the counts follow that path and d_counts holds two more entries: [6] grid lookups
+ * (spheres that reach the cloud's box), [7] spheres the grid decides (a certain miss
+ * needs nothing more; a certain hit ends its configuration); only the undecided
+ * descend.  d_counts: device uint64[8].  The caller zeroes d_counts.  Errors as
+ * capt_query_configs. */
 int capt_count_config_work(const capt_tree* t, const float* d_centers, const float* d_radii, size_t C, int S,
                            uint64_t* d_counts, void* stream);
 
 /* capt_count_config_work for capt_query_spheres: m spheres with their own radii
- * (d_radii device float[m]), each counted as a configuration of one sphere; the same six
- * counters. */
+ * (d_radii device float[m]), each counted as a configuration of one sphere; the same
+ * eight counters (the grid's when the tree's sphere launch has grid = 1). */
 int capt_count_sphere_work(const capt_tree* t, const float* d_centers, const float* d_radii, size_t m,
                            uint64_t* d_counts, void* stream);
 

@@ -415,7 +415,7 @@ def capt_count_config_work(tree: CaptTree, centers, radii, stream=None):
     if centers.dim() != 3 or centers.shape[2] != 3 or radii.shape != (centers.shape[1],):
         raise ValueError("centers must be [C, S, 3] and radii [S]")
     Cn, S = centers.shape[0], centers.shape[1]
-    counts = torch.zeros(6, dtype=torch.int64, device=centers.device)
+    counts = torch.zeros(8, dtype=torch.int64, device=centers.device)
     _check(_load().capt_count_config_work(tree.h, _dev(centers, torch.float32, "centers"),
                                           _dev(radii, torch.float32, "radii"), Cn, S,
                                           _dev(counts, torch.int64, "counts"), _stream(stream)),
@@ -424,12 +424,12 @@ def capt_count_config_work(tree: CaptTree, centers, radii, stream=None):
 
 
 def capt_count_sphere_work(tree: CaptTree, centers, radii, stream=None):
-    """The six work counters of capt_count_config_work for sphere queries [m, 3] with
+    """The eight work counters of capt_count_config_work for sphere queries [m, 3] with
     radii [m]."""
     import torch
     if centers.dim() != 2 or centers.shape[1] != 3 or radii.shape != (centers.shape[0],):
         raise ValueError("centers must be [m, 3] and radii [m]")
-    counts = torch.zeros(6, dtype=torch.int64, device=centers.device)
+    counts = torch.zeros(8, dtype=torch.int64, device=centers.device)
     _check(_load().capt_count_sphere_work(tree.h, _dev(centers, torch.float32, "centers"),
                                           _dev(radii, torch.float32, "radii"), centers.shape[0],
                                           _dev(counts, torch.int64, "counts"), _stream(stream)),

@@ -893,8 +893,8 @@ int capt_count_config_work(const capt_tree* t, const float* d_centers, const flo
     if (C == 0) return CAPT_OK;
     if (!d_centers || !d_radii || !d_counts) return fail(CAPT_E_ARG, "NULL device pointer");
     std::string err;
-    rc = capt::launch_count_configs(t->args(), d_centers, d_radii, C, S, false, d_counts,
-                                    static_cast<cudaStream_t>(stream), err);
+    rc = capt::launch_count_configs(t->args(), d_centers, d_radii, C, S, false, t->cfg[CAPT_KERNEL_CONFIGS].grid != 0,
+                                    d_counts, static_cast<cudaStream_t>(stream), err);
     return rc ? fail(rc, err) : CAPT_OK;
 }
 
@@ -905,8 +905,8 @@ int capt_count_sphere_work(const capt_tree* t, const float* d_centers, const flo
     if (m == 0) return CAPT_OK;
     if (!d_centers || !d_radii || !d_counts) return fail(CAPT_E_ARG, "NULL device pointer");
     std::string err;
-    rc = capt::launch_count_configs(t->args(), d_centers, d_radii, m, 1, true, d_counts,
-                                    static_cast<cudaStream_t>(stream), err);
+    rc = capt::launch_count_configs(t->args(), d_centers, d_radii, m, 1, true, t->cfg[CAPT_KERNEL_SPHERES].grid != 0,
+                                    d_counts, static_cast<cudaStream_t>(stream), err);
     return rc ? fail(rc, err) : CAPT_OK;
 }
 

@@ -20,7 +20,7 @@ int launch_query(const DevArgs& t, int mode, const float* centers, const float* 
 
 // Sequential Alg. 3 work counters for configuration queries.
 int launch_count_configs(const DevArgs& t, const float* centers, const float* radii, uint64_t C, int S, bool per_sphere,
-                         uint64_t* counts, cudaStream_t st, std::string& err);
+                         bool use_grid, uint64_t* counts, cudaStream_t st, std::string& err);
 
 // Boxes of the chunks of kChunkBlocks blocks (cbox: 8 floats per chunk, chunk_count).
 int launch_chunk_boxes(const float* blocks, uint64_t total_blocks, float* cbox, cudaStream_t st, std::string& err);

@@ -654,10 +654,13 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs_grid(DevArgs t,
 // With per_sphere, radii holds one radius per sphere (C x S of them) instead of one per
 // sphere slot of a configuration (S); sphere queries are counted as configurations of
 // one sphere with their own radii.
+// With use_grid, a sphere that reaches the cloud's box is first classified by the
+// distance-bound grid (counts[6] lookups, counts[7] decided there: a certain miss needs
+// nothing more, a certain hit ends its configuration); only the undecided descend.
 __global__ void k_count_configs(DevArgs t, const float* __restrict__ centers, const float* __restrict__ radii,
-                                uint64_t C, int S, bool per_sphere, unsigned long long* counts) {
+                                uint64_t C, int S, bool per_sphere, bool use_grid, unsigned long long* counts) {
     const uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long nsph = 0, nnear = 0, npass = 0, npts = 0, nbox = 0, ncpts = 0;
+    unsigned long long nsph = 0, nnear = 0, npass = 0, npts = 0, nbox = 0, ncpts = 0, ngl = 0, ngd = 0;
     const float4* cbox = reinterpret_cast<const float4*>(t.cbox);
     const float4 rlo = make_float4(t.lo[0], t.lo[1], t.lo[2], 0.f);
     const float4 rhi = make_float4(t.hi[0], t.hi[1], t.hi[2], 0.f);
@@ -668,6 +671,13 @@ __global__ void k_count_configs(DevArgs t, const float* __restrict__ centers, co
             nsph++;
             if (!(box_dist2(x[0], x[1], x[2], rlo, rhi) <= r2)) continue;
             nnear++;
+            if (use_grid) {
+                ngl++;
+                const int cls = grid_classify(t, x[0], x[1], x[2], r);
+                if (cls != 2) ngd++;
+                if (cls == 0) continue;
+                if (cls == 1) break;
+            }
             const uint32_t leaf = descend(x[0], x[1], x[2], t, nullptr);
             float4 a, b;
             load_leaf(t.leaves, leaf, a, b);
@@ -707,6 +717,8 @@ __global__ void k_count_configs(DevArgs t, const float* __restrict__ centers, co
         npts += __shfl_xor_sync(0xffffffffu, npts, o);
         nbox += __shfl_xor_sync(0xffffffffu, nbox, o);
         ncpts += __shfl_xor_sync(0xffffffffu, ncpts, o);
+        ngl += __shfl_xor_sync(0xffffffffu, ngl, o);
+        ngd += __shfl_xor_sync(0xffffffffu, ngd, o);
     }
     if ((threadIdx.x & 31) == 0 && nsph) {
         atomicAdd(counts, nsph);
@@ -715,6 +727,8 @@ __global__ void k_count_configs(DevArgs t, const float* __restrict__ centers, co
         atomicAdd(counts + 3, npts);
         atomicAdd(counts + 4, nbox);
         atomicAdd(counts + 5, ncpts);
+        atomicAdd(counts + 6, ngl);
+        atomicAdd(counts + 7, ngd);
     }
 }
 
@@ -931,11 +945,11 @@ int launch_query(const DevArgs& t, int mode, const float* centers, const float* 
 }
 
 int launch_count_configs(const DevArgs& t, const float* centers, const float* radii, uint64_t C, int S,
-                         bool per_sphere, uint64_t* counts, cudaStream_t st, std::string& err) {
+                         bool per_sphere, bool use_grid, uint64_t* counts, cudaStream_t st, std::string& err) {
     if (C == 0) return CAPT_OK;
     const unsigned threads = 256;
     k_count_configs<<<(unsigned)((C + threads - 1) / threads), threads, 0, st>>>(
-        t, centers, radii, C, S, per_sphere, reinterpret_cast<unsigned long long*>(counts));
+        t, centers, radii, C, S, per_sphere, use_grid && t.grid, reinterpret_cast<unsigned long long*>(counts));
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) { err = std::string("count launch: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
     return CAPT_OK;

@@ -210,7 +210,17 @@ def test_sphere_work_counters_match_oracle(uniform2k, orc, capt_lib, torch_):
     assert g[2] == int((ms > 0).sum())
     assert g[3] == int(ms.sum())
     assert g[5] <= g[3] and g[4] >= g[2]
-    assert capt_lib.capt_device_status(uniform2k["tree"]) == 0
+    assert g[6] == g[7] == 0
+    # with the grid every sphere that reaches the cloud's box is looked up, and the
+    # decided ones never descend
+    t = uniform2k["tree"]
+    capt_lib.capt_build_grid(t, 1 << 16)
+    capt_lib.capt_set_launch_cfg(t, capt_lib.CAPT_KERNEL_SPHERES, 8, 2, 1, 0, 0, 1)
+    h = capt_lib.capt_count_sphere_work(t, uniform2k["dc"], uniform2k["dr"]).cpu().numpy()
+    capt_lib.capt_set_launch_cfg(t, capt_lib.CAPT_KERNEL_SPHERES, 8, 2, 1, 0)
+    assert h[0] == g[0] and h[1] == g[1] and h[6] == g[1]
+    assert 0 < h[7] <= h[6] and h[2] <= g[2] and h[3] <= g[3]
+    assert capt_lib.capt_device_status(t) == 0
 
 
 def test_clearance_work_counters_match_oracle_tree(tabletop, orc, capt_lib, torch_):
