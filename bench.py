@@ -57,6 +57,84 @@ def hbm_peak():
         return HBM_FALLBACK_GBS, "fallback (no MEASURED_PEAKS.json)"
 
 
+# Profiling mode (--profile NAME): the workload, its kernel and the fixed launch
+# configuration used (warps per block, spheres per lane, staging, scan, prefetch, grid).
+PROFILES = {
+    "configs": ("tabletop, 1,048,576 configurations x 60 spheres, grid of 2^24 cells", "k_configs_grid",
+                (16, 16, 0, 0, 0, 1)),
+    "configs_nogrid": ("tabletop, 1,048,576 configurations x 60 spheres, no grid", "k_configs", (4, 4, 0, 1, 0, 0)),
+    "room": ("room, 200,000 points, 4,194,304 spheres, grid of 2^24 cells", "k_spheres", (8, 2, 0, 0, 0, 1)),
+    "clearance": ("tabletop, 16,384 x 32 x 60 spheres, r_min = 0", "k_clearance_dist", (16, 2, 0, 0, 0, 0)),
+    "edges": ("tabletop, 4,096 edges (1,038,247 configurations)", "k_edges_persistent", (8, 1, 0, 32, 0, 0)),
+    "joints": ("tabletop, 1,048,576 configurations by joint angles", "k_joint_configs", (16, 1, 0, 0, 0, 0)),
+}
+
+
+def run_profile(args):
+    """Set up one workload, then launch only the kernel under study: --warmup launches,
+    then --steps launches (an ncu capture skips the first with -s and takes one with -c)."""
+    import torch
+    import paper_2406_02807_gb300 as capt
+    capt.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    _, _, cfg = PROFILES[args.profile]
+    name = args.profile
+    if name == "room":
+        pr = W.room_cloud(1004)
+        tree = capt.capt_build(pr, 0.02, 0.10)
+        capt.capt_upload(tree, 0)
+        capt.capt_build_grid(tree, GRID_CELLS)
+        cr, rr = W.room_queries(1 << 22, 1004)
+        dc, dr = torch.from_numpy(cr).to(dev), torch.from_numpy(rr).to(dev)
+        f = torch.empty(1 << 22, dtype=torch.uint8, device=dev)
+        capt.capt_set_launch_cfg(tree, capt.CAPT_KERNEL_SPHERES, *cfg)
+        step = lambda: capt.capt_query_spheres(tree, dc, dr, f)   # noqa: E731
+    else:
+        raw, _, arm = W.tabletop_scene(1001)
+        pts = raw[capt.sfc_filter(raw, R_FILTER)]
+        if name == "clearance":
+            tree = capt.capt_build(pts, 0.0, R_MAX)
+            capt.capt_upload(tree, 0)
+            q = W.random_trajectories(16384, 32, 1003)
+            c = torch.from_numpy(W.fk_centers(arm, q.reshape(-1, 7)).reshape(16384, 32, SPHERES, 3)).to(dev)
+            r = torch.from_numpy(arm.sphere_radius.copy()).to(dev)
+            capt.capt_set_launch_cfg(tree, capt.CAPT_KERNEL_CLEARANCE, *cfg)
+            cost = torch.empty(16384, dtype=torch.float32, device=dev)
+            d = torch.empty((16384, 32, SPHERES), dtype=torch.float32, device=dev)
+            am = torch.empty((16384, 32, SPHERES), dtype=torch.int32, device=dev)
+            step = lambda: capt.capt_clearance_fwd(tree, c, r, 0.01, cost, d, am)   # noqa: E731
+        else:
+            tree = capt.capt_build(pts, R_MIN, R_MAX)
+            capt.capt_upload(tree, 0)
+            if name == "edges":
+                qa, qb, ns = W.random_edges(4096, 1002)
+                dqa, dqb, dns = (torch.from_numpy(a).to(dev) for a in (qa, qb, ns))
+                v = torch.empty(4096, dtype=torch.uint8, device=dev)
+                capt.capt_set_launch_cfg(tree, capt.CAPT_KERNEL_EDGES, *cfg)
+                step = lambda: capt.capt_validate_edges(tree, arm, dqa, dqb, dns, v)   # noqa: E731
+            elif name == "joints":
+                dq = torch.from_numpy(W.random_configs(1 << 20, 1001)).to(dev)
+                f = torch.empty(1 << 20, dtype=torch.uint8, device=dev)
+                capt.capt_set_launch_cfg(tree, capt.CAPT_KERNEL_JOINTS, *cfg)
+                step = lambda: capt.capt_query_joint_configs(tree, arm, dq, f)   # noqa: E731
+            else:
+                if cfg[5]:
+                    capt.capt_build_grid(tree, GRID_CELLS)
+                cen = torch.from_numpy(W.fk_centers(arm, W.random_configs(1 << 20, 1001))).to(dev)
+                r = torch.from_numpy(arm.sphere_radius.copy()).to(dev)
+                f = torch.empty(1 << 20, dtype=torch.uint8, device=dev)
+                capt.capt_set_launch_cfg(tree, capt.CAPT_KERNEL_CONFIGS, *cfg)
+                step = lambda: capt.capt_query_configs(tree, cen, r, f)   # noqa: E731
+    torch.cuda.synchronize()
+    for _ in range(args.warmup + args.steps):
+        step()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": name, "workload": PROFILES[name][0], "kernel": PROFILES[name][1],
+                      "launch_cfg": list(cfg), "launches": args.warmup + args.steps,
+                      "device_status": capt.capt_device_status(tree)}), flush=True)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -70,6 +148,9 @@ def parse():
                     help="skip the clearance, room and uniform-cloud workloads of the default run")
     ap.add_argument("--headline-only", action="store_true",
                     help="time only the configuration query (for profiling); the JSON line lacks e2e and the rest")
+    ap.add_argument("--profile", choices=sorted(PROFILES),
+                    help="for ncu: set up one workload, then launch only its kernel, --warmup times and then "
+                         "--steps times, with the fixed launch configuration listed in PROFILES")
     return ap.parse_args()
 
 
@@ -307,6 +388,9 @@ def run_reference(args, rank, world):
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
+    if args.profile:
+        run_profile(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
@@ -383,7 +467,7 @@ def main():
     collide = float(flags.float().mean().item())
     flags_host = flags[:PARITY_SAMPLE].cpu().numpy()
 
-    sec = None if args.headline_only else secondary(capt, torch, dev, stream, tree, arm, q, cen_host, r_host,
+    sec = None if args.headline_only else secondary(capt, torch, dev, stream, tree, arm, q, cen, cen_host, r_host,
                                                     flags, C, args, pg)
 
     out = None
@@ -453,7 +537,7 @@ def main():
         pg.destroy_process_group()
 
 
-def secondary(capt, torch, dev, stream, tree, arm, q, cen_host, r_host, flags, C, args, pg):
+def secondary(capt, torch, dev, stream, tree, arm, q, cen, cen_host, r_host, flags, C, args, pg):
     """The host-buffer (e2e) run of the headline, edges (persistent graph vs per edge)
     and the joint-angle configuration query, as extra keys of the JSON line."""
     from paper_2406_02807_gb300.shard import max_over_ranks
@@ -472,6 +556,21 @@ def secondary(capt, torch, dev, stream, tree, arm, q, cen_host, r_host, flags, C
     if pg:
         e2e_s = max_over_ranks(e2e_s, pg, dev)
     e2e_ok = bool(torch.equal(h_flags, flags.cpu()))
+    # the host link's ceiling on this machine: plain page-locked copies of the same centres
+    # (one NUMA node holds every host core and the GPU's affinity here)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    link = {}
+    for name, fn in (("h2d", lambda: cen.copy_(cen_host, non_blocking=True)),
+                     ("d2h", lambda: cen_host.copy_(cen, non_blocking=True))):
+        fn()
+        best = 0.0
+        for _ in range(3):
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            best = max(best, cen_host.numel() * 4 / (e0.elapsed_time(e1) / 1e3) / 1e9)
+        link[name + "_GBps"] = best
 
     # batched edge validation: persistent graph launch vs one launch per edge
     qa, qb, ns = W.random_edges(4096, 1002)
@@ -512,7 +611,9 @@ def secondary(capt, torch, dev, stream, tree, arm, q, cen_host, r_host, flags, C
     return {
         "e2e": {"value": world * C * SPHERES / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": C * SPHERES * 12 + SPHERES * 4, "d2h_bytes_per_step": C,
-                "flags_equal_device_path": e2e_ok},
+                "flags_equal_device_path": e2e_ok,
+                "link": dict(link, frac_of_h2d=(C * SPHERES * 12 / e2e_s / 1e9) / max(link["h2d_GBps"], 1e-9),
+                             note="plain page-locked copies of the same 755 MB of centres, best of 3")},
         "edges": {"edges": 4096, "configs": int(ns.sum()), "persistent_graph_ms": edge_ms,
                   "edges_per_s_persistent": 4096 / (edge_ms / 1e3), "per_edge_launch_ms": per_edge_ms,
                   "edges_per_s_per_edge": 4096 / (per_edge_ms / 1e3), "valid_fraction": float(valid2.float().mean()),

@@ -370,3 +370,14 @@ def test_edges_tree_equals_brute_force(orc):
     ns0 = ns.copy()
     ns0[:4] = 0
     assert orc.edges(arm, qa, qb, ns0, tree=t)[:4].tolist() == [1, 1, 1, 1]
+
+
+@pytest.mark.parametrize("case", [t for t in GOLD["trees"] if "config_queries" in t], ids=lambda t: t["name"])
+def test_capt_hand_derived_work_counts(orc, case):
+    """The oracle's Alg. 3 work counts (spheres examined up to each configuration's first
+    hit, leaf box passes, points scanned up to the first hit), worked out by hand."""
+    t = orc.PlainCAPT(np.array(case["points"], np.float32), case["r_min"], case["r_max"])
+    q = case["config_queries"]
+    flags, counts = t.query_configs(np.array(q["centers"], np.float32), np.array(q["radii"], np.float32))
+    assert flags.tolist() == q["flags"]
+    assert counts.tolist() == q["counts"]
