@@ -361,13 +361,14 @@ typedef struct capt_launch_cfg {
                                   test hit L2.  Clearance: the same per block, a
                                   trajectory k x (resident blocks) ahead.  0 = none.  Other
                                   kernels: must be 0. */
-    int32_t grid;              /* configurations and spheres: 1 = test each sphere that reaches the
-                                  cloud's bounding box against the tree's distance-bound
-                                  grid (staged in shared memory) before it is queued for a
-                                  descent; exact (a cell stores a rounded-down lower bound
-                                  of the distance from the cell to the cloud), it only
-                                  removes spheres that cannot hit.  0 = descend for every
-                                  such sphere.  Other kernels: must be 0. */
+    int32_t grid;              /* sphere, configuration, edge and joint-angle queries:
+                                  1 = classify each sphere that reaches the cloud's
+                                  bounding box by the tree's distance-bound grid
+                                  (capt_build_grid) before any descent: a certain miss is
+                                  dropped, a certain hit decides its sphere, configuration
+                                  or edge at once, only the undecided descend.  Exact (the
+                                  flags do not change).  Ignored while the tree has no
+                                  grid.  Clearance: must be 0. */
 } capt_launch_cfg;
 #define CAPT_MAX_PREFETCH 4
 

@@ -58,7 +58,7 @@ bool valid_cfg(int kernel, const capt_launch_cfg& c) {
     if (c.prefetch < 0 || c.prefetch > CAPT_MAX_PREFETCH) return false;
     if (c.prefetch != 0 && kernel != CAPT_KERNEL_CONFIGS && kernel != CAPT_KERNEL_CLEARANCE) return false;
     if (c.grid != 0 && c.grid != 1) return false;
-    if (c.grid != 0 && kernel != CAPT_KERNEL_CONFIGS && kernel != CAPT_KERNEL_SPHERES) return false;
+    if (c.grid != 0 && kernel == CAPT_KERNEL_CLEARANCE) return false;
     const int spl = c.spheres_per_lane;
     const bool scan_mode = c.chunk >= CAPT_SCAN_SETS && c.chunk <= CAPT_SCAN_COMPACT;
     if (kernel == CAPT_KERNEL_SPHERES) return (spl == 1 || spl == 2 || spl == 4 || spl == 8) && scan_mode;
@@ -1140,8 +1140,10 @@ int capt_autotune_joint_configs(capt_tree* t, const capt_arm* arm, const float* 
     capt_launch_cfg best_c = t->cfg[CAPT_KERNEL_JOINTS];
     std::string err;
     for (int warps : {2, 4, 8, 16})
-        for (int stage : {CAPT_STAGE_GLOBAL, CAPT_STAGE_SMEM}) {
-            capt_launch_cfg c = {warps, 1, stage, 0};
+        for (int stage : {CAPT_STAGE_GLOBAL, CAPT_STAGE_SMEM})
+            for (int grid : {0, 1}) {
+            if (grid && !t->d_grid) continue;
+            capt_launch_cfg c = {warps, 1, stage, 0, 0, grid};
             float tt = INFINITY;
             for (int rep = 0; rep < 3; rep++) {
                 cudaEventRecord(e0, st);
@@ -1217,8 +1219,10 @@ int capt_edge_plan_create(capt_tree* t, const capt_arm* arm, const float* d_qa, 
         capt_launch_cfg bc = t->cfg[CAPT_KERNEL_EDGES];
         for (int warps : {4, 8, 16})
             for (int stage : {CAPT_STAGE_GLOBAL, CAPT_STAGE_SMEM})
-                for (int chunk : {32, 64, 128}) {
-                        capt_launch_cfg c = {warps, 1, stage, chunk};
+                for (int chunk : {32, 64, 128})
+                    for (int grid : {0, 1}) {
+                        if (grid && !t->d_grid) continue;
+                        capt_launch_cfg c = {warps, 1, stage, chunk, 0, grid};
                         float tt = INFINITY;
                         for (int rep = 0; rep < 3 && !rc; rep++) {
                             cudaEventRecord(e0, st);

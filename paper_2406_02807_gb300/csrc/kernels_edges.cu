@@ -38,6 +38,7 @@ struct ArmPlan {
     int32_t sbeg[CAPT_MAX_JOINTS + 1];   // spheres of link j: [sbeg[j], sbeg[j + 1])
     float off[CAPT_MAX_SPHERES][3];      // offsets in the link frame, in that order
     float r2[CAPT_MAX_SPHERES];          // fl(r * r), in that order
+    float rr[CAPT_MAX_SPHERES];          // r, in that order (for the distance-bound grid)
     // per link: a bounding sphere of its spheres (centre offset in the link frame) and
     // the squared box distance beyond which none of them can reach the cloud's box
     float cull_o[CAPT_MAX_JOINTS][3];
@@ -61,6 +62,7 @@ ArmPlan make_plan(const capt_arm& a) {
             if (a.sphere_link[s] == j) {
                 for (int d = 0; d < 3; d++) p.off[n][d] = a.sphere_offset[s][d];
                 p.r2[n] = a.sphere_radius[s] * a.sphere_radius[s];
+                p.rr[n] = a.sphere_radius[s];
                 n++;
             }
     }
@@ -190,14 +192,53 @@ __device__ __forceinline__ void link_point(const float R[9], const float p[3], f
 }
 
 struct EdgeScratch {
-    float4 nc[64];   // queued near spheres (< 32 left over + 32 from one sphere step)
+    float4 nc[64];   // queued near spheres (< 32 left over + 32 from one sphere step);
+                     // with the grid: centre and r, awaiting classification
+    float4 rq[64];   // with the grid: the undecided ones, centre and r^2
     RoundEntries re;
 };
+
+// With the distance-bound grid: classify the first n queued spheres of an edge pass by
+// their cells (dist_grid.cu).  Returns true when one of them certainly collides (the
+// edge is invalid); the undecided ones join the rest queue (a round runs once it holds
+// 32), the others are dropped; the rest of the queue moves to the front.
+template <int MODE>
+__device__ __forceinline__ bool edge_grid_step(const DevArgs& t, const float* Ts, EdgeScratch* ws, uint32_t n,
+                                               uint32_t& n_near, uint32_t& n_rest, uint32_t lane,
+                                               uint32_t lt_mask) {
+    const bool live = lane < n;
+    float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+    int cls = 0;
+    if (live) {
+        c = ws->nc[lane];
+        cls = grid_classify(t, c.x, c.y, c.z, c.w);
+    }
+    if (__any_sync(0xffffffffu, cls == 1)) return true;
+    const uint32_t km = __ballot_sync(0xffffffffu, cls == 2);
+    if (cls == 2) ws->rq[n_rest + __popc(km & lt_mask)] = make_float4(c.x, c.y, c.z, __fmul_rn(c.w, c.w));
+    n_rest += __popc(km);
+    const bool mv = lane + n < n_near;
+    const float4 cc = mv ? ws->nc[lane + n] : make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncwarp();
+    if (mv) ws->nc[lane] = cc;
+    n_near -= n;
+    __syncwarp();
+    if (n_rest >= 32) {
+        if (sphere_round<true, MODE>(t, Ts, &ws->re, nullptr, ws->rq[lane], 0, true, lane, lt_mask)) return true;
+        const bool mr = lane + 32 < n_rest;
+        const float4 cr = mr ? ws->rq[lane + 32] : make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncwarp();
+        if (mr) ws->rq[lane] = cr;
+        n_rest -= 32;
+        __syncwarp();
+    }
+    return false;
+}
 
 // One pass: configurations k0 + stride * i, i = 0 .. count - 1 (count <= 32), of the
 // edge with n_e configurations from qa_e to qb_e, lane i taking the i-th.  Returns true
 // as soon as one of them collides.
-template <int MODE>
+template <int MODE, bool GRID>
 __device__ bool edge_pass(const DevArgs& t, const ArmPlan& arm, const float* __restrict__ qa_e,
                           const float* __restrict__ qb_e, int n_e, int k0, int stride, int count, const float* Ts,
                           EdgeScratch* ws) {
@@ -210,7 +251,7 @@ __device__ bool edge_pass(const DevArgs& t, const ArmPlan& arm, const float* __r
     const float tk = n_e > 1 ? __fdiv_rn((float)(k0 + stride * (int)lane), (float)(n_e - 1)) : 0.f;
     float R[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
     float p[3] = {arm.base[0], arm.base[1], arm.base[2]};
-    uint32_t n_near = 0;
+    uint32_t n_near = 0, n_rest = 0;
     for (int j = 0; j < arm.J; j++) {
         const float a = __ldg(qa_e + j), b = __ldg(qb_e + j);
         const float q = __fadd_rn(a, __fmul_rn(tk, __fsub_rn(b, a)));
@@ -234,9 +275,12 @@ __device__ bool edge_pass(const DevArgs& t, const ArmPlan& arm, const float* __r
             const float r2 = arm.r2[i];
             const bool near = live && box_dist2(cx, cy, cz, rlo, rhi) <= r2;
             const uint32_t mask = __ballot_sync(0xffffffffu, near);
-            if (near) ws->nc[n_near + __popc(mask & lt_mask)] = make_float4(cx, cy, cz, r2);
+            if (near) ws->nc[n_near + __popc(mask & lt_mask)] = make_float4(cx, cy, cz, GRID ? arm.rr[i] : r2);
             n_near += __popc(mask);
-            if (n_near >= 32) {
+            if (GRID && n_near >= 32) {
+                __syncwarp();
+                if (edge_grid_step<MODE>(t, Ts, ws, 32, n_near, n_rest, lane, lt_mask)) return true;
+            } else if (n_near >= 32) {
                 __syncwarp();
                 if (sphere_round<true, MODE>(t, Ts, &ws->re, nullptr, ws->nc[lane], 0, true, lane, lt_mask)) return true;
                 const uint32_t rest = n_near - 32;
@@ -255,6 +299,14 @@ __device__ bool edge_pass(const DevArgs& t, const ArmPlan& arm, const float* __r
         p[0] = __fadd_rn(p[0], tx);
         p[1] = __fadd_rn(p[1], ty);
         p[2] = __fadd_rn(p[2], tz);
+    }
+    if constexpr (GRID) {
+        __syncwarp();
+        if (n_near && edge_grid_step<MODE>(t, Ts, ws, n_near, n_near, n_rest, lane, lt_mask)) return true;
+        if (n_rest == 0) return false;
+        const bool in_rest = lane < n_rest;
+        const float4 c = in_rest ? ws->rq[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        return sphere_round<true, MODE>(t, Ts, &ws->re, nullptr, c, 0, in_rest, lane, lt_mask);
     }
     if (n_near == 0) return false;
     __syncwarp();
@@ -328,7 +380,7 @@ __global__ void k_edges_setup(const int32_t* __restrict__ ns, uint32_t E, uint32
     }
 }
 
-template <bool STAGE, int MODE>
+template <bool STAGE, int MODE, bool GRID>
 __global__ void __launch_bounds__(512, 2) k_edges_persistent(DevArgs t, const __grid_constant__ ArmPlan arm,
                                                              const float* __restrict__ qa, const float* __restrict__ qb,
                                                              const int32_t* __restrict__ ns, uint32_t E, uint32_t chunk,
@@ -370,7 +422,7 @@ __global__ void __launch_bounds__(512, 2) k_edges_persistent(DevArgs t, const __
         const float* qa_e = qa + (size_t)e * J;
         const float* qb_e = qb + (size_t)e * J;
         for (int j = 0; j < cnt; j += 32) {
-            if (edge_pass<MODE>(t, arm, qa_e, qb_e, n_e, ci + nci * j, nci, min(32, cnt - j), Ts, ws)) {
+            if (edge_pass<MODE, GRID>(t, arm, qa_e, qb_e, n_e, ci + nci * j, nci, min(32, cnt - j), Ts, ws)) {
                 if (lane == 0) valid[e] = 0;
                 break;
             }
@@ -380,7 +432,7 @@ __global__ void __launch_bounds__(512, 2) k_edges_persistent(DevArgs t, const __
 }
 
 // One edge per launch (the per-edge baseline): warps stride over its configurations.
-template <int MODE>
+template <int MODE, bool GRID>
 __global__ void __launch_bounds__(512, 2) k_edge_single(DevArgs t, const __grid_constant__ ArmPlan arm,
                                                         const float* __restrict__ qa_e, const float* __restrict__ qb_e,
                                                         int n_e, uint8_t* valid_e) {
@@ -390,7 +442,7 @@ __global__ void __launch_bounds__(512, 2) k_edge_single(DevArgs t, const __grid_
     const int gw = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
     for (int64_t k = (int64_t)gw * 32; k < n_e; k += (int64_t)warps * 32) {
         if (load_volatile_u8(valid_e) == 0) break;
-        if (edge_pass<MODE>(t, arm, qa_e, qb_e, n_e, (int)k, 1, (int)min((int64_t)32, n_e - k), nullptr, ws)) {
+        if (edge_pass<MODE, GRID>(t, arm, qa_e, qb_e, n_e, (int)k, 1, (int)min((int64_t)32, n_e - k), nullptr, ws)) {
             if (lane_id() == 0) *valid_e = 0;
             break;
         }
@@ -403,13 +455,16 @@ __global__ void __launch_bounds__(512, 2) k_edge_single(DevArgs t, const __grid_
 // resolves its own configuration only; the others of the pass go on).
 // ------------------------------------------------------------------------------------
 struct JointScratch {
-    float4 nc[64];     // queued near spheres: centre and r^2 (< 32 left over + 32 new)
+    float4 nc[64];     // queued near spheres: centre and r^2 (< 32 left over + 32 new);
+                       // with the grid: centre and r, awaiting classification
     uint32_t ng[64];   // their configuration (lane of the pass)
+    float4 rq[64];     // with the grid: the undecided ones, centre and r^2
+    uint32_t rg[64];   // their configuration
     uint32_t ghit[32]; // per configuration of the pass: 1 once it collides
     RoundEntries re;
 };
 
-template <bool STAGE, int MODE>
+template <bool STAGE, int MODE, bool GRID>
 __global__ void __launch_bounds__(512, 2) k_joint_configs(DevArgs t, const __grid_constant__ ArmPlan arm,
                                                           const float* __restrict__ q, uint64_t C,
                                                           uint8_t* __restrict__ out, unsigned long long* ctr) {
@@ -434,6 +489,56 @@ __global__ void __launch_bounds__(512, 2) k_joint_configs(DevArgs t, const __gri
         const float4 c = in_queue ? ws->nc[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
         const uint32_t g = in_queue ? ws->ng[lane] : 0u;
         sphere_round<false, MODE>(t, Ts, &ws->re, ws->ghit, c, g, in_queue, lane, lt_mask);
+    };
+    // with the grid: a round over the first n undecided spheres, the rest to the front
+    uint32_t n_rest = 0;
+    auto rest_round = [&](uint32_t n) {
+        const bool in_queue = lane < n;
+        const float4 c = in_queue ? ws->rq[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const uint32_t g = in_queue ? ws->rg[lane] : 0u;
+        sphere_round<false, MODE>(t, Ts, &ws->re, ws->ghit, c, g, in_queue, lane, lt_mask);
+        const bool mv = lane + n < n_rest;
+        const float4 cc = mv ? ws->rq[lane + n] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const uint32_t gg = mv ? ws->rg[lane + n] : 0u;
+        __syncwarp();
+        if (mv) {
+            ws->rq[lane] = cc;
+            ws->rg[lane] = gg;
+        }
+        n_rest -= n;
+        __syncwarp();
+    };
+    // with the grid: classify the first n queued spheres by their cells; a certain hit
+    // resolves its configuration, a certain miss is dropped, the undecided join the rest
+    auto classify = [&](uint32_t n, uint32_t& n_near) {
+        const bool live = lane < n;
+        float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+        uint32_t g = 0;
+        int cls = 0;
+        if (live) {
+            c = ws->nc[lane];
+            g = ws->ng[lane];
+            if (!ws->ghit[g]) cls = grid_classify(t, c.x, c.y, c.z, c.w);
+        }
+        if (cls == 1) ws->ghit[g] = 1;
+        const uint32_t km = __ballot_sync(0xffffffffu, cls == 2);
+        if (cls == 2) {
+            const uint32_t pos = n_rest + __popc(km & lt_mask);
+            ws->rq[pos] = make_float4(c.x, c.y, c.z, __fmul_rn(c.w, c.w));
+            ws->rg[pos] = g;
+        }
+        n_rest += __popc(km);
+        const bool mv = lane + n < n_near;
+        const float4 cc = mv ? ws->nc[lane + n] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const uint32_t gg = mv ? ws->ng[lane + n] : 0u;
+        __syncwarp();
+        if (mv) {
+            ws->nc[lane] = cc;
+            ws->ng[lane] = gg;
+        }
+        n_near -= n;
+        __syncwarp();
+        if (n_rest >= 32) rest_round(32);
     };
     const TileSched sched{ctr, nwarps};
     for (uint64_t pass = sched.first((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)); pass < passes;
@@ -462,11 +567,15 @@ __global__ void __launch_bounds__(512, 2) k_joint_configs(DevArgs t, const __gri
                 const uint32_t mask = __ballot_sync(0xffffffffu, near);
                 if (near) {
                     const uint32_t pos = n_near + __popc(mask & lt_mask);
-                    ws->nc[pos] = make_float4(cx, cy, cz, r2);
+                    ws->nc[pos] = make_float4(cx, cy, cz, GRID ? arm.rr[i] : r2);
                     ws->ng[pos] = lane;
                 }
                 n_near += __popc(mask);
-                if (n_near >= 32) {
+                if (GRID && n_near >= 32) {
+                    __syncwarp();
+                    classify(32, n_near);
+                    done = done || ws->ghit[lane] != 0;
+                } else if (n_near >= 32) {
                     __syncwarp();
                     run_round(32);
                     const uint32_t rest = n_near - 32;
@@ -487,7 +596,7 @@ __global__ void __launch_bounds__(512, 2) k_joint_configs(DevArgs t, const __gri
                 }
             }
             // every configuration of the pass resolved: the rest of the chain is moot
-            if (__all_sync(0xffffffffu, done) && n_near == 0) break;
+            if (__all_sync(0xffffffffu, done) && n_near == 0 && n_rest == 0) break;
             const float l0 = arm.link[j][0], l1 = arm.link[j][1], l2 = arm.link[j][2];
             const float tx = row_dot(R, 0, l0, l1, l2);
             const float ty = row_dot(R, 1, l0, l1, l2);
@@ -496,7 +605,11 @@ __global__ void __launch_bounds__(512, 2) k_joint_configs(DevArgs t, const __gri
             p[1] = __fadd_rn(p[1], ty);
             p[2] = __fadd_rn(p[2], tz);
         }
-        if (n_near) {
+        if constexpr (GRID) {
+            __syncwarp();
+            if (n_near) classify(n_near, n_near);
+            if (n_rest) rest_round(n_rest);
+        } else if (n_near) {
             __syncwarp();
             run_round(n_near);
         }
@@ -511,8 +624,15 @@ int launch_joint_configs(const DevArgs& t, const capt_arm& arm, const float* q, 
     if (C == 0) return CAPT_OK;
     const bool stage = cfg.staging == CAPT_STAGE_SMEM && t.stage_floats > 0;
     // the chunked scan, or the compact one once the replicated sets are dropped
-    auto fn = t.blocks ? (stage ? k_joint_configs<true, kScanChunked> : k_joint_configs<false, kScanChunked>)
-                       : (stage ? k_joint_configs<true, kScanCompact> : k_joint_configs<false, kScanCompact>);
+    const bool grid = cfg.grid != 0 && t.grid != nullptr;
+    auto fn = grid ? (t.blocks ? (stage ? k_joint_configs<true, kScanChunked, true>
+                                        : k_joint_configs<false, kScanChunked, true>)
+                               : (stage ? k_joint_configs<true, kScanCompact, true>
+                                        : k_joint_configs<false, kScanCompact, true>))
+                   : (t.blocks ? (stage ? k_joint_configs<true, kScanChunked, false>
+                                        : k_joint_configs<false, kScanChunked, false>)
+                               : (stage ? k_joint_configs<true, kScanCompact, false>
+                                        : k_joint_configs<false, kScanCompact, false>));
     const int warps = std::max(1, std::min(16, (int)cfg.warps_per_block));
     const size_t smem = (stage ? stage_offset(t) : 0u) + sizeof(JointScratch) * (size_t)warps;
     cudaError_t ce = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -551,8 +671,15 @@ int launch_edges_persistent(const DevArgs& t, const capt_arm& arm, const float* 
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) { err = std::string("edge setup launch: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
     const bool stage = cfg.staging == CAPT_STAGE_SMEM && t.stage_floats > 0;
-    auto fn = t.blocks ? (stage ? k_edges_persistent<true, kScanChunked> : k_edges_persistent<false, kScanChunked>)
-                       : (stage ? k_edges_persistent<true, kScanCompact> : k_edges_persistent<false, kScanCompact>);
+    const bool grid = cfg.grid != 0 && t.grid != nullptr;
+    auto fn = grid ? (t.blocks ? (stage ? k_edges_persistent<true, kScanChunked, true>
+                                        : k_edges_persistent<false, kScanChunked, true>)
+                               : (stage ? k_edges_persistent<true, kScanCompact, true>
+                                        : k_edges_persistent<false, kScanCompact, true>))
+                   : (t.blocks ? (stage ? k_edges_persistent<true, kScanChunked, false>
+                                        : k_edges_persistent<false, kScanChunked, false>)
+                               : (stage ? k_edges_persistent<true, kScanCompact, false>
+                                        : k_edges_persistent<false, kScanCompact, false>));
     const int warps = std::max(1, std::min(16, (int)cfg.warps_per_block));
     const size_t smem = (stage ? stage_offset(t) : 0u) + sizeof(EdgeScratch) * (size_t)warps;
     ce = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -574,7 +701,9 @@ int launch_edges_per_edge(const DevArgs& t, const capt_arm& arm, const float* qa
     if (ce != cudaSuccess) { err = std::string("memset: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
     const int warps = std::max(1, std::min(16, (int)cfg.warps_per_block));
     const size_t smem = sizeof(EdgeScratch) * (size_t)warps;
-    auto fn = t.blocks ? k_edge_single<kScanChunked> : k_edge_single<kScanCompact>;
+    const bool grid = cfg.grid != 0 && t.grid != nullptr;
+    auto fn = grid ? (t.blocks ? k_edge_single<kScanChunked, true> : k_edge_single<kScanCompact, true>)
+                   : (t.blocks ? k_edge_single<kScanChunked, false> : k_edge_single<kScanCompact, false>);
     ce = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (ce != cudaSuccess) { err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
     const ArmPlan plan = make_plan(arm);

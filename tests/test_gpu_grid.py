@@ -223,3 +223,69 @@ def test_grid_spheres_every_launch_cfg(scene, orc, capt_lib, torch_, warps, spl,
     capt_lib.capt_set_launch_cfg(t, capt_lib.CAPT_KERNEL_SPHERES, 8, 2, 1, 0)
     assert np.array_equal(f.cpu().numpy(), ref)
     assert capt_lib.capt_device_status(t) == 0
+
+
+@pytest.mark.parametrize("mode", ["persistent", "per_edge", "plan", "static"])
+def test_grid_edges_match_oracle(scene, orc, capt_lib, torch_, mode):
+    """Edges with the grid: a sphere the grid proves colliding invalidates its edge at
+    once; flags equal the oracle's interpolation + kinematics + brute force."""
+    arm = scene["arm"]
+    qa, qb, ns = W.random_edges(600, 1014, nmax=120)
+    ref = orc.edges(arm, qa, qb, ns, points=scene["pts"])
+    assert 0.05 < ref.mean() < 0.95
+    t = scene["tree"]
+    dqa, dqb, dns = _cuda(torch_, qa), _cuda(torch_, qb), _cuda(torch_, ns)
+    valid = torch_.empty(len(ns), dtype=torch_.uint8, device="cuda")
+    for warps, stage, chunk in ((8, 0, 32), (16, 1, 64), (4, 0, 128)):
+        cfg = dict(warps_per_block=warps, spheres_per_lane=1, staging=stage, chunk=chunk, prefetch=0, grid=1)
+        if mode == "plan":
+            plan = capt_lib.capt_edge_plan_create(t, arm, dqa, dqb, dns, valid, cfg=cfg)
+            capt_lib.capt_edge_plan_launch(plan)
+            capt_lib.capt_edge_plan_launch(plan)
+            capt_lib.capt_edge_plan_free(plan)
+        else:
+            capt_lib.capt_set_launch_cfg(t, capt_lib.CAPT_KERNEL_EDGES, warps, 1, stage, chunk, 0, 1)
+            if mode == "static":
+                capt_lib.capt_validate_edges_static(t, arm, dqa, dqb, dns, valid)
+            else:
+                capt_lib.capt_validate_edges(t, arm, dqa, dqb, dns, valid,
+                                             mode=capt_lib.CAPT_EDGES_PER_EDGE if mode == "per_edge"
+                                             else capt_lib.CAPT_EDGES_PERSISTENT)
+        torch_.cuda.synchronize()
+        assert np.array_equal(valid.cpu().numpy(), ref), (mode, warps, stage, chunk)
+    capt_lib.capt_set_launch_cfg(t, capt_lib.CAPT_KERNEL_EDGES, 8, 2, 1, 32)
+    assert capt_lib.capt_device_status(t) == 0
+
+
+@pytest.mark.parametrize("warps,stage", [(2, 0), (4, 1), (8, 0), (16, 0)])
+def test_grid_joint_configs_match_oracle(scene, orc, capt_lib, torch_, warps, stage):
+    arm = scene["arm"]
+    q = W.random_configs(3001, 1015)
+    ref = orc.brute_config_flags(scene["pts"], orc.fk32(arm, q), arm.sphere_radius)
+    t = scene["tree"]
+    capt_lib.capt_set_launch_cfg(t, capt_lib.CAPT_KERNEL_JOINTS, warps, 1, stage, 0, 0, 1)
+    f = capt_lib.capt_query_joint_configs(t, arm, _cuda(torch_, q))
+    capt_lib.capt_set_launch_cfg(t, capt_lib.CAPT_KERNEL_JOINTS, 4, 1, 0, 0)
+    assert np.array_equal(f.cpu().numpy(), ref)
+    assert capt_lib.capt_device_status(t) == 0
+
+
+def test_grid_edges_and_joints_on_compact_sets(scene, orc, capt_lib, torch_):
+    """After the replicated sets are dropped the edge and joint-angle kernels scan the
+    compact sets; the grid built before the drop still decides most spheres."""
+    pts = scene["pts"]
+    arm = scene["arm"]
+    tree = capt_lib.capt_build(pts, 0.02, 0.08)
+    capt_lib.capt_upload(tree, 0)
+    capt_lib.capt_build_grid(tree)
+    capt_lib.capt_compact(tree, drop_full=True)
+    qa, qb, ns = W.random_edges(400, 1016, nmax=80)
+    ref = orc.edges(arm, qa, qb, ns, points=pts)
+    capt_lib.capt_set_launch_cfg(tree, capt_lib.CAPT_KERNEL_EDGES, 8, 1, 0, 32, 0, 1)
+    v = capt_lib.capt_validate_edges(tree, arm, _cuda(torch_, qa), _cuda(torch_, qb), _cuda(torch_, ns))
+    assert np.array_equal(v.cpu().numpy(), ref)
+    q = W.random_configs(2000, 1017)
+    refj = orc.brute_config_flags(pts, orc.fk32(arm, q), arm.sphere_radius)
+    capt_lib.capt_set_launch_cfg(tree, capt_lib.CAPT_KERNEL_JOINTS, 8, 1, 0, 0, 0, 1)
+    f = capt_lib.capt_query_joint_configs(tree, arm, _cuda(torch_, q))
+    assert np.array_equal(f.cpu().numpy(), refj)
