@@ -61,12 +61,14 @@ def hbm_peak():
 # configuration used (warps per block, spheres per lane, staging, scan, prefetch, grid).
 PROFILES = {
     "configs": ("tabletop, 1,048,576 configurations x 60 spheres, grid of 2^24 cells", "k_configs_grid",
-                (16, 16, 0, 0, 0, 1)),
+                (16, 16, 0, 0, 1, 1)),
     "configs_nogrid": ("tabletop, 1,048,576 configurations x 60 spheres, no grid", "k_configs", (4, 4, 0, 1, 0, 0)),
     "room": ("room, 200,000 points, 4,194,304 spheres, grid of 2^24 cells", "k_spheres", (8, 2, 0, 0, 0, 1)),
     "clearance": ("tabletop, 16,384 x 32 x 60 spheres, r_min = 0", "k_clearance_dist", (16, 2, 0, 0, 0, 0)),
-    "edges": ("tabletop, 4,096 edges (1,038,247 configurations)", "k_edges_persistent", (8, 1, 0, 32, 0, 0)),
-    "joints": ("tabletop, 1,048,576 configurations by joint angles", "k_joint_configs", (16, 1, 0, 0, 0, 0)),
+    "edges": ("tabletop, 4,096 edges (1,038,247 configurations), grid of 2^24 cells", "k_edges_persistent",
+              (4, 1, 0, 64, 0, 1)),
+    "joints": ("tabletop, 1,048,576 configurations by joint angles, grid of 2^24 cells", "k_joint_configs",
+               (8, 1, 0, 0, 0, 1)),
 }
 
 
@@ -107,6 +109,8 @@ def run_profile(args):
         else:
             tree = capt.capt_build(pts, R_MIN, R_MAX)
             capt.capt_upload(tree, 0)
+            if cfg[5]:
+                capt.capt_build_grid(tree, GRID_CELLS)
             if name == "edges":
                 qa, qb, ns = W.random_edges(4096, 1002)
                 dqa, dqb, dns = (torch.from_numpy(a).to(dev) for a in (qa, qb, ns))
@@ -119,8 +123,6 @@ def run_profile(args):
                 capt.capt_set_launch_cfg(tree, capt.CAPT_KERNEL_JOINTS, *cfg)
                 step = lambda: capt.capt_query_joint_configs(tree, arm, dq, f)   # noqa: E731
             else:
-                if cfg[5]:
-                    capt.capt_build_grid(tree, GRID_CELLS)
                 cen = torch.from_numpy(W.fk_centers(arm, W.random_configs(1 << 20, 1001))).to(dev)
                 r = torch.from_numpy(arm.sphere_radius.copy()).to(dev)
                 f = torch.empty(1 << 20, dtype=torch.uint8, device=dev)

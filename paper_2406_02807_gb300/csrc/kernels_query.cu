@@ -311,18 +311,19 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs(DevArgs t, cons
         sphere_round<false, MODE>(t, Ts, &ws->re, ws->ghit, c, g, live, lane, lt_mask);
     };
 
-    // tiles are taken in increasing order across the grid (from the counter, or w, w +
-    // warps, ... without one), so tile + pf x warps is the one some warp starts about pf
-    // tile-times from now: its centres are fetched into L2 meanwhile
-    const uint64_t pf_tiles = (uint64_t)pf * nwarps;
+    // L2 lookahead of the centre stream (pf passes of 128 spheres): tiles are taken in
+    // increasing order across the grid (from the counter, or w, w + warps, ... without
+    // one), so tile + warps is the one some warp starts about one tile-time from now
     const TileSched sched{ctr, nwarps};
     for (uint64_t tile = sched.first((uint64_t)blockIdx.x * (blockDim.x >> 5) + warp); tile < n_tiles;
          tile = sched.next(tile)) {
         const uint64_t first = tile * CPT;
         const uint32_t ncfg = (uint32_t)min((uint64_t)CPT, C - first);
-        if (pf_tiles && lane == 0 && tile + pf_tiles < n_tiles) {
-            const uint64_t pfirst = (tile + pf_tiles) * CPT;
-            prefetch_l2(centers + 3 * pfirst * (uint64_t)S, min((uint64_t)CPT, C - pfirst) * (uint64_t)S * 12u);
+        if (pf && lane == 0 && tile + nwarps < n_tiles) {
+            // the first pf passes of the tile some warp takes about one tile-time from now
+            const uint64_t pfirst = (tile + nwarps) * CPT;
+            const uint64_t pn = min((uint64_t)CPT, C - pfirst) * (uint64_t)S;
+            prefetch_l2(centers + 3 * pfirst * (uint64_t)S, min(pn, (uint64_t)128u * pf) * 12u);
         }
         const uint32_t nsph = ncfg * (uint32_t)S;
         const float* base = centers + 3 * first * (uint64_t)S;
@@ -335,6 +336,9 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs(DevArgs t, cons
         const uint32_t all_cfg = ncfg >= 32u ? 0xffffffffu : ((1u << ncfg) - 1u);
         uint32_t n_near = 0;
         for (uint32_t p0 = 0; p0 < nsph; p0 += 128) {
+            // the pass pf passes ahead in this tile, into L2 while this one is tested
+            if (pf && lane == 0 && p0 + 128 * pf < nsph)
+                prefetch_l2(base + 3 * (size_t)(p0 + 128 * pf), (uint64_t)min(128u, nsph - (p0 + 128 * pf)) * 12u);
             // ---- root box test of 4 consecutive spheres per lane ----
             const uint32_t i0 = p0 + 4 * lane;
             const uint32_t nv = i0 < nsph ? min(4u, nsph - i0) : 0u;
@@ -477,7 +481,6 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs_grid(DevArgs t,
     const float4 rhi = make_float4(t.hi[0], t.hi[1], t.hi[2], 0.f);
     const uint32_t inv_s = (1u << 20) / (uint32_t)S + 1u;   // i / S = (i * inv_s) >> 20 for i < 4096
     const bool s4 = (S & 3) == 0;
-    const uint64_t pf_tiles = (uint64_t)pf * nwarps;
 
     uint32_t n2 = 0;   // carried undecided spheres (warp-uniform)
     uint64_t first = 0;
@@ -566,9 +569,11 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs_grid(DevArgs t,
          tile = sched.next(tile)) {
         first = tile * CPT;
         ncfg = (uint32_t)min((uint64_t)CPT, C - first);
-        if (pf_tiles && lane == 0 && tile + pf_tiles < n_tiles) {
-            const uint64_t pfirst = (tile + pf_tiles) * CPT;
-            prefetch_l2(centers + 3 * pfirst * (uint64_t)S, min((uint64_t)CPT, C - pfirst) * (uint64_t)S * 12u);
+        if (pf && lane == 0 && tile + nwarps < n_tiles) {
+            // the first pf passes of the tile some warp takes about one tile-time from now
+            const uint64_t pfirst = (tile + nwarps) * CPT;
+            const uint64_t pn = min((uint64_t)CPT, C - pfirst) * (uint64_t)S;
+            prefetch_l2(centers + 3 * pfirst * (uint64_t)S, min(pn, (uint64_t)128u * pf) * 12u);
         }
         const uint32_t nsph = ncfg * (uint32_t)S;
         const float* base = centers + 3 * first * (uint64_t)S;
@@ -579,6 +584,9 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs_grid(DevArgs t,
         const uint32_t all_cfg = ncfg >= 32u ? 0xffffffffu : ((1u << ncfg) - 1u);
         n1 = 0;
         for (uint32_t p0 = 0; p0 < nsph; p0 += 128) {
+            // the pass pf passes ahead in this tile, into L2 while this one is tested
+            if (pf && lane == 0 && p0 + 128 * pf < nsph)
+                prefetch_l2(base + 3 * (size_t)(p0 + 128 * pf), (uint64_t)min(128u, nsph - (p0 + 128 * pf)) * 12u);
             // ---- root box test of 4 consecutive spheres per lane ----
             const uint32_t i0 = p0 + 4 * lane;
             const uint32_t nv = i0 < nsph ? min(4u, nsph - i0) : 0u;

@@ -581,3 +581,17 @@ def test_room_full_size(orc, capt_lib, torch_):
         capt_lib.capt_set_launch_cfg(tree, capt_lib.CAPT_KERNEL_SPHERES, 8, 2, 0, chunked, 0, 1)
         assert np.array_equal(capt_lib.capt_query_spheres(tree, _cuda(torch_, c), _cuda(torch_, r)).cpu().numpy(), ref)
     assert capt_lib.capt_device_status(tree) == 0
+
+
+@pytest.mark.parametrize("pf", [1, 2, 4])
+@pytest.mark.parametrize("spl", [2, 16])
+def test_configs_l2_lookahead(tabletop, orc, capt_lib, torch_, pf, spl):
+    """The L2 lookahead of the centre stream changes no flag (ragged batch)."""
+    cen = _configs(tabletop, 2999, first=123)
+    r = tabletop["arm"].sphere_radius
+    ref, _ = tabletop["oracle_tree"].query_configs(cen, r)
+    t = tabletop["tree"]
+    capt_lib.capt_set_launch_cfg(t, capt_lib.CAPT_KERNEL_CONFIGS, 8, spl, 0, 1, pf, 0)
+    f = capt_lib.capt_query_configs(t, _cuda(torch_, cen), _cuda(torch_, r))
+    capt_lib.capt_set_launch_cfg(t, capt_lib.CAPT_KERNEL_CONFIGS, 4, 8, 0, 1)
+    assert np.array_equal(f.cpu().numpy(), ref)
