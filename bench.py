@@ -46,6 +46,18 @@ TRAFFIC = {"68092aa0999048d9": 849318656 + 4137728}   # k_configs_grid<32, 0>, t
 HBM_FALLBACK_GBS = 6800.0   # used only when MEASURED_PEAKS.json is absent
 PARITY_SAMPLE = 32768       # configurations of the timed run checked against the oracle
 GRID_CELLS = 1 << 24        # cells of the distance-bound grid of the tabletop tree (32 MB)
+# FP32 operations per configuration evaluated by the kernels that run the arm's
+# kinematics, counted from their code: per joint 3 (interpolation) + 30 (sin and cos)
+# + 12 (rotation) + 18 (translation); per sphere 18 (placement) + 14 (box test); per link
+# 32 for the edge kernel's cull.  Spheres of culled links and of configurations resolved
+# early are counted too, so the ALU fractions below are upper bounds.
+JOINT_OPS_PER_CFG = 7 * (3 + 30 + 12 + 18) + 60 * (18 + 14)
+EDGE_OPS_PER_CFG = JOINT_OPS_PER_CFG + 7 * 32
+EDGE_OPS_NOTE = ("issue-bound kinematics: ops = configurations the launch evaluated (counted on the device) x "
+                 f"{EDGE_OPS_PER_CFG} FP32 operations each (interpolation, sin/cos, rotations, translations, link "
+                 "culls, 60 sphere placements and box tests); an upper bound")
+JOINT_OPS_NOTE = (f"issue-bound kinematics: ops = configurations x {JOINT_OPS_PER_CFG} FP32 operations each "
+                  "(sin/cos, rotations, translations, 60 sphere placements and box tests); an upper bound")
 
 
 def hbm_peak():
@@ -583,6 +595,8 @@ def secondary(capt, torch, dev, stream, tree, arm, q, cen, cen_host, r_host, fla
     for _ in range(3):
         capt.capt_edge_plan_launch(plan)
     edge_ms = time_events(torch, lambda: capt.capt_edge_plan_launch(plan), max(args.steps, 5), stream)
+    torch.cuda.synchronize()
+    evaluated = capt.capt_edge_plan_work(plan)
     v_plan = valid.clone()
     valid2 = torch.empty_like(valid)
     capt.capt_set_launch_cfg(tree, capt.CAPT_KERNEL_EDGES, ecfg["warps_per_block"], ecfg["spheres_per_lane"],
@@ -609,6 +623,7 @@ def secondary(capt, torch, dev, stream, tree, arm, q, cen, cen_host, r_host, fla
     joint_ms = time_events_flushed(torch, lambda: capt.capt_query_joint_configs(tree, arm, dq, jflags), args.steps,
                                    stream, flush)
     del flush
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
 
     return {
         "e2e": {"value": world * C * SPHERES / e2e_s, "unit": UNIT,
@@ -619,11 +634,15 @@ def secondary(capt, torch, dev, stream, tree, arm, q, cen, cen_host, r_host, fla
         "edges": {"edges": 4096, "configs": int(ns.sum()), "persistent_graph_ms": edge_ms,
                   "edges_per_s_persistent": 4096 / (edge_ms / 1e3), "per_edge_launch_ms": per_edge_ms,
                   "edges_per_s_per_edge": 4096 / (per_edge_ms / 1e3), "valid_fraction": float(valid2.float().mean()),
-                  "equal_results": edges_equal, "launch_cfg": ecfg},
+                  "equal_results": edges_equal, "launch_cfg": ecfg, "configs_evaluated": evaluated,
+                  "roofline": roof(edge_ms, int(qa.nbytes + qb.nbytes + ns.nbytes + 4096), evaluated * EDGE_OPS_PER_CFG,
+                                   None, sms, note=EDGE_OPS_NOTE)},
         "joint_configs": {"configs": C, "ms": joint_ms, "configs_per_s": world * C / (joint_ms / 1e3),
                           "sphere_queries_per_s": world * C * SPHERES / (joint_ms / 1e3),
                           "collision_fraction": float(jflags.float().mean().item()), "launch_cfg": jcfg,
-                          "input_bytes": int(q.nbytes), "l2": "flushed before every timed call"},
+                          "input_bytes": int(q.nbytes), "l2": "flushed before every timed call",
+                          "roofline": roof(joint_ms, int(q.nbytes) + C, C * JOINT_OPS_PER_CFG, None, sms,
+                                           note=JOINT_OPS_NOTE)},
     }
 
 

@@ -492,6 +492,11 @@ int capt_edge_plan_create(capt_tree* t, const capt_arm* arm, const float* d_qa, 
 int capt_edge_plan_launch(capt_edge_plan* p, void* stream);
 /* The plan's launch configuration and, when it was autotuned, the best time (else 0). */
 int capt_edge_plan_info(const capt_edge_plan* p, capt_launch_cfg* cfg, float* tuned_ms);
+/* Configurations the plan's last launch evaluated (its warps ran their interpolation,
+ * kinematics and sphere tests; an edge stops being evaluated once one collides, so this
+ * is at most the sum of n_e), for work accounting.  Synchronous: call it after the
+ * launch's stream has finished.  Errors: CAPT_E_ARG, CAPT_E_CUDA. */
+int capt_edge_plan_work(const capt_edge_plan* p, uint64_t* configs_evaluated);
 void capt_edge_plan_free(capt_edge_plan* p);
 
 /* ---------------------------------------------------------------------------------

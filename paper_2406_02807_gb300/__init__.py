@@ -26,7 +26,7 @@ __all__ = [
     "capt_autotune_joint_configs", "CAPT_KERNEL_JOINTS", "sfc_filter_device", "capt_autotune_spheres",
     "capt_morton_order", "capt_build_frame_device", "capt_compact", "CAPT_SCAN_SETS", "CAPT_SCAN_CHUNKED",
     "capt_count_sphere_work", "capt_count_clearance_work", "capt_build_grid", "capt_grid_export",
-    "CAPT_SCAN_COMPACT", "STATUS", "CAPT_STAGE_GLOBAL", "CAPT_STAGE_SMEM", "CAPT_KERNEL_SPHERES", "CAPT_KERNEL_CONFIGS",
+    "capt_edge_plan_work", "CAPT_SCAN_COMPACT", "STATUS", "CAPT_STAGE_GLOBAL", "CAPT_STAGE_SMEM", "CAPT_KERNEL_SPHERES", "CAPT_KERNEL_CONFIGS",
     "CAPT_KERNEL_EDGES", "CAPT_KERNEL_CLEARANCE", "CAPT_EDGES_PERSISTENT", "CAPT_EDGES_PER_EDGE",
     "EXPORTED_SYMBOLS",
 ]
@@ -49,6 +49,7 @@ EXPORTED_SYMBOLS = [
     "capt_validate_edges_static", "capt_build_device", "capt_query_joint_configs", "capt_autotune_joint_configs",
     "sfc_filter_device", "capt_autotune_spheres", "capt_morton_order", "capt_build_frame_device", "capt_compact",
     "capt_count_sphere_work", "capt_count_clearance_work", "capt_build_grid", "capt_grid_export",
+    "capt_edge_plan_work",
 ]
 CAPT_STATIC_MAX_EDGES = 65536
 
@@ -119,6 +120,7 @@ def _load():
         "capt_count_sphere_work": [P, P, P, SZ, P, P],
         "capt_count_clearance_work": [P, P, SZ, P, P],
         "capt_build_grid": [P, C.c_uint64, P],
+        "capt_edge_plan_work": [P, C.POINTER(C.c_uint64)],
         "capt_grid_export": [P, C.POINTER(_GridInfo), P],
         "capt_query_leaves": [P, P, SZ, P, P],
         "capt_device_status": [P, P],
@@ -671,6 +673,13 @@ def capt_edge_plan_info(plan: EdgePlan):
     ms = C.c_float()
     _check(_load().capt_edge_plan_info(plan.h, C.byref(c), C.byref(ms)), "capt_edge_plan_info")
     return {k: getattr(c, k) for k, _ in _LaunchCfg._fields_}, ms.value
+
+
+def capt_edge_plan_work(plan: EdgePlan) -> int:
+    """Configurations the plan's last launch evaluated (call after it has finished)."""
+    v = C.c_uint64()
+    _check(_load().capt_edge_plan_work(plan.h, C.byref(v)), "capt_edge_plan_work")
+    return int(v.value)
 
 
 def capt_edge_plan_free(plan: EdgePlan):

@@ -1070,6 +1070,7 @@ struct capt_edge_plan {
     cudaGraphExec_t exec = nullptr;
     capt_launch_cfg cfg{};
     float tuned_ms = 0.f;
+    size_t E = 0;
 };
 
 extern "C" {
@@ -1197,6 +1198,7 @@ int capt_edge_plan_create(capt_tree* t, const capt_arm* arm, const float* d_qa, 
     capt_edge_plan* p = new (std::nothrow) capt_edge_plan();
     if (!p) return fail(CAPT_E_NOMEM, "host allocation failed");
     p->tree = t;
+    p->E = E;
     p->device = t->device;
     p->tree_plans = t->n_plans;
     ++*p->tree_plans;
@@ -1271,6 +1273,16 @@ int capt_edge_plan_launch(capt_edge_plan* p, void* stream) {
     if (cudaGetDevice(&cur) != cudaSuccess || cur != p->device)
         return fail(CAPT_E_STATE, "current CUDA device differs from the plan's device");
     CUDA_TRY(cudaGraphLaunch(p->exec, static_cast<cudaStream_t>(stream)), "cudaGraphLaunch");
+    return CAPT_OK;
+}
+
+int capt_edge_plan_work(const capt_edge_plan* p, uint64_t* configs_evaluated) {
+    if (!p || !configs_evaluated) return fail(CAPT_E_ARG, "NULL argument");
+    DeviceGuard g(p->device);
+    unsigned long long v = 0;
+    CUDA_TRY(cudaMemcpy(&v, p->d_scratch + capt::edge_eval_word((uint32_t)p->E), sizeof(v), cudaMemcpyDeviceToHost),
+             "edge work D2H");
+    *configs_evaluated = v;
     return CAPT_OK;
 }
 

@@ -41,6 +41,8 @@ int launch_clearance_bwd(const DevArgs& t, const float* centers, const float* ra
 
 // Edge validation: scratch holds (E + 1) uint32 work-item offsets plus one counter.
 size_t edge_scratch_words(size_t E);
+// Word of the edge scratch that holds the 64-bit count of configurations evaluated.
+__host__ __device__ __forceinline__ uint32_t edge_eval_word(uint32_t E) { return (E + 3u) & ~1u; }
 int launch_edges_persistent(const DevArgs& t, const capt_arm& arm, const float* qa, const float* qb,
                             const int32_t* ns, uint64_t E, uint8_t* valid, uint32_t* scratch,
                             const capt_launch_cfg& cfg, cudaStream_t st, std::string& err);

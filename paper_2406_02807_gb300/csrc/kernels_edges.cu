@@ -376,6 +376,8 @@ __global__ void k_edges_setup(const int32_t* __restrict__ ns, uint32_t E, uint32
     if (threadIdx.x == 0) {
         scratch[E] = refuse ? 0u : (uint32_t)carry;
         scratch[E + 1] = 0;   // work counter
+        // configurations evaluated (64 bits, 8-byte aligned, in the scratch's slack)
+        *reinterpret_cast<unsigned long long*>(scratch + edge_eval_word(E)) = 0ull;
         if (refuse) atomicOr(status, kStatusBounds);
     }
 }
@@ -397,6 +399,7 @@ __global__ void __launch_bounds__(512, 2) k_edges_persistent(DevArgs t, const __
     EdgeScratch* ws = reinterpret_cast<EdgeScratch*>(smem_raw + off) + (threadIdx.x >> 5);
     const uint32_t total_items = scratch[E];
     uint32_t* counter = scratch + E + 1;
+    unsigned long long evaluated = 0;   // configurations this warp ran (lane 0's count)
     const int J = arm.J;
     while (true) {
         uint32_t item = 0;
@@ -422,6 +425,7 @@ __global__ void __launch_bounds__(512, 2) k_edges_persistent(DevArgs t, const __
         const float* qa_e = qa + (size_t)e * J;
         const float* qb_e = qb + (size_t)e * J;
         for (int j = 0; j < cnt; j += 32) {
+            evaluated += (unsigned long long)min(32, cnt - j);
             if (edge_pass<MODE, GRID>(t, arm, qa_e, qb_e, n_e, ci + nci * j, nci, min(32, cnt - j), Ts, ws)) {
                 if (lane == 0) valid[e] = 0;
                 break;
@@ -429,6 +433,8 @@ __global__ void __launch_bounds__(512, 2) k_edges_persistent(DevArgs t, const __
             if (load_volatile_u8(valid + e) == 0) break;
         }
     }
+    if (lane == 0 && evaluated)
+        atomicAdd(reinterpret_cast<unsigned long long*>(scratch + edge_eval_word(E)), evaluated);
 }
 
 // One edge per launch (the per-edge baseline): warps stride over its configurations.

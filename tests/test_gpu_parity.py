@@ -595,3 +595,29 @@ def test_configs_l2_lookahead(tabletop, orc, capt_lib, torch_, pf, spl):
     f = capt_lib.capt_query_configs(t, _cuda(torch_, cen), _cuda(torch_, r))
     capt_lib.capt_set_launch_cfg(t, capt_lib.CAPT_KERNEL_CONFIGS, 4, 8, 0, 1)
     assert np.array_equal(f.cpu().numpy(), ref)
+
+
+def test_edge_plan_counts_the_configurations_it_evaluates(orc, capt_lib, torch_):
+    """With the cloud out of the arm's reach every edge is valid, so every configuration
+    is evaluated and the plan's count is exactly the sum of n_e; with a cloud in reach it
+    is at most that (work items already running when their edge is found to collide
+    finish their pass; a small batch starts every item at once)."""
+    arm = W.arm_7dof()
+    qa, qb, ns = W.random_edges(300, 1021, nmax=90)
+    far = (W.uniform_cloud(500, 21) + np.float32(10.0)).astype(np.float32)
+    for pts, all_valid in ((far, True), (W.tabletop_scene(1001)[0][:8000], False)):
+        t = capt_lib.capt_build(pts, 0.02, 0.08)
+        capt_lib.capt_upload(t, 0)
+        valid = torch_.empty(len(ns), dtype=torch_.uint8, device="cuda")
+        plan = capt_lib.capt_edge_plan_create(t, arm, _cuda(torch_, qa), _cuda(torch_, qb), _cuda(torch_, ns), valid,
+                                              cfg=dict(warps_per_block=8, spheres_per_lane=1, staging=0, chunk=32))
+        capt_lib.capt_edge_plan_launch(plan)
+        torch_.cuda.synchronize()
+        n = capt_lib.capt_edge_plan_work(plan)
+        v = valid.cpu().numpy()
+        assert np.array_equal(v, orc.edges(arm, qa, qb, ns, points=pts))
+        if all_valid:
+            assert v.all() and n == int(np.maximum(ns, 0).sum())
+        else:
+            assert not v.all() and 0 < n <= int(np.maximum(ns, 0).sum())
+        capt_lib.capt_edge_plan_free(plan)
