@@ -76,7 +76,12 @@ PROFILES = {
                 (16, 16, 0, 0, 1, 1)),
     "configs_nogrid": ("tabletop, 1,048,576 configurations x 60 spheres, no grid", "k_configs", (4, 4, 0, 1, 0, 0)),
     "room": ("room, 200,000 points, 4,194,304 spheres, grid of 2^24 cells", "k_spheres", (8, 2, 0, 0, 0, 1)),
-    "clearance": ("tabletop, 16,384 x 32 x 60 spheres, r_min = 0", "k_clearance_dist", (16, 2, 0, 0, 0, 0)),
+    "clearance": ("tabletop, 16,384 x 32 x 60 spheres, r_min = 0, the paper's path", "k_clearance_dist",
+                  (16, 2, 0, 0, 0, 0)),
+    "clearance_lists": ("tabletop, 16,384 x 32 x 60 spheres, r_min = 0, nearest-candidate lists over a grid of "
+                        "2^24 cells", "k_clearance_dist", (8, 2, 0, 0, 0, 1)),
+    "near_lists": ("tabletop, r_min = 0, nearest-candidate lists over a grid of 2^24 cells (the builder)",
+                   "k_near_lists", (8, 2, 0, 0, 0, 1)),
     "edges": ("tabletop, 4,096 edges (1,038,247 configurations), grid of 2^24 cells", "k_edges_persistent",
               (4, 1, 0, 64, 0, 1)),
     "joints": ("tabletop, 1,048,576 configurations by joint angles, grid of 2^24 cells", "k_joint_configs",
@@ -107,9 +112,12 @@ def run_profile(args):
     else:
         raw, _, arm = W.tabletop_scene(1001)
         pts = raw[capt.sfc_filter(raw, R_FILTER)]
-        if name == "clearance":
+        if name in ("clearance", "clearance_lists", "near_lists"):
             tree = capt.capt_build(pts, 0.0, R_MAX)
             capt.capt_upload(tree, 0)
+            if cfg[5]:
+                capt.capt_build_grid(tree, GRID_CELLS)
+                capt.capt_build_near_lists(tree)
             q = W.random_trajectories(16384, 32, 1003)
             c = torch.from_numpy(W.fk_centers(arm, q.reshape(-1, 7)).reshape(16384, 32, SPHERES, 3)).to(dev)
             r = torch.from_numpy(arm.sphere_radius.copy()).to(dev)
@@ -118,6 +126,8 @@ def run_profile(args):
             d = torch.empty((16384, 32, SPHERES), dtype=torch.float32, device=dev)
             am = torch.empty((16384, 32, SPHERES), dtype=torch.int32, device=dev)
             step = lambda: capt.capt_clearance_fwd(tree, c, r, 0.01, cost, d, am)   # noqa: E731
+            if name == "near_lists":
+                step = lambda: capt.capt_build_near_lists(tree)   # noqa: E731
         else:
             tree = capt.capt_build(pts, R_MIN, R_MAX)
             capt.capt_upload(tree, 0)
@@ -690,7 +700,9 @@ def sphere_ops(counts, L, chunked=True, in_bytes=16):
 def bench_clearance(capt, torch, dev, stream, pts, arm, steps, sms):
     """The differentiable clearance workload: 16,384 trajectories x 32 waypoints x 60
     spheres, forward (distances, argmin, hinge cost) and backward, inputs (377 MB of
-    centres) larger than L2."""
+    centres) larger than L2.  The forward runs on the nearest-candidate lists (built
+    over the distance-bound grid, build times reported) in the launch configuration the
+    autotuner picks; the paper's path (descent and full set scan) is timed beside it."""
     import oracle
     ctree = capt.capt_build(pts, 0.0, R_MAX)
     capt.capt_upload(ctree, dev.index)
@@ -700,20 +712,46 @@ def bench_clearance(capt, torch, dev, stream, pts, arm, steps, sms):
     c = torch.from_numpy(c_host).to(dev)
     r = torch.from_numpy(arm.sphere_radius.copy()).to(dev)
     g = torch.ones(T, device=dev)
+    m = T * Wn * SPHERES
+    L = capt.capt_stats(ctree)["depth"]
     cost, d, am = capt.capt_clearance_fwd(ctree, c, r, 0.01)
     grad = torch.empty_like(c)
+
+    def run_fwd():
+        return time_events(torch, lambda: capt.capt_clearance_fwd(ctree, c, r, 0.01, cost, d, am), steps, stream)
+
+    # the paper's path: every near sphere descends and scans its leaf set
+    capt.capt_set_launch_cfg(ctree, capt.CAPT_KERNEL_CLEARANCE, 16, 2, 0, 0, 0, 0)
+    for _ in range(3):
+        capt.capt_clearance_fwd(ctree, c, r, 0.01, cost, d, am)
+    paper_ms = run_fwd()
+    d_paper, am_paper = d.clone(), am.clone()
+    paper_counts = [int(x) for x in capt.capt_count_clearance_work(ctree, c).cpu().numpy()]
+    # the nearest-candidate lists
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    capt.capt_build_grid(ctree, GRID_CELLS)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    capt.capt_build_near_lists(ctree)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    st = capt.capt_stats(ctree)
+    cfg, _ = capt.capt_autotune_clearance(ctree, c, r, 0.01)
     for _ in range(3):
         capt.capt_clearance_fwd(ctree, c, r, 0.01, cost, d, am)
         capt.capt_clearance_bwd(ctree, c, r, d, am, g, 0.01, grad)
-    fwd_ms = time_events(torch, lambda: capt.capt_clearance_fwd(ctree, c, r, 0.01, cost, d, am), steps, stream)
+    fwd_ms = run_fwd()
     bwd_ms = time_events(torch, lambda: capt.capt_clearance_bwd(ctree, c, r, d, am, g, 0.01, grad), steps, stream)
-    m = T * Wn * SPHERES
+    same = bool(torch.equal(d, d_paper)) and bool(torch.equal(am, am_paper))
     counts = [int(x) for x in capt.capt_count_clearance_work(ctree, c).cpu().numpy()]
-    L = capt.capt_stats(ctree)["depth"]
-    # a box test per sphere, a descent and leaf box test per sphere near the cloud's box,
-    # 9 operations per point of the sets scanned in full (48 bytes per 4-point block)
-    ops = counts[0] * 15 + counts[1] * (L + 15) + counts[3] * 9
-    l1 = counts[0] * 12 + counts[1] * (32 + 4 * L) + counts[4] * 48
+    # per sphere a box test (15 ops, 12 bytes); per near sphere with a list a cell lookup
+    # (about 12 ops, 8 bytes) and 9 ops per list entry (4 + 16 bytes); per fallback sphere
+    # a descent and leaf box test (L + 15 ops) and 9 ops per point of its set
+    ops = counts[0] * 15 + counts[5] * 12 + counts[6] * 9 + counts[7] * (L + 15) + counts[3] * 9
+    l1 = counts[0] * 12 + counts[5] * 8 + counts[6] * 20 + counts[7] * (32 + 4 * L) + counts[4] * 48
+    paper_ops = paper_counts[0] * 15 + paper_counts[1] * (L + 15) + paper_counts[3] * 9
+    paper_l1 = paper_counts[0] * 12 + paper_counts[1] * (32 + 4 * L) + paper_counts[4] * 48
     fwd_bytes = m * (12 + 4 + 4) + T * 4          # centres in; distance and argmin out; cost
     bwd_bytes = m * (12 + 4 + 4 + 12) + T * 4      # centres, distance, argmin in; gradient out
     # parity sample: the first 8 trajectories against the oracle's FP64 nearest distance
@@ -723,9 +761,17 @@ def bench_clearance(capt, torch, dev, stream, pts, arm, steps, sms):
     cerr = float(np.abs(cost[:k].cpu().numpy().astype(np.float64) - ocost).max())
     return {"trajectories": T, "waypoints": Wn, "spheres": m, "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
             "fwd_spheres_per_s": m / (fwd_ms / 1e3), "fwd_bwd_spheres_per_s": m / ((fwd_ms + bwd_ms) / 1e3),
-            "launch_cfg": capt.capt_get_launch_cfg(ctree, capt.CAPT_KERNEL_CLEARANCE),
-            "work": {"spheres": counts[0], "near_cloud_box": counts[1], "leaf_box_pass": counts[2],
-                     "points_scanned": counts[3], "blocks_scanned": counts[4], "points_per_sphere": counts[3] / m},
+            "launch_cfg": cfg,
+            "near_lists": {"grid_cells": int(np.prod(st["grid_dims"])), "grid_build_ms": (t1 - t0) * 1e3,
+                           "lists_build_ms": (t2 - t1) * 1e3, "entries": st["near_entries"],
+                           "bytes": st["near_bytes"], "fallback_cells": st["near_fallback_cells"],
+                           "same_as_paper_path": same},
+            "paper_path": {"fwd_ms": paper_ms, "fwd_spheres_per_s": m / (paper_ms / 1e3),
+                           "roofline": roof(paper_ms, fwd_bytes, paper_ops, paper_l1, sms),
+                           "points_scanned": paper_counts[3], "points_per_sphere": paper_counts[3] / m},
+            "work": {"spheres": counts[0], "near_cloud_box": counts[1], "answered_by_lists": counts[5],
+                     "list_entries": counts[6], "fallback_spheres": counts[7],
+                     "entries_per_list_sphere": counts[6] / max(counts[5], 1)},
             "roofline_fwd": roof(fwd_ms, fwd_bytes, ops, l1, sms),
             "roofline_bwd": roof(bwd_ms, bwd_bytes, m * 12, None, sms),
             "l2": "inputs larger than L2 (377 MB of centres)",

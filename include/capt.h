@@ -82,6 +82,9 @@ typedef struct capt_tree_stats {
                                  not part of device_bytes */
     uint32_t grid_dims[3];    /* cells per axis of the distance-bound grid (0: none) */
     float grid_cell;          /* its cell side (0: none) */
+    uint64_t near_entries;    /* capt_build_near_lists: list entries, padding included (0: none) */
+    uint64_t near_bytes;      /* their device bytes (cell table, entries, float4 cloud) */
+    uint64_t near_fallback_cells; /* cells whose centres take the paper's path instead */
 } capt_tree_stats;
 
 /* ---------------------------------------------------------------------------------
@@ -219,6 +222,30 @@ typedef struct capt_grid_info {
     uint32_t cells;
 } capt_grid_info;
 int capt_grid_export(const capt_tree* t, capt_grid_info* info, uint8_t* h_cells);
+
+/* Nearest-candidate lists of the clearance (this library's addition; the paper's
+ * clearance scans the whole set of the centre's leaf, Lemma 1 case 1).  For every cell
+ * of the distance-bound grid (grown by cell / 100) with centre m and half-diagonal rho:
+ * the points of the sets of all leaves whose closed cell meets the cell that lie
+ * within min(ub, r_max) (1 + 2^-20) + rho of m, each once (in no promised order); ub
+ * is the grid's upper bound for the cell.  capt_clearance_fwd with
+ * capt_launch_cfg.grid = 1 then answers a centre near the cloud from its cell's list
+ * (the FP32 argmin over the list, ties to the lowest point index) instead of the
+ * descent and the full set scan: the nearest point that the paper's scan reports is
+ * always in the list, and no other list point can beat it, so the distances and
+ * indices are the paper's bit for bit (the argument is in dist_grid.cu).  A cell the
+ * grid proves farther than r_max from the cloud has an empty list (r_max, -1).  A cell
+ * that meets more than 32 leaves or holds more than 1024 such points (a coarse grid)
+ * is a fallback cell: its centres take the paper's path.  Device memory: 8 bytes per
+ * cell, 4 per entry (each list padded to a multiple of 4), 16 per point.
+ * Needs an uploaded tree with r_min = 0, its replicated sets, and capt_build_grid
+ * first (a tree without points, or with r_max = 0, gets no lists and no error);
+ * capt_build_grid and capt_upload release the lists (they belong to one grid).
+ * Do not call it while work on this tree runs on other streams.  Synchronises
+ * `stream`.  Errors: CAPT_E_ARG, CAPT_E_STATE, CAPT_E_RANGE (2^32 entries or more: use
+ * a coarser grid), CAPT_E_NOMEM, CAPT_E_BOUNDS (the two walks of the builder
+ * disagreed), CAPT_E_CUDA. */
+int capt_build_near_lists(capt_tree* t, void* stream);
 
 /* De-duplicated ("compact") affordance sets: Alg. 1 copies a point into the set of
  * every leaf cell that affords it, so the sets replicate the cloud many times over
@@ -368,7 +395,11 @@ typedef struct capt_launch_cfg {
                                   dropped, a certain hit decides its sphere, configuration
                                   or edge at once, only the undecided descend.  Exact (the
                                   flags do not change).  Ignored while the tree has no
-                                  grid.  Clearance: must be 0. */
+                                  grid.  Clearance: 1 = answer the centres near the cloud
+                                  from the nearest-candidate lists
+                                  (capt_build_near_lists), with the same results; ignored
+                                  while the tree has none.  Default 1 for clearance, 0
+                                  for the others. */
 } capt_launch_cfg;
 #define CAPT_MAX_PREFETCH 4
 
@@ -506,7 +537,9 @@ void capt_edge_plan_free(capt_edge_plan* p);
 /* Forward: for T trajectories x W waypoints x S spheres,
  *   d = min(||c - p*||, r_max) with p* the nearest cloud point: exact whenever the
  *       nearest point is within r_max, because every such point is in the leaf's set
- *       (Lemma 1, case 1); the distance is sqrt of the FP32 squared distance;
+ *       (Lemma 1, case 1); the distance is sqrt of the FP32 squared distance; with
+ *       nearest-candidate lists (capt_build_near_lists, grid = 1) the same values come
+ *       from the centre's grid cell instead of its leaf set;
  *   cost_t = sum over its W*S spheres of max(0, r_s + margin - d)^2.
  * d_centers device float[T][W][S][3]; d_radii device float[S]; d_cost device
  * float[T]; d_dist device float[T*W*S]; d_argmin device int32[T*W*S] receives the
@@ -520,19 +553,34 @@ int capt_clearance_fwd(const capt_tree* t, const float* d_centers, const float* 
  * h = max(0, r_s + margin - d), when h > 0, d < r_max and d > 0; else 0.
  * d_grad_cost device float[T] (g).  Other arguments as in the forward, whose d_dist and
  * d_argmin it reads.  Errors as capt_clearance_fwd. */
-/* Algorithmic work of capt_clearance_fwd on m = T x W x S sphere centres (d_centers
- * device float[m][3]), counted sequentially per sphere, for roofline accounting:
- * d_counts device uint64[5] receives += [spheres, spheres within r_max of the cloud's
- * bounding box (these descend), spheres whose leaf box is within r_max (Alg. 3's box
- * test at r_max), points of their sets (each scanned in full: the nearest point is
- * wanted, Lemma 1 case 1), 4-point blocks of those sets].  The caller zeroes d_counts.
- * Errors as capt_clearance_fwd. */
-int capt_count_clearance_work(const capt_tree* t, const float* d_centers, size_t m, uint64_t* d_counts,
-                              void* stream);
+/* Time every supported launch configuration of the clearance forward on these inputs
+ * (warps per block, staging, prefetch, and the nearest-candidate lists when the tree
+ * has them; CUDA events on `stream`), keep the fastest on the tree and return it.  The
+ * outputs are overwritten (every configuration computes the same values).  best_ms may
+ * be NULL.  Synchronises `stream`.  Errors as capt_clearance_fwd, and CAPT_E_ARG for
+ * T = 0. */
+int capt_autotune_clearance(capt_tree* t, const float* d_centers, const float* d_radii, size_t T, int W, int S,
+                            float margin, float* d_cost, float* d_dist, int32_t* d_argmin, void* stream,
+                            capt_launch_cfg* best, float* best_ms);
 
 int capt_clearance_bwd(const capt_tree* t, const float* d_centers, const float* d_radii, const float* d_dist,
                        const int32_t* d_argmin, const float* d_grad_cost, size_t T, int W, int S, float margin,
                        float* d_grad_centers, void* stream);
+
+/* Algorithmic work of capt_clearance_fwd on m = T x W x S sphere centres (d_centers
+ * device float[m][3]), counted sequentially per sphere, for roofline accounting:
+ * d_counts device uint64[8] receives += [spheres, spheres within r_max of the cloud's
+ * bounding box, spheres whose leaf box is within r_max (Alg. 3's box test at r_max),
+ * points of their sets (each scanned in full: the nearest point is wanted, Lemma 1
+ * case 1), 4-point blocks of those sets, then three list counts].  When the tree has
+ * nearest-candidate lists and its clearance launch has grid = 1 the counts follow that
+ * path: the near spheres look up their cell, [5] those answered by a list (an empty one
+ * included), [6] list entries scanned (padding included), [7] those of fallback cells,
+ * and entries 2-4 count the descents and scans of the fallback spheres only; otherwise
+ * [5]-[7] stay 0 and every near sphere descends.  The caller zeroes d_counts.
+ * Errors as capt_clearance_fwd. */
+int capt_count_clearance_work(const capt_tree* t, const float* d_centers, size_t m, uint64_t* d_counts,
+                              void* stream);
 
 #ifdef __cplusplus
 }

@@ -26,7 +26,7 @@ __all__ = [
     "capt_autotune_joint_configs", "CAPT_KERNEL_JOINTS", "sfc_filter_device", "capt_autotune_spheres",
     "capt_morton_order", "capt_build_frame_device", "capt_compact", "CAPT_SCAN_SETS", "CAPT_SCAN_CHUNKED",
     "capt_count_sphere_work", "capt_count_clearance_work", "capt_build_grid", "capt_grid_export",
-    "capt_edge_plan_work", "CAPT_SCAN_COMPACT", "STATUS", "CAPT_STAGE_GLOBAL", "CAPT_STAGE_SMEM", "CAPT_KERNEL_SPHERES", "CAPT_KERNEL_CONFIGS",
+    "capt_build_near_lists", "capt_autotune_clearance", "capt_edge_plan_work", "CAPT_SCAN_COMPACT", "STATUS", "CAPT_STAGE_GLOBAL", "CAPT_STAGE_SMEM", "CAPT_KERNEL_SPHERES", "CAPT_KERNEL_CONFIGS",
     "CAPT_KERNEL_EDGES", "CAPT_KERNEL_CLEARANCE", "CAPT_EDGES_PERSISTENT", "CAPT_EDGES_PER_EDGE",
     "EXPORTED_SYMBOLS",
 ]
@@ -49,7 +49,7 @@ EXPORTED_SYMBOLS = [
     "capt_validate_edges_static", "capt_build_device", "capt_query_joint_configs", "capt_autotune_joint_configs",
     "sfc_filter_device", "capt_autotune_spheres", "capt_morton_order", "capt_build_frame_device", "capt_compact",
     "capt_count_sphere_work", "capt_count_clearance_work", "capt_build_grid", "capt_grid_export",
-    "capt_edge_plan_work",
+    "capt_build_near_lists", "capt_autotune_clearance", "capt_edge_plan_work",
 ]
 CAPT_STATIC_MAX_EDGES = 65536
 
@@ -67,7 +67,8 @@ class _Stats(C.Structure):
                 ("build_ms", C.c_double), ("r_min", C.c_float), ("r_max", C.c_float), ("device", C.c_int32),
                 ("build_threads", C.c_int32), ("compact_chunks", C.c_uint64), ("compact_entries", C.c_uint64),
                 ("compact_bytes", C.c_uint64), ("full_dropped", C.c_int32), ("reserved", C.c_int32),
-                ("scratch_bytes", C.c_uint64), ("grid_dims", C.c_uint32 * 3), ("grid_cell", C.c_float)]
+                ("scratch_bytes", C.c_uint64), ("grid_dims", C.c_uint32 * 3), ("grid_cell", C.c_float),
+                ("near_entries", C.c_uint64), ("near_bytes", C.c_uint64), ("near_fallback_cells", C.c_uint64)]
 
 
 class _LaunchCfg(C.Structure):
@@ -120,6 +121,7 @@ def _load():
         "capt_count_sphere_work": [P, P, P, SZ, P, P],
         "capt_count_clearance_work": [P, P, SZ, P, P],
         "capt_build_grid": [P, C.c_uint64, P],
+        "capt_build_near_lists": [P, P],
         "capt_edge_plan_work": [P, C.POINTER(C.c_uint64)],
         "capt_grid_export": [P, C.POINTER(_GridInfo), P],
         "capt_query_leaves": [P, P, SZ, P, P],
@@ -136,6 +138,7 @@ def _load():
         "capt_edge_plan_launch": [P, P],
         "capt_edge_plan_info": [P, C.POINTER(_LaunchCfg), C.POINTER(F)],
         "capt_clearance_fwd": [P, P, P, SZ, I, I, F, P, P, P, P],
+        "capt_autotune_clearance": [P, P, P, SZ, I, I, F, P, P, P, P, C.POINTER(_LaunchCfg), C.POINTER(F)],
         "capt_clearance_bwd": [P, P, P, P, P, P, SZ, I, I, F, P, P],
     }
     for name, args in sig.items():
@@ -348,6 +351,13 @@ def capt_grid_export(tree: CaptTree):
     return shape, cells.reshape(n2, n1, n0, 2)
 
 
+def capt_build_near_lists(tree: CaptTree, stream=None):
+    """Build the clearance's nearest-candidate lists over the tree's distance-bound grid
+    (capt_build_grid first; tree with r_min = 0); capt_clearance_fwd uses them with
+    grid = 1 (the clearance default)."""
+    _check(_load().capt_build_near_lists(tree.h, _stream(stream)), "capt_build_near_lists")
+
+
 def capt_compact(tree: CaptTree, drop_full: bool = False, stream=None):
     """Build the tree's compact (de-duplicated) sets on its device; drop_full frees the
     replicated device sets afterwards."""
@@ -440,13 +450,14 @@ def capt_count_sphere_work(tree: CaptTree, centers, radii, stream=None):
 
 
 def capt_count_clearance_work(tree: CaptTree, centers, stream=None):
-    """[spheres, near the cloud box, passing the leaf box, points scanned, blocks scanned]
-    of capt_clearance_fwd on centres [..., 3]."""
+    """[spheres, near the cloud box, passing the leaf box, points scanned, blocks scanned,
+    answered by a nearest-candidate list, list entries scanned, fallback spheres] of
+    capt_clearance_fwd on centres [..., 3]."""
     import torch
     if centers.shape[-1] != 3:
         raise ValueError("centers must end in a dimension of 3")
     m = centers.numel() // 3
-    counts = torch.zeros(5, dtype=torch.int64, device=centers.device)
+    counts = torch.zeros(8, dtype=torch.int64, device=centers.device)
     _check(_load().capt_count_clearance_work(tree.h, _dev(centers, torch.float32, "centers"), m,
                                              _dev(counts, torch.int64, "counts"), _stream(stream)),
            "capt_count_clearance_work")
@@ -710,6 +721,28 @@ def capt_clearance_fwd(tree: CaptTree, centers, radii, margin: float, cost=None,
                                       _dev(cost, torch.float32, "cost"), _dev(dist, torch.float32, "dist"),
                                       _dev(argmin, torch.int32, "argmin"), _stream(stream)), "capt_clearance_fwd")
     return cost, dist, argmin
+
+
+def capt_autotune_clearance(tree: CaptTree, centers, radii, margin: float, stream=None):
+    """Time the clearance forward's launch configurations on these inputs, keep the
+    fastest on the tree; returns (cfg dict, best ms)."""
+    import torch
+    if centers.dim() != 4 or centers.shape[3] != 3:
+        raise ValueError("centers must be [T, W, S, 3]")
+    T, W, S = centers.shape[:3]
+    if radii.shape != (S,):
+        raise ValueError("radii must be [S]")
+    dev = centers.device
+    cost = torch.empty(T, dtype=torch.float32, device=dev)
+    dist = torch.empty((T, W, S), dtype=torch.float32, device=dev)
+    argmin = torch.empty((T, W, S), dtype=torch.int32, device=dev)
+    best, ms = _LaunchCfg(), C.c_float()
+    _check(_load().capt_autotune_clearance(tree.h, _dev(centers, torch.float32, "centers"),
+                                           _dev(radii, torch.float32, "radii"), T, W, S, float(margin),
+                                           _dev(cost, torch.float32, "cost"), _dev(dist, torch.float32, "dist"),
+                                           _dev(argmin, torch.int32, "argmin"), _stream(stream), C.byref(best),
+                                           C.byref(ms)), "capt_autotune_clearance")
+    return {k: getattr(best, k) for k, _ in _LaunchCfg._fields_}, ms.value
 
 
 def capt_clearance_bwd(tree: CaptTree, centers, radii, dist, argmin, grad_cost, margin: float, grad=None,

@@ -58,7 +58,6 @@ bool valid_cfg(int kernel, const capt_launch_cfg& c) {
     if (c.prefetch < 0 || c.prefetch > CAPT_MAX_PREFETCH) return false;
     if (c.prefetch != 0 && kernel != CAPT_KERNEL_CONFIGS && kernel != CAPT_KERNEL_CLEARANCE) return false;
     if (c.grid != 0 && c.grid != 1) return false;
-    if (c.grid != 0 && kernel == CAPT_KERNEL_CLEARANCE) return false;
     const int spl = c.spheres_per_lane;
     const bool scan_mode = c.chunk >= CAPT_SCAN_SETS && c.chunk <= CAPT_SCAN_COMPACT;
     if (kernel == CAPT_KERNEL_SPHERES) return (spl == 1 || spl == 2 || spl == 4 || spl == 8) && scan_mode;
@@ -86,6 +85,7 @@ struct capt_tree {
     void* d_cbox = nullptr;      // chunk boxes (chunk_count(total_blocks) x 8 floats)
     uint8_t* d_grid = nullptr;   // distance-bound grid of capt_build_grid (2 bytes per cell)
     capt::GridShape gshape;
+    capt::NearLists nl;          // nearest-candidate lists of capt_build_near_lists (over the grid)
     int* d_status = nullptr;
     uint64_t total_blocks = 0;
     size_t dev_bytes = 0;
@@ -135,7 +135,7 @@ struct capt_tree {
         cfg[CAPT_KERNEL_SPHERES] = {8, 2, CAPT_STAGE_SMEM, 0};
         cfg[CAPT_KERNEL_CONFIGS] = {4, 8, CAPT_STAGE_GLOBAL, 1};
         cfg[CAPT_KERNEL_EDGES] = {8, 2, CAPT_STAGE_SMEM, 32};
-        cfg[CAPT_KERNEL_CLEARANCE] = {16, 2, CAPT_STAGE_GLOBAL, 0};
+        cfg[CAPT_KERNEL_CLEARANCE] = {16, 2, CAPT_STAGE_GLOBAL, 0, 0, 1};   // lists once built
         cfg[CAPT_KERNEL_JOINTS] = {4, 1, CAPT_STAGE_GLOBAL, 0};
     }
 
@@ -162,6 +162,9 @@ struct capt_tree {
         a.status = d_status;
         a.grid = gshape.cells ? d_grid : nullptr;
         a.g = gshape;
+        a.nl_cell = static_cast<const uint32_t*>(nl.cell);
+        a.nl_cand = static_cast<const uint32_t*>(nl.cand);
+        a.nl_cloud = static_cast<const float*>(nl.cloud);
         a.N = (uint32_t)h.N;
         a.L = h.L;
         a.r_min = h.r_min;
@@ -182,6 +185,7 @@ struct capt_tree {
                         d_set_idx, d_set_begin, d_pruned})
             if (p) cudaFree(p);
         cs.release();
+        nl.release();
         full_dropped = false;
         for (int i = 0; i < kCtrSlots; i++) {
             if (ctr_ev[i]) cudaEventDestroy(ctr_ev[i]);
@@ -583,6 +587,9 @@ int capt_stats(const capt_tree* t, capt_tree_stats* s) {
                        2 * ((uint64_t)t->pipe_cap * sizeof(float) + t->pipe_fbytes) + (uint64_t)t->zc_cap;
     for (int d = 0; d < 3; d++) s->grid_dims[d] = t->gshape.cells ? (uint32_t)t->gshape.n[d] : 0u;
     s->grid_cell = t->gshape.cells ? t->gshape.h : 0.f;
+    s->near_entries = t->nl.entries;
+    s->near_bytes = t->nl.bytes;
+    s->near_fallback_cells = t->nl.fallback_cells;
     s->full_dropped = t->full_dropped ? 1 : 0;
     return CAPT_OK;
 }
@@ -705,6 +712,11 @@ int capt_build_grid(capt_tree* t, uint64_t max_cells, void* stream) {
     DeviceGuard g(t->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const capt::GridShape gs = capt::grid_shape(t->box_lo, t->box_hi, t->h.r_max, t->h.n, max_cells);
+    if (t->nl.cell) {   // the lists belong to the old grid
+        CUDA_TRY(cudaStreamSynchronize(st), "synchronize");
+        t->dev_bytes -= std::min<size_t>(t->dev_bytes, t->nl.bytes);
+        t->nl.release();
+    }
     if (t->d_grid) {
         CUDA_TRY(cudaStreamSynchronize(st), "synchronize");
         cudaFree(t->d_grid);
@@ -753,6 +765,29 @@ int capt_grid_export(const capt_tree* t, capt_grid_info* info, uint8_t* h_cells)
         DeviceGuard dg(t->device);
         CUDA_TRY(cudaMemcpy(h_cells, t->d_grid, 2 * (size_t)g.cells, cudaMemcpyDeviceToHost), "grid D2H");
     }
+    return CAPT_OK;
+}
+
+int capt_build_near_lists(capt_tree* t, void* stream) {
+    int rc = check_full(t);
+    if (rc) return rc;
+    if (t->h.r_min != 0.f) return fail(CAPT_E_STATE, "the nearest-candidate lists need a tree built with r_min = 0");
+    if (t->h.n == 0 || !(t->h.r_max > 0.f)) return CAPT_OK;   // no cloud to be near: nothing to list
+    if (!t->d_grid || t->gshape.cells == 0)
+        return fail(CAPT_E_STATE, "the nearest-candidate lists need the distance-bound grid (capt_build_grid)");
+    std::lock_guard<std::mutex> lk(t->mu);
+    DeviceGuard g(t->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (t->nl.cell) {
+        CUDA_TRY(cudaStreamSynchronize(st), "synchronize");
+        t->dev_bytes -= std::min<size_t>(t->dev_bytes, t->nl.bytes);
+        t->nl.release();
+    }
+    std::string err;
+    capt::DevArgs a = t->args();
+    rc = capt::device_near_lists(a, t->h.n, st, t->nl, err);
+    if (rc) return fail(rc, err);
+    t->dev_bytes += t->nl.bytes;
     return CAPT_OK;
 }
 
@@ -1308,6 +1343,56 @@ int capt_clearance_fwd(const capt_tree* t, const float* d_centers, const float* 
     return rc ? fail(rc, err) : CAPT_OK;
 }
 
+int capt_autotune_clearance(capt_tree* t, const float* d_centers, const float* d_radii, size_t T, int W, int S,
+                            float margin, float* d_cost, float* d_dist, int32_t* d_argmin, void* stream,
+                            capt_launch_cfg* best, float* best_ms) {
+    int rc = check_full(t);
+    if (rc) return rc;
+    if (t->h.r_min != 0.f) return fail(CAPT_E_STATE, "clearance needs a tree built with r_min = 0 (no prune)");
+    if (S < 1 || S > CAPT_MAX_SPHERES || W < 1) return fail(CAPT_E_ARG, "need 1 <= S <= 64 and W >= 1");
+    if (!std::isfinite(margin)) return fail(CAPT_E_ARG, "margin must be finite");
+    if (T == 0) return fail(CAPT_E_ARG, "need T > 0");
+    if (!d_centers || !d_radii || !d_cost || !d_dist || !d_argmin) return fail(CAPT_E_ARG, "NULL device pointer");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0), "event");
+    CUDA_TRY(cudaEventCreate(&e1), "event");
+    float best_t = INFINITY;
+    capt_launch_cfg best_c = t->cfg[CAPT_KERNEL_CLEARANCE];
+    std::string err;
+    for (int warps : {4, 8, 16})
+        for (int stage : {CAPT_STAGE_GLOBAL, CAPT_STAGE_SMEM})
+            for (int pf : {0, 1})
+                for (int grid : {0, 1}) {
+                    if (grid && !t->nl.cell) continue;
+                    const capt_launch_cfg c = {warps, 2, stage, 0, pf, grid};
+                    float tt = INFINITY;
+                    for (int rep = 0; rep < 3; rep++) {
+                        cudaEventRecord(e0, st);
+                        rc = capt::launch_clearance_fwd(t->args(), d_centers, d_radii, T, W, S, margin, d_cost, d_dist,
+                                                        d_argmin, c, st, err);
+                        cudaEventRecord(e1, st);
+                        if (rc) break;
+                        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = CAPT_E_CUDA; break; }
+                        float ms = 0;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        if (rep > 0) tt = std::min(tt, ms);
+                    }
+                    if (rc) {
+                        cudaEventDestroy(e0);
+                        cudaEventDestroy(e1);
+                        return fail(rc, err.empty() ? "autotune failed" : err);
+                    }
+                    if (tt < best_t) { best_t = tt; best_c = c; }
+                }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    t->cfg[CAPT_KERNEL_CLEARANCE] = best_c;
+    if (best) *best = best_c;
+    if (best_ms) *best_ms = best_t;
+    return CAPT_OK;
+}
+
 int capt_count_clearance_work(const capt_tree* t, const float* d_centers, size_t m, uint64_t* d_counts,
                               void* stream) {
     int rc = check_full(t);
@@ -1316,7 +1401,8 @@ int capt_count_clearance_work(const capt_tree* t, const float* d_centers, size_t
     if (m == 0) return CAPT_OK;
     if (!d_centers || !d_counts) return fail(CAPT_E_ARG, "NULL device pointer");
     std::string err;
-    rc = capt::launch_count_clearance(t->args(), d_centers, m, d_counts, static_cast<cudaStream_t>(stream), err);
+    rc = capt::launch_count_clearance(t->args(), d_centers, m, t->cfg[CAPT_KERNEL_CLEARANCE].grid != 0, d_counts,
+                                      static_cast<cudaStream_t>(stream), err);
     return rc ? fail(rc, err) : CAPT_OK;
 }
 

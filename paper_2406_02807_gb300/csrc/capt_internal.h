@@ -77,6 +77,10 @@ struct GridShape {
 };
 GridShape grid_shape(const float lo[3], const float hi[3], float r_max, uint64_t n_points, uint64_t max_cells);
 
+// Entry count of a grid cell whose centres take the paper's path (descent and full set
+// scan) instead of a nearest-candidate list.
+constexpr uint32_t kNearFallback = 0xffffffffu;
+
 // Kernel view of an uploaded tree (raw device pointers, passed by value).
 struct DevArgs {
     const float* T = nullptr;        // blocked split array (BlockedSplits::data)
@@ -103,6 +107,16 @@ struct DevArgs {
     float hi[3] = {-1.f, -1.f, -1.f};
     const uint8_t* grid = nullptr;   // distance-bound grid, 2 g.cells bytes (null: none)
     GridShape g;
+    // nearest-candidate lists of the clearance (null: none): per grid cell two words
+    // {first entry, entries (a multiple of 4), or kNearFallback}, the entries (point
+    // indices, padded with n), and the cloud as 4 floats per point plus a point at
+    // +inf (index n)
+    const uint32_t* nl_cell = nullptr;
+    const uint32_t* nl_cand = nullptr;
+    const float* nl_cloud = nullptr;
+    // always -0: the zero addend of the packed exact products (f2_mulz), passed as an
+    // argument so that the code generator cannot see its value
+    float nzero = -0.f;
 };
 
 }  // namespace capt

@@ -205,18 +205,24 @@ __device__ __forceinline__ void prefetch_l2(const void* p, uint64_t bytes) {
 // Distance-bound grid (dist_grid.cu): 0 when the grid proves that the sphere (x, r)
 // misses every cloud point under the FP32 test, 1 when it proves that it hits one, 2
 // when it cannot tell.
-__device__ __forceinline__ int grid_classify(const DevArgs& t, float x, float y, float z, float r) {
-    const GridShape& g = t.g;
+// Cell of the distance-bound grid that the kernels assign to x: floor(fl(fl(x - org) *
+// inv_h)) per axis, clamped to the grid.  `inside`: x is inside the grid box, and then
+// the cell (grown by h / 100) holds x.
+__device__ __forceinline__ uint32_t grid_cell(const GridShape& g, float x, float y, float z, bool& inside) {
     const float ux = __fmul_rn(__fsub_rn(x, g.org[0]), g.inv_h);
     const float uy = __fmul_rn(__fsub_rn(y, g.org[1]), g.inv_h);
     const float uz = __fmul_rn(__fsub_rn(z, g.org[2]), g.inv_h);
-    // inside the grid box: the cell computed below holds x (grown by h / 100)
-    const bool inside = ux >= 0.f && uy >= 0.f && uz >= 0.f && ux < (float)g.n[0] && uy < (float)g.n[1] &&
-                        uz < (float)g.n[2];
+    inside = ux >= 0.f && uy >= 0.f && uz >= 0.f && ux < (float)g.n[0] && uy < (float)g.n[1] && uz < (float)g.n[2];
     const uint32_t i = (uint32_t)fminf(fmaxf(ux, 0.f), (float)(g.n[0] - 1));
     const uint32_t j = (uint32_t)fminf(fmaxf(uy, 0.f), (float)(g.n[1] - 1));
     const uint32_t k = (uint32_t)fminf(fmaxf(uz, 0.f), (float)(g.n[2] - 1));
-    const uint32_t c = (k * (uint32_t)g.n[1] + j) * (uint32_t)g.n[0] + i;
+    return (k * (uint32_t)g.n[1] + j) * (uint32_t)g.n[0] + i;
+}
+
+__device__ __forceinline__ int grid_classify(const DevArgs& t, float x, float y, float z, float r) {
+    const GridShape& g = t.g;
+    bool inside;
+    const uint32_t c = grid_cell(g, x, y, z, inside);
     const unsigned short q = __ldg(reinterpret_cast<const unsigned short*>(t.grid) + c);
     if (__fmul_rn((float)(q & 0xffu), g.unit) > r) return 0;
     if (inside && (q >> 8) < 255u && __fmul_rn((float)(q >> 8), g.unit) < r) return 1;

@@ -101,25 +101,32 @@ __device__ __forceinline__ void abs_diff_bounds(float a, float b, float& lo, flo
     hi = fmaxf(fabsf(dn), fabsf(up));
 }
 
+// Cell c grown by h / 100 on every side: the box [L, U] (rounded outward), its
+// representative point m and rho >= max |x - m| over the box (rounded up).
+__device__ __forceinline__ void cell_box(const GridShape& g, uint32_t c, float L[3], float U[3], float m[3],
+                                         float& rho) {
+    const uint32_t nx = (uint32_t)g.n[0], ny = (uint32_t)g.n[1];
+    const uint32_t idx[3] = {c % nx, (c / nx) % ny, c / (nx * ny)};
+    const float dl = __fmul_ru(g.h, 0.01f);
+    float rho2 = 0.f;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        L[d] = __fsub_rd(__fadd_rd(g.org[d], __fmul_rd((float)idx[d], g.h)), dl);
+        U[d] = __fadd_ru(__fadd_ru(g.org[d], __fmul_ru((float)(idx[d] + 1u), g.h)), dl);
+        m[d] = __fmul_rn(__fadd_rn(L[d], U[d]), 0.5f);
+        const float e = fmaxf(__fsub_ru(m[d], L[d]), __fsub_ru(U[d], m[d]));
+        rho2 = __fadd_ru(rho2, __fmul_ru(e, e));
+    }
+    rho = __fsqrt_ru(rho2);
+}
+
 // One thread per cell: the bounds of the distance from the grown cell to the cloud,
 // through the cell's representative point m and its leaf's set.
 __global__ void __launch_bounds__(kGridThreads) k_dist_grid(DevArgs t, GridShape g, uchar2* __restrict__ out) {
     const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.cells) return;
-    const uint32_t nx = (uint32_t)g.n[0], ny = (uint32_t)g.n[1];
-    const uint32_t idx[3] = {c % nx, (c / nx) % ny, c / (nx * ny)};
-    const float dl = __fmul_ru(g.h, 0.01f);
-    float m[3];
-    float rho2 = 0.f;
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-        const float L = __fsub_rd(__fadd_rd(g.org[d], __fmul_rd((float)idx[d], g.h)), dl);
-        const float U = __fadd_ru(__fadd_ru(g.org[d], __fmul_ru((float)(idx[d] + 1u), g.h)), dl);
-        m[d] = __fmul_rn(__fadd_rn(L, U), 0.5f);
-        const float e = fmaxf(__fsub_ru(m[d], L), __fsub_ru(U, m[d]));
-        rho2 = __fadd_ru(rho2, __fmul_ru(e, e));
-    }
-    const float rho = __fsqrt_ru(rho2);
+    float L[3], U[3], m[3], rho;
+    cell_box(g, c, L, U, m, rho);
     const uint32_t leaf = descend(m[0], m[1], m[2], t, nullptr);
     float4 a, b;
     load_leaf(t.leaves, leaf, a, b);
@@ -159,6 +166,335 @@ int launch_dist_grid(const DevArgs& t, const GridShape& g, uint8_t* out, cudaStr
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) { err = std::string("distance grid launch: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
     return CAPT_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// Nearest-candidate lists of the clearance (this build's addition; the paper's
+// clearance scans the whole set of the centre's leaf, Lemma 1 case 1).
+//
+// For each cell C of the grid (grown by h / 100, centre m, rho as above) the list holds
+// the cloud points of the sets of every leaf whose closed cell meets C that lie within
+//   R_C = min(ub_C, r_max) (1 + 2^-20) + rho          (rounded up)
+// of m, each point once; ub_C is the grid's rounded-up upper bound of the distance
+// from C to the cloud.  Why a centre x of C gets the paper's answer from its cell's
+// list (the FP32 argmin over the list, ties to the lowest point index):
+//  a. The paper's answer is p*, the lowest-index point of minimal FP32 squared
+//     distance in S_x, the set of x's leaf, reported when its distance is below r_max.
+//     x lies in C (argument 1 above) and in the closed cell of its leaf, so that leaf
+//     meets C and S_x is among the sets the list is cut from.
+//  b. A reported p* has |x - p*| < r_max (1 + 2.5e-7) (five rounded operations and a
+//     rounded square root).  Then D(x) < r_max (1 + 1e-5), so the nearest cloud point
+//     is in S_x (the builder's affordance radius) and |x - p*| <= D(x) (1 + 3e-7) <=
+//     ub_C (1 + 3e-7).  So |m - p*| <= |x - p*| + rho <= R_C: p* is in the list.
+//  c. Any point p that beats p* in FP32, or is reportable at all, lies within
+//     r_max (1 + 2.5e-7) of x and therefore in S_x, where p* already beats it.  So the
+//     argmin over the list is p*, and when the paper reports nothing no list point is
+//     reportable either: the distance and index are the paper's, bit for bit (the same
+//     FP32 expression).
+//  d. A centre outside the grid box is farther than r_max + h / 300 from every point:
+//     both paths answer r_max, -1 whatever they scan.
+// Cells that the grid proves farther than r_max from the cloud (the reject rule at
+// r = r_max) get an empty list.  A cell whose leaves or points overflow the builder's
+// per-warp buffers is marked kNearFallback and its centres take the paper's path.
+// The membership test is conservative (the FP32 distance from m rounded down against
+// R_C^2 rounded up), so extra points may enter a list; by c they change nothing.
+// ------------------------------------------------------------------------------------
+
+namespace {
+
+constexpr int kNearThreads = 128;              // four warps, one cell each at a time
+constexpr uint32_t kNearMaxLeaves = 32;        // leaves meeting one cell
+constexpr uint32_t kNearMaxCand = 1024;        // points collected for one cell
+constexpr int kNearScanThreads = 1024;         // cells per block of the offset scan
+
+struct NearScratch {
+    uint32_t leaf[kNearMaxLeaves];
+    uint32_t seg[kNearMaxLeaves + 1];   // first entry of each leaf's points in cand
+    uint32_t cand[kNearMaxCand];
+};
+
+// Split value of the node at depth lev reached by `path` (lev decisions, the first one
+// most significant, 1 = right) in the blocked split array of the descent.
+__device__ __forceinline__ float split_at(const DevArgs& t, int lev, uint32_t path) {
+    const int k = lev / 3, j = lev - 3 * k;
+    if (k < t.K) {
+        uint32_t u = 0;
+        for (int i = 0; i < k; i++) u = 8u * u + 1u + ((path >> (lev - 3 * (i + 1))) & 7u);
+        const float* b = t.T + 8ull * u;
+        if (j == 0) return __ldg(b);
+        if (j == 1) return __ldg(b + ((path & 1u) ? 2 : 1));
+        return __ldg(b + 3 + 2 * ((path >> 1) & 1u) + (path & 1u));
+    }
+    const uint32_t bits = path >> (lev - 3 * t.K);   // the decisions of the full super-levels
+    const float* q = t.T + (size_t)t.tail_off + 4ull * bits;
+    return j == 0 ? __ldg(q) : __ldg(q + ((path & 1u) ? 2 : 1));
+}
+
+// Warp per cell.  COUNT: cell[2c + 1] = the cell's entries (its points rounded up to a
+// multiple of 4; 0: empty; kNearFallback).  FILL: the entries at cand[cell[2c] ...]
+// (padded with `pad`, the index of the point at +inf); the same deterministic walk
+// finds the same points, and a count that differs is flagged in *bad with no write
+// past the counted entries.
+template <bool FILL>
+__global__ void __launch_bounds__(kNearThreads) k_near_lists(DevArgs t, GridShape g, const uchar2* __restrict__ grid,
+                                                             uint32_t* __restrict__ cell, uint32_t* __restrict__ cand,
+                                                             uint32_t pad, unsigned long long* __restrict__ n_fallback,
+                                                             uint32_t* __restrict__ bad) {
+    __shared__ NearScratch sh[kNearThreads / 32];
+    NearScratch& s = sh[threadIdx.x >> 5];
+    const uint32_t lane = threadIdx.x & 31u, lt = (1u << lane) - 1u;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    const uint64_t pl = 4ull * t.plane;
+    for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < g.cells; c += warps) {
+        const uchar2 q = grid[c];
+        uint32_t result = 0;
+        const uint32_t limit = FILL ? cell[2 * (size_t)c + 1] : 0u;
+        const uint32_t cap = limit == kNearFallback ? 0u : limit;   // entries reserved for the cell
+        const uint32_t base = FILL ? cell[2 * (size_t)c] : 0u;
+        if (!(__fmul_rn((float)q.x, g.unit) > t.r_max)) {
+            float L[3], U[3], m[3], rho;
+            cell_box(g, c, L, U, m, rho);
+            const float R = __fadd_ru(__fmul_ru(fminf(__fmul_ru((float)q.y, g.unit), t.r_max), 1.00000095367431640625f),
+                                      rho);
+            const float R2 = __fmul_ru(R, R);
+            // leaves whose closed cell meets [L, U]: depth-first over the splits, every
+            // lane walking the same nodes (left child: x_d <= T, right child: x_d >= T)
+            uint32_t nl = 0;
+            bool over = false;
+            uint64_t stk[34];
+            int sp = 0;
+            stk[sp++] = 0;
+            while (sp > 0) {
+                const uint64_t e = stk[--sp];
+                const int lev = (int)(e >> 32);
+                const uint32_t path = (uint32_t)e;
+                if (lev == t.L) {
+                    if (nl == kNearMaxLeaves) {
+                        over = true;
+                        break;
+                    }
+                    if (lane == 0) s.leaf[nl] = path;
+                    nl++;
+                    continue;
+                }
+                const float T = split_at(t, lev, path);
+                const int ax = lev % 3;
+                const uint64_t child = (uint64_t)(lev + 1) << 32;
+                if (U[ax] >= T) stk[sp++] = child | ((path << 1) | 1u);
+                if (L[ax] <= T) stk[sp++] = child | (path << 1);
+            }
+            __syncwarp();
+            uint32_t n = 0;
+            if (!over) {
+                // their points within R_C of m, leaf by leaf
+                for (uint32_t k = 0; k < nl; k++) {
+                    if (lane == 0) s.seg[k] = n;
+                    float4 a, b;
+                    load_leaf(t.leaves, s.leaf[k], a, b);
+                    const uint32_t b0 = __float_as_uint(a.w), cnt = __float_as_uint(b.w);
+                    for (uint32_t j0 = 0; j0 < cnt; j0 += 32) {
+                        const uint32_t j = j0 + lane;
+                        bool in = false;
+                        uint32_t id = 0;
+                        if (j < cnt) {
+                            const float* p = t.blocks + 4ull * b0 + j;
+                            float l0, h0, l1, h1, l2, h2;
+                            abs_diff_bounds(m[0], __ldg(p), l0, h0);
+                            abs_diff_bounds(m[1], __ldg(p + pl), l1, h1);
+                            abs_diff_bounds(m[2], __ldg(p + 2 * pl), l2, h2);
+                            const float lo2 = __fadd_rd(__fadd_rd(__fmul_rd(l0, l0), __fmul_rd(l1, l1)), __fmul_rd(l2, l2));
+                            in = lo2 <= R2;
+                            id = __ldg(t.ids + 4ull * b0 + j);
+                        }
+                        const uint32_t mask = __ballot_sync(0xffffffffu, in);
+                        const uint32_t pos = n + __popc(mask & lt);
+                        if (in && pos < kNearMaxCand) s.cand[pos] = id;
+                        n += __popc(mask);
+                    }
+                }
+                if (lane == 0) s.seg[nl] = n;
+                over = n > kNearMaxCand;
+            }
+            __syncwarp();
+            if (over) {
+                result = kNearFallback;
+            } else {
+                // each point once: an entry is dropped when an earlier leaf's points hold it
+                uint32_t u = 0;
+                for (uint32_t i0 = 0; i0 < n; i0 += 32) {
+                    const uint32_t i = i0 + lane;
+                    bool keep = false;
+                    uint32_t id = 0;
+                    if (i < n) {
+                        id = s.cand[i];
+                        uint32_t first = 0;   // start of i's leaf segment
+                        for (uint32_t k = 1; k < nl; k++)
+                            if (s.seg[k] <= i) first = s.seg[k];
+                        keep = true;
+                        for (uint32_t j = 0; j < first; j++)
+                            if (s.cand[j] == id) {
+                                keep = false;
+                                break;
+                            }
+                    }
+                    const uint32_t mask = __ballot_sync(0xffffffffu, keep);
+                    const uint32_t pos = u + __popc(mask & lt);
+                    if constexpr (FILL) {
+                        if (keep && pos < cap) cand[(size_t)base + pos] = id;
+                    }
+                    u += __popc(mask);
+                }
+                result = (u + 3u) & ~3u;
+                if constexpr (FILL) {
+                    for (uint32_t i = u + lane; i < result && i < cap; i += 32) cand[(size_t)base + i] = pad;
+                }
+            }
+            __syncwarp();
+        }
+        if (lane == 0) {
+            if (!FILL) {
+                cell[2 * (size_t)c + 1] = result;
+                if (result == kNearFallback) atomicAdd(n_fallback, 1ull);
+            } else if (result != limit) {
+                atomicOr(bad, 1u);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t near_entries(uint32_t v) { return v == kNearFallback ? 0u : v; }
+
+// Entries of each block of kNearScanThreads cells.
+__global__ void __launch_bounds__(kNearScanThreads) k_near_block_sums(const uint32_t* __restrict__ cell, uint32_t cells,
+                                                                       uint32_t* __restrict__ bsum) {
+    __shared__ uint32_t ws[32];
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t v = i < cells ? near_entries(cell[2 * (size_t)i + 1]) : 0u;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31u) == 0) ws[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t w = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0u;
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if (threadIdx.x == 0) bsum[blockIdx.x] = w;
+    }
+}
+
+// First entry of each cell: the block's exclusive prefix plus the prefix of the blocks
+// before it (boff, 64-bit; the host refuses totals of 2^32 entries or more).
+__global__ void __launch_bounds__(kNearScanThreads) k_near_offsets(uint32_t* __restrict__ cell, uint32_t cells,
+                                                                    const unsigned long long* __restrict__ boff) {
+    __shared__ uint32_t ws[32];
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t v = i < cells ? near_entries(cell[2 * (size_t)i + 1]) : 0u;
+    uint32_t incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += y;
+    }
+    if (lane == 31) ws[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < (blockDim.x >> 5) ? ws[lane] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= (uint32_t)o) w += y;
+        }
+        ws[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t before = (warp ? ws[warp - 1] : 0u) + incl - v;
+    if (i < cells) cell[2 * (size_t)i] = (uint32_t)(boff[blockIdx.x] + before);
+}
+
+// The cloud as 4 floats per point, then one point at +inf (the padding entry).
+__global__ void k_near_cloud(const float* __restrict__ cloud, uint32_t n, float4* __restrict__ out) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_float4(cloud[3 * (size_t)i], cloud[3 * (size_t)i + 1], cloud[3 * (size_t)i + 2], 0.f);
+    else if (i == n) out[i] = make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+}
+
+}  // namespace
+
+void NearLists::release() {
+    for (void* p : {cell, cand, cloud})
+        if (p) cudaFree(p);
+    cell = cand = cloud = nullptr;
+    entries = fallback_cells = 0;
+    bytes = 0;
+}
+
+#define NL_CUDA(call, what)                                              \
+    do {                                                                 \
+        cudaError_t _e = (call);                                         \
+        if (_e != cudaSuccess) {                                         \
+            err = std::string(what) + ": " + cudaGetErrorString(_e);     \
+            rc = _e == cudaErrorMemoryAllocation ? CAPT_E_NOMEM : CAPT_E_CUDA; \
+            goto done;                                                   \
+        }                                                                \
+    } while (0)
+
+int device_near_lists(const DevArgs& t, size_t n, cudaStream_t st, NearLists& out, std::string& err) {
+    out = NearLists();
+    const GridShape& g = t.g;
+    if (!t.grid || g.cells == 0) {
+        err = "the nearest-candidate lists need the distance-bound grid";
+        return CAPT_E_STATE;
+    }
+    int rc = CAPT_OK;
+    const uint32_t nb = (g.cells + kNearScanThreads - 1) / kNearScanThreads;
+    uint32_t* bsum = nullptr;
+    unsigned long long* boff = nullptr;   // nb + 1 offsets, then the fallback count and the bad flag
+    unsigned long long h_tail[3] = {0, 0, 0};
+    unsigned walk_blocks = 0;
+    {
+        int sms = sm_count();
+        walk_blocks = (unsigned)std::min<uint64_t>(((uint64_t)g.cells + 3) / 4, (uint64_t)sms * 16);
+    }
+    NL_CUDA(cudaMalloc(&out.cell, 8 * (size_t)g.cells), "near lists: cell table");
+    NL_CUDA(cudaMalloc((void**)&bsum, 4 * (size_t)nb), "near lists: scratch");
+    NL_CUDA(cudaMalloc((void**)&boff, 8 * ((size_t)nb + 3)), "near lists: scratch");
+    NL_CUDA(cudaMalloc(&out.cloud, 16 * (n + 1)), "near lists: cloud");
+    NL_CUDA(cudaMemsetAsync(boff + nb + 1, 0, 16, st), "near lists: memset");
+    k_near_cloud<<<(unsigned)((n + 1 + 255) / 256), 256, 0, st>>>(t.cloud, (uint32_t)n,
+                                                                  static_cast<float4*>(out.cloud));
+    k_near_lists<false><<<walk_blocks, kNearThreads, 0, st>>>(t, g, reinterpret_cast<const uchar2*>(t.grid),
+                                                               static_cast<uint32_t*>(out.cell), nullptr, 0u,
+                                                               boff + nb + 1, nullptr);
+    k_near_block_sums<<<nb, kNearScanThreads, 0, st>>>(static_cast<const uint32_t*>(out.cell), g.cells, bsum);
+    NL_CUDA(cudaGetLastError(), "near lists: launch");
+    rc = launch_scan64(bsum, nb, boff, st, err);
+    if (rc) goto done;
+    k_near_offsets<<<nb, kNearScanThreads, 0, st>>>(static_cast<uint32_t*>(out.cell), g.cells, boff);
+    NL_CUDA(cudaGetLastError(), "near lists: launch");
+    NL_CUDA(cudaMemcpyAsync(h_tail, boff + nb, 16, cudaMemcpyDeviceToHost, st), "near lists: D2H");
+    NL_CUDA(cudaStreamSynchronize(st), "near lists: count");
+    if (h_tail[0] >= (1ull << 32)) {
+        err = "the nearest-candidate lists would hold 2^32 entries or more (use a coarser grid)";
+        rc = CAPT_E_RANGE;
+        goto done;
+    }
+    out.entries = h_tail[0];
+    out.fallback_cells = h_tail[1];
+    NL_CUDA(cudaMalloc(&out.cand, 4 * std::max<size_t>((size_t)out.entries, 4)), "near lists: entries");
+    k_near_lists<true><<<walk_blocks, kNearThreads, 0, st>>>(
+        t, g, reinterpret_cast<const uchar2*>(t.grid), static_cast<uint32_t*>(out.cell),
+        static_cast<uint32_t*>(out.cand), (uint32_t)n, nullptr, reinterpret_cast<uint32_t*>(boff + nb + 2));
+    NL_CUDA(cudaGetLastError(), "near lists: launch");
+    NL_CUDA(cudaMemcpyAsync(h_tail + 2, boff + nb + 2, 8, cudaMemcpyDeviceToHost, st), "near lists: D2H");
+    NL_CUDA(cudaStreamSynchronize(st), "near lists: fill");
+    if (h_tail[2] != 0) {
+        err = "nearest-candidate lists: the fill walk disagreed with the count walk";
+        rc = CAPT_E_BOUNDS;
+        goto done;
+    }
+    out.bytes = 8 * (size_t)g.cells + 4 * std::max<size_t>((size_t)out.entries, 4) + 16 * (n + 1);
+done:
+    if (bsum) cudaFree(bsum);
+    if (boff) cudaFree(boff);
+    if (rc) out.release();
+    return rc;
 }
 
 }  // namespace capt

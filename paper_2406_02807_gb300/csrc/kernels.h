@@ -28,10 +28,25 @@ int launch_chunk_boxes(const float* blocks, uint64_t total_blocks, float* cbox, 
 int launch_leaves(const DevArgs& t, const float* centers, uint64_t m, uint32_t* leaves, cudaStream_t st,
                   std::string& err);
 
-// Clearance forward / backward.
+// Distance-bound grid: 2 bytes per cell of g (dist_grid.cu).
 int launch_dist_grid(const DevArgs& t, const GridShape& g, uint8_t* out, cudaStream_t st, std::string& err);
-int launch_count_clearance(const DevArgs& t, const float* centers, uint64_t m, uint64_t* counts, cudaStream_t st,
-                           std::string& err);
+
+// Nearest-candidate lists of the clearance over the tree's grid (dist_grid.cu): device
+// buffers owned by the tree once built (release() frees them).
+struct NearLists {
+    void* cell = nullptr;    // 2 uint32 per grid cell: {first entry, entries or kNearFallback}
+    void* cand = nullptr;    // uint32 point indices, each list padded to a multiple of 4 with n
+    void* cloud = nullptr;   // float4 per point, then one at +inf
+    uint64_t entries = 0, fallback_cells = 0;
+    size_t bytes = 0;
+    void release();
+};
+// Builds them from the tree's grid, sets and cloud (n points).  Synchronises st.
+int device_near_lists(const DevArgs& t, size_t n, cudaStream_t st, NearLists& out, std::string& err);
+
+// Clearance forward / backward.
+int launch_count_clearance(const DevArgs& t, const float* centers, uint64_t m, bool lists, uint64_t* counts,
+                           cudaStream_t st, std::string& err);
 int launch_clearance_fwd(const DevArgs& t, const float* centers, const float* radii, uint64_t T, int W, int S,
                          float margin, float* cost, float* dist, int32_t* argmin, const capt_launch_cfg& cfg,
                          cudaStream_t st, std::string& err);

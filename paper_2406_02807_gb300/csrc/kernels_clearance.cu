@@ -45,6 +45,20 @@ struct ClearScratch {
 // (the common case) takes one step, all its loads in flight together.
 constexpr int kClearV = 3;
 
+// Key of cloud point i for centre c on the nearest-candidate lists: the FP32 squared
+// distance of the paper's scan (the same expression as block_d2, so the same bits) and
+// the point index, so that the smallest key is the lowest-index nearest point.
+__device__ __forceinline__ unsigned long long near_key(const float* __restrict__ cloud4, uint32_t i, const float4& c) {
+    const float4 p = __ldg(reinterpret_cast<const float4*>(cloud4) + i);
+    const float dx = __fsub_rn(p.x, c.x), dy = __fsub_rn(p.y, c.y), dz = __fsub_rn(p.z, c.z);
+    const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    return ((unsigned long long)__float_as_uint(d2) << 32) | i;
+}
+
+// With LISTS, a queued sphere first looks up its grid cell's nearest-candidate list
+// (capt_build_near_lists): an empty list answers r_max, -1; a list is scanned by the
+// sphere's own lane, four entries per 16-byte load, and gives the paper's answer bit for
+// bit (the argument is in dist_grid.cu); only the spheres of fallback cells go on below.
 // One round over the first n queued spheres of the trajectory at `tbase` (sphere index
 // offset of the trajectory in dist / argmin).  Each lane descends for its sphere and
 // applies the leaf box test against r_max; spheres that fail get d = r_max at once, the
@@ -55,6 +69,7 @@ constexpr int kClearV = 3;
 // to the lowest slot, i.e. the lowest point index.  Once every entry is scanned, lane e
 // turns entry e's key into its distance and point index (the index loads of all entries
 // in flight together) and writes them.
+template <bool LISTS>
 __device__ __forceinline__ void clearance_round(const DevArgs& t, const float* Ts, ClearScratch* ws, uint32_t n,
                                                 uint64_t tbase, float rmax, float rmax2, float* __restrict__ dist,
                                                 int32_t* __restrict__ argmin, uint32_t lane, uint32_t lt_mask) {
@@ -64,9 +79,39 @@ __device__ __forceinline__ void clearance_round(const DevArgs& t, const float* T
     uint32_t nb = 0, fb = 0;
     uint64_t gi = 0;
     float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool paper = live;
     if (live) {
         c = ws->nq[lane];
         gi = ws->ni[lane];
+    }
+    if constexpr (LISTS) {
+        if (live) {
+            bool inside;
+            const uint2 rec = __ldg(reinterpret_cast<const uint2*>(t.nl_cell) + grid_cell(t.g, c.x, c.y, c.z, inside));
+            if (rec.y != kNearFallback) {
+                paper = false;
+                unsigned long long best = ~0ull;
+                const uint4* e = reinterpret_cast<const uint4*>(t.nl_cand + rec.x);
+                for (uint32_t j = 0; j < rec.y / 4u; j++) {
+                    const uint4 ix = __ldg(e + j);
+                    const unsigned long long k0 = near_key(t.nl_cloud, ix.x, c), k1 = near_key(t.nl_cloud, ix.y, c);
+                    const unsigned long long k2 = near_key(t.nl_cloud, ix.z, c), k3 = near_key(t.nl_cloud, ix.w, c);
+                    const unsigned long long a01 = k0 < k1 ? k0 : k1, a23 = k2 < k3 ? k2 : k3;
+                    const unsigned long long a4 = a01 < a23 ? a01 : a23;
+                    best = a4 < best ? a4 : best;
+                }
+                const float dd = rec.y ? __fsqrt_rn(__uint_as_float((uint32_t)(best >> 32))) : rmax;
+                if (dd < rmax) {
+                    dist[tbase + gi] = dd;
+                    argmin[tbase + gi] = (int32_t)(uint32_t)best;
+                } else {
+                    dist[tbase + gi] = rmax;
+                    argmin[tbase + gi] = -1;
+                }
+            }
+        }
+    }
+    if (paper) {
         const uint32_t leaf = descend(c.x, c.y, c.z, t, Ts);
         float4 a, b;
         load_leaf(t.leaves, leaf, a, b);
@@ -106,14 +151,15 @@ __device__ __forceinline__ void clearance_round(const DevArgs& t, const float* T
         const float4 ce = ws->ec[e];
         const uint32_t b0 = ws->eb0[e];
         const uint32_t nbs = ws->enb[e];
-        const uint64_t cxx = f2_dup(ce.x), cyy = f2_dup(ce.y), czz = f2_dup(ce.z);
+        const uint64_t cxx = f2_dup(ce.x), cyy = f2_dup(ce.y), czz = f2_dup(ce.z), z2 = f2_dup(t.nzero);
         unsigned long long best = ~0ull;
         for (uint32_t r = lane; r < nbs; r += 32 * kClearV) {
             uint64_t s01[kClearV], s23[kClearV];
 #pragma unroll
             for (int v = 0; v < kClearV; v++) {
                 s01[v] = s23[v] = ~0ull;
-                if (r + 32u * v < nbs) block_d2(blocks, t.plane, (int64_t)b0 + r + 32u * v, cxx, cyy, czz, s01[v], s23[v]);
+                if (r + 32u * v < nbs)
+                    block_d2(blocks, t.plane, (int64_t)b0 + r + 32u * v, cxx, cyy, czz, z2, s01[v], s23[v]);
             }
 #pragma unroll
             for (int v = 0; v < kClearV; v++) {
@@ -152,7 +198,7 @@ __device__ __forceinline__ void clearance_round(const DevArgs& t, const float* T
     __syncwarp();
 }
 
-template <bool STAGE>
+template <bool STAGE, bool LISTS>
 __global__ void __launch_bounds__(512, 2) k_clearance_dist(DevArgs t, const float* __restrict__ centers, int W,
                                                            int S, float* __restrict__ dist,
                                                            int32_t* __restrict__ argmin, uint32_t pf_blocks) {
@@ -239,7 +285,7 @@ __global__ void __launch_bounds__(512, 2) k_clearance_dist(DevArgs t, const floa
                     ws->ni[lane] = ii;
                     __syncwarp();
                 }
-                clearance_round(t, Ts, ws, 32, 0, rmax, rmax2, dist, argmin, lane, lt_mask);
+                clearance_round<LISTS>(t, Ts, ws, 32, 0, rmax, rmax2, dist, argmin, lane, lt_mask);
             }
             const uint32_t rest = n_q - r0;
             float4 cc = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -259,7 +305,7 @@ __global__ void __launch_bounds__(512, 2) k_clearance_dist(DevArgs t, const floa
     }
     if (n_q) {
         __syncwarp();
-        clearance_round(t, Ts, ws, n_q, 0, rmax, rmax2, dist, argmin, lane, lt_mask);
+        clearance_round<LISTS>(t, Ts, ws, n_q, 0, rmax, rmax2, dist, argmin, lane, lt_mask);
     }
 }
 
@@ -325,52 +371,63 @@ __global__ void k_clearance_bwd(DevArgs t, const float* __restrict__ centers, co
 // bounding box at r_max; a sphere within r_max of it descends and gets the leaf box
 // test at r_max; a sphere passing that scans its whole set (no early exit: the
 // nearest point is wanted).  counts += [spheres, spheres near the cloud box, spheres
-// passing the leaf box, points scanned, blocks scanned (4 slots each)].
-__global__ void k_count_clearance(DevArgs t, const float* __restrict__ centers, uint64_t m,
+// passing the leaf box, points scanned, blocks scanned (4 slots each)].  With LISTS the
+// near spheres first look up their cell: counts[5] += those answered by a list (an
+// empty one included), counts[6] += list entries scanned, counts[7] += those of
+// fallback cells, and only these descend (entries 2-4 count their work).
+__global__ void k_count_clearance(DevArgs t, const float* __restrict__ centers, uint64_t m, bool lists,
                                   unsigned long long* counts) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long nsph = 0, nnear = 0, npass = 0, npts = 0, nblk = 0;
+    unsigned long long v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const float rmax2 = __fmul_rn(t.r_max, t.r_max);
     const float4 rlo = make_float4(t.lo[0], t.lo[1], t.lo[2], 0.f);
     const float4 rhi = make_float4(t.hi[0], t.hi[1], t.hi[2], 0.f);
     if (i < m) {
         const float x = centers[3 * i], y = centers[3 * i + 1], z = centers[3 * i + 2];
-        nsph = 1;
+        v[0] = 1;
         if (box_dist2(x, y, z, rlo, rhi) <= rmax2) {
-            nnear = 1;
-            const uint32_t leaf = descend(x, y, z, t, nullptr);
-            float4 a, b;
-            load_leaf(t.leaves, leaf, a, b);
-            const uint32_t cnt = __float_as_uint(b.w);
-            if (cnt > 0 && box_dist2(x, y, z, a, b) <= rmax2) {
-                npass = 1;
-                npts = cnt;
-                nblk = (cnt + 3u) / 4u;
+            v[1] = 1;
+            bool paper = true;
+            if (lists) {
+                bool inside;
+                const uint2 rec = reinterpret_cast<const uint2*>(t.nl_cell)[grid_cell(t.g, x, y, z, inside)];
+                if (rec.y != kNearFallback) {
+                    paper = false;
+                    v[5] = 1;
+                    v[6] = rec.y;
+                } else {
+                    v[7] = 1;
+                }
+            }
+            if (paper) {
+                const uint32_t leaf = descend(x, y, z, t, nullptr);
+                float4 a, b;
+                load_leaf(t.leaves, leaf, a, b);
+                const uint32_t cnt = __float_as_uint(b.w);
+                if (cnt > 0 && box_dist2(x, y, z, a, b) <= rmax2) {
+                    v[2] = 1;
+                    v[3] = cnt;
+                    v[4] = (cnt + 3u) / 4u;
+                }
             }
         }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        nsph += __shfl_xor_sync(0xffffffffu, nsph, o);
-        nnear += __shfl_xor_sync(0xffffffffu, nnear, o);
-        npass += __shfl_xor_sync(0xffffffffu, npass, o);
-        npts += __shfl_xor_sync(0xffffffffu, npts, o);
-        nblk += __shfl_xor_sync(0xffffffffu, nblk, o);
-    }
-    if ((threadIdx.x & 31) == 0 && nsph) {
-        atomicAdd(counts, nsph);
-        atomicAdd(counts + 1, nnear);
-        atomicAdd(counts + 2, npass);
-        atomicAdd(counts + 3, npts);
-        atomicAdd(counts + 4, nblk);
+#pragma unroll
+    for (int k = 0; k < 8; k++)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if ((threadIdx.x & 31) == 0 && v[0]) {
+#pragma unroll
+        for (int k = 0; k < 8; k++)
+            if (v[k]) atomicAdd(counts + k, v[k]);
     }
 }
 
-int launch_count_clearance(const DevArgs& t, const float* centers, uint64_t m, uint64_t* counts, cudaStream_t st,
-                           std::string& err) {
+int launch_count_clearance(const DevArgs& t, const float* centers, uint64_t m, bool lists, uint64_t* counts,
+                           cudaStream_t st, std::string& err) {
     if (m == 0) return CAPT_OK;
     const unsigned threads = 256;
     k_count_clearance<<<(unsigned)((m + threads - 1) / threads), threads, 0, st>>>(
-        t, centers, m, reinterpret_cast<unsigned long long*>(counts));
+        t, centers, m, lists && t.nl_cell, reinterpret_cast<unsigned long long*>(counts));
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) { err = std::string("clearance count launch: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
     return CAPT_OK;
@@ -383,7 +440,9 @@ int launch_clearance_fwd(const DevArgs& t, const float* centers, const float* ra
     if (W > 8192) { err = "clearance takes at most 8192 waypoints per trajectory"; return CAPT_E_ARG; }
     if (T > 0x7fffffffull) { err = "too many trajectories for one launch"; return CAPT_E_ARG; }
     const bool stage = cfg.staging == CAPT_STAGE_SMEM && t.stage_floats > 0;
-    auto fn = stage ? k_clearance_dist<true> : k_clearance_dist<false>;
+    const bool lists = cfg.grid && t.nl_cell;
+    auto fn = stage ? (lists ? k_clearance_dist<true, true> : k_clearance_dist<true, false>)
+                    : (lists ? k_clearance_dist<false, true> : k_clearance_dist<false, false>);
     const int warps = std::max(1, std::min(16, std::min((int)cfg.warps_per_block, W)));
     const size_t smem = (stage ? stage_offset(t) : 0u) + sizeof(ClearScratch) * (size_t)warps;
     cudaError_t ce = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

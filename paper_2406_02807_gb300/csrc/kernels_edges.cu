@@ -159,12 +159,14 @@ __device__ __forceinline__ float row_dot(const float R[9], int r, float v0, floa
 }
 
 // Centres p + R o of one link's points: x and y as an FP32x2 pair (each element the
-// scalar expression p_r + ((R_r0 o_0 + R_r1 o_1) + R_r2 o_2), rounded the same way), z
-// alone.  Set up once per link from its frame.
+// scalar expression p_r + ((R_r0 o_0 + R_r1 o_1) + R_r2 o_2), rounded the same way: the
+// products by f2_mulz, so that none is fused into its sum), z alone.  Set up once per
+// link from its frame; nzero is DevArgs::nzero.
 struct LinkXform {
-    uint64_t c0, c1, c2, p01;   // {R00, R10}, {R01, R11}, {R02, R12}, {p0, p1}
+    uint64_t c0, c1, c2, p01, z2;   // {R00, R10}, {R01, R11}, {R02, R12}, {p0, p1}, {-0, -0}
     float r20, r21, r22, p2;
-    __device__ __forceinline__ void set(const float R[9], const float p[3]) {
+    __device__ __forceinline__ void set(const float R[9], const float p[3], float nzero) {
+        z2 = f2_dup(nzero);
         asm("mov.b64 %0, {%1, %2};" : "=l"(c0) : "f"(R[0]), "f"(R[3]));
         asm("mov.b64 %0, {%1, %2};" : "=l"(c1) : "f"(R[1]), "f"(R[4]));
         asm("mov.b64 %0, {%1, %2};" : "=l"(c2) : "f"(R[2]), "f"(R[5]));
@@ -175,8 +177,8 @@ struct LinkXform {
         p2 = p[2];
     }
     __device__ __forceinline__ void apply(float ox, float oy, float oz, float& cx, float& cy, float& cz) const {
-        const uint64_t xy =
-            f2_add(p01, f2_add(f2_add(f2_mul(c0, f2_dup(ox)), f2_mul(c1, f2_dup(oy))), f2_mul(c2, f2_dup(oz))));
+        const uint64_t xy = f2_add(
+            p01, f2_add(f2_add(f2_mulz(c0, f2_dup(ox), z2), f2_mulz(c1, f2_dup(oy), z2)), f2_mulz(c2, f2_dup(oz), z2)));
         const float2 v = f2_split(xy);
         cx = v.x;
         cy = v.y;
@@ -563,7 +565,7 @@ __global__ void __launch_bounds__(512, 2) k_joint_configs(DevArgs t, const __gri
             sincos_cw(live ? __ldg(qk + j) : 0.f, sj, cj);
             rotate_frame(R, arm.axis[j], sj, cj);
             LinkXform X;
-            X.set(R, p);
+            X.set(R, p, t.nzero);
             for (int i = arm.sbeg[j]; i < arm.sbeg[j + 1]; i++) {
                 const float ox = arm.off[i][0], oy = arm.off[i][1], oz = arm.off[i][2];
                 float cx, cy, cz;

@@ -19,6 +19,13 @@ namespace capt {
 
 // Packed FP32x2 arithmetic: two IEEE-rounded FP32 operations per instruction; the
 // element results are bitwise those of the scalar __fsub_rn / __fmul_rn / __fadd_rn.
+// One trap: the code generator fuses a packed multiply whose product has a single use
+// into the packed add (or sub, or fma) that consumes it, whatever rounding modifier
+// either carries, and a fused multiply-add rounds the sum of products once instead of
+// twice (measured on sm_103a: about a fifth of the squared distances changed).  So a
+// product that feeds a sum is formed by f2_mulz, an fma with a zero addend that only
+// the kernel's arguments know (DevArgs::nzero = -0): fl(a * b + (-0)) = fl(a * b)
+// exactly, and an fma is never fused into the add after it.
 __device__ __forceinline__ uint64_t f2_dup(float a) {
     uint64_t r;
     asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(a));
@@ -29,14 +36,15 @@ __device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
-__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
-    uint64_t d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
 __device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
     uint64_t d;
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+// a * b rounded, element by element; z = f2_dup(t.nzero)
+__device__ __forceinline__ uint64_t f2_mulz(uint64_t a, uint64_t b, uint64_t z) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(z));
     return d;
 }
 __device__ __forceinline__ float2 f2_split(uint64_t v) {
@@ -49,26 +57,17 @@ __device__ __forceinline__ float2 f2_split(uint64_t v) {
 // block b: ((p_x - c_x)^2 + (p_y - c_y)^2) + (p_z - c_z)^2 per point, each operation
 // rounded; p - c is the exact negation of c - p, so the squares are those of the
 // defining expression.  Returns the pairs (points 0,1) and (points 2,3).
-// The block's quads live in three planes `plane` float4s apart.
+// The block's quads live in three planes `plane` float4s apart; z = f2_dup(t.nzero).
 __device__ __forceinline__ void block_d2(const float4* __restrict__ blocks, uint64_t plane, int64_t b, uint64_t cxx,
-                                         uint64_t cyy, uint64_t czz, uint64_t& s01, uint64_t& s23) {
+                                         uint64_t cyy, uint64_t czz, uint64_t z, uint64_t& s01, uint64_t& s23) {
     const ulonglong2 px = __ldg(reinterpret_cast<const ulonglong2*>(blocks + b));
     const ulonglong2 py = __ldg(reinterpret_cast<const ulonglong2*>(blocks + plane + b));
     const ulonglong2 pz = __ldg(reinterpret_cast<const ulonglong2*>(blocks + 2 * plane + b));
     const uint64_t x01 = f2_sub(px.x, cxx), x23 = f2_sub(px.y, cxx);
     const uint64_t y01 = f2_sub(py.x, cyy), y23 = f2_sub(py.y, cyy);
     const uint64_t z01 = f2_sub(pz.x, czz), z23 = f2_sub(pz.y, czz);
-    s01 = f2_add(f2_add(f2_mul(x01, x01), f2_mul(y01, y01)), f2_mul(z01, z01));
-    s23 = f2_add(f2_add(f2_mul(x23, x23), f2_mul(y23, y23)), f2_mul(z23, z23));
-}
-
-// Does any of the four points of block b lie within r2 of the centre?
-__device__ __forceinline__ bool block_hit2(const float4* __restrict__ blocks, uint64_t plane, int64_t b, uint64_t cxx,
-                                           uint64_t cyy, uint64_t czz, float r2) {
-    uint64_t s01, s23;
-    block_d2(blocks, plane, b, cxx, cyy, czz, s01, s23);
-    const float2 a = f2_split(s01), c = f2_split(s23);
-    return (a.x <= r2) | (a.y <= r2) | (c.x <= r2) | (c.y <= r2);
+    s01 = f2_add(f2_add(f2_mulz(x01, x01, z), f2_mulz(y01, y01, z)), f2_mulz(z01, z01, z));
+    s23 = f2_add(f2_add(f2_mulz(x23, x23, z), f2_mulz(y23, y23, z)), f2_mulz(z23, z23, z));
 }
 
 // Per-warp storage of one round.
@@ -192,7 +191,8 @@ __device__ __forceinline__ bool round_chunked(const DevArgs& t, const float* Ts,
                     gv[v] = re->grp[it.x];
                     if ((COMPACT || (b >= re->b0[it.x] && b < re->b1[it.x])) && (SINGLE || !ghit[gv[v]])) {
                         const float4 ce = re->c[it.x];
-                        block_d2(blocks, plane, (int64_t)b, f2_dup(ce.x), f2_dup(ce.y), f2_dup(ce.z), s01[v], s23[v]);
+                        block_d2(blocks, plane, (int64_t)b, f2_dup(ce.x), f2_dup(ce.y), f2_dup(ce.z), f2_dup(t.nzero), s01[v],
+                                 s23[v]);
                         r2v[v] = ce.w;
                         v_ok[v] = true;
                     }
@@ -275,14 +275,14 @@ __device__ __forceinline__ bool round_plain(const DevArgs& t, const float* Ts, R
         const uint32_t b_end = re->end[e];
         const uint32_t b_beg = e ? re->end[e - 1] : 0u;
         const int64_t o = (int64_t)re->boff[e];
-        const uint64_t cxx = f2_dup(ce.x), cyy = f2_dup(ce.y), czz = f2_dup(ce.z);
+        const uint64_t cxx = f2_dup(ce.x), cyy = f2_dup(ce.y), czz = f2_dup(ce.z), z2 = f2_dup(t.nzero);
         bool hit = false;
         for (uint32_t p = b_beg + lane; __any_sync(0xffffffffu, p < b_end); p += 32 * V) {
             uint64_t s01[V], s23[V];
 #pragma unroll
             for (int v = 0; v < V; v++) {
                 s01[v] = s23[v] = 0;
-                if (p + 32 * v < b_end) block_d2(blocks, t.plane, o + p + 32 * v, cxx, cyy, czz, s01[v], s23[v]);
+                if (p + 32 * v < b_end) block_d2(blocks, t.plane, o + p + 32 * v, cxx, cyy, czz, z2, s01[v], s23[v]);
             }
             bool h = false;
 #pragma unroll
@@ -341,7 +341,7 @@ __device__ __forceinline__ bool round_plain(const DevArgs& t, const float* Ts, R
             s01[u] = s23[u] = 0;
             if (live[u])
                 block_d2(blocks, t.plane, (int64_t)oo[u] + base + lane + 32u * u, f2_dup(cc[u].x), f2_dup(cc[u].y),
-                         f2_dup(cc[u].z), s01[u], s23[u]);
+                         f2_dup(cc[u].z), f2_dup(t.nzero), s01[u], s23[u]);
         }
         bool h = false;
 #pragma unroll

@@ -247,7 +247,7 @@ def test_clearance_work_counters_match_oracle_tree(tabletop, orc, capt_lib, torc
     ok = near & (cnt[leaf] > 0) & (box_d2(c, lb[:, :3], lb[:, 3:]) <= r2)
     want = [len(c), int(near.sum()), int(ok.sum()), int(cnt[leaf][ok].sum()), int(((cnt[leaf][ok] + 3) // 4).sum())]
     g = capt_lib.capt_count_clearance_work(tabletop["ctree"], _cuda(torch_, c)).cpu().numpy()
-    assert g.tolist() == want
+    assert g.tolist() == want + [0, 0, 0]   # no nearest-candidate lists on this tree
     assert want[2] > 0
 
 
