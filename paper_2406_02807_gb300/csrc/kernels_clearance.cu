@@ -198,10 +198,145 @@ __device__ __forceinline__ void clearance_round(const DevArgs& t, const float* T
     __syncwarp();
 }
 
-template <bool STAGE, bool LISTS>
+// One pass over the spheres [p0, p0 + 128) of [.., s_hi) of the trajectory whose first
+// sphere is tbase (4 per lane, three 16-byte loads): a sphere farther than r_max from
+// the cloud's bounding box is farther than r_max from every point and gets d = r_max,
+// argmin = -1 at once (one 16-byte store per output when all four of a lane's spheres
+// are that far); the others are queued (centre and global index).
+__device__ __forceinline__ void clearance_pass(const float* __restrict__ centers, uint64_t tbase, uint32_t p0,
+                                               uint32_t s_hi, const float4& rlo, const float4& rhi, float rmax,
+                                               float rmax2, float* __restrict__ dist, int32_t* __restrict__ argmin,
+                                               ClearScratch* ws, uint32_t& n_q, uint32_t lane, uint32_t lt_mask) {
+    const uint64_t i0 = tbase + p0 + 4 * lane;
+    const uint32_t nv = p0 + 4 * lane < s_hi ? min(4u, s_hi - (p0 + 4 * lane)) : 0u;
+    const float* src = centers + 3 * i0;
+    float v[12];
+    if (nv == 4 && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0)) {
+        const float4* q = reinterpret_cast<const float4*>(src);
+        const float4 a = __ldg(q), b = __ldg(q + 1), cc = __ldg(q + 2);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        v[8] = cc.x; v[9] = cc.y; v[10] = cc.z; v[11] = cc.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 12; k++) v[k] = (uint32_t)(k / 3) < nv ? __ldg(src + k) : 0.f;
+    }
+    bool nr[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        nr[k] = (uint32_t)k < nv && box_dist2(v[3 * k], v[3 * k + 1], v[3 * k + 2], rlo, rhi) <= rmax2;
+    const bool all_far = nv == 4 && !(nr[0] | nr[1] | nr[2] | nr[3]) &&
+                         ((reinterpret_cast<uintptr_t>(dist + i0) | reinterpret_cast<uintptr_t>(argmin + i0)) & 15u) == 0;
+    if (all_far) {
+        *reinterpret_cast<float4*>(dist + i0) = make_float4(rmax, rmax, rmax, rmax);
+        *reinterpret_cast<int4*>(argmin + i0) = make_int4(-1, -1, -1, -1);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const bool near = nr[k];
+        if ((uint32_t)k < nv && !near && !all_far) {
+            dist[i0 + k] = rmax;
+            argmin[i0 + k] = -1;
+        }
+        const uint32_t mask = __ballot_sync(0xffffffffu, near);
+        if (near) {
+            const uint32_t pos = n_q + __popc(mask & lt_mask);
+            ws->nq[pos] = make_float4(v[3 * k], v[3 * k + 1], v[3 * k + 2], 0.f);
+            ws->ni[pos] = i0 + k;
+        }
+        n_q += __popc(mask);
+    }
+}
+
+// Rounds of 32 while at least 32 spheres are queued; the rest moves to the front.
+template <bool LISTS>
+__device__ __forceinline__ void clearance_drain(const DevArgs& t, const float* Ts, ClearScratch* ws, uint32_t& n_q,
+                                                float rmax, float rmax2, float* __restrict__ dist,
+                                                int32_t* __restrict__ argmin, uint32_t lane, uint32_t lt_mask) {
+    __syncwarp();
+    uint32_t r0 = 0;
+    for (; n_q - r0 >= 32; r0 += 32) {
+        if (r0) {
+            const float4 cc = ws->nq[r0 + lane];
+            const unsigned long long ii = ws->ni[r0 + lane];
+            __syncwarp();
+            ws->nq[lane] = cc;
+            ws->ni[lane] = ii;
+            __syncwarp();
+        }
+        clearance_round<LISTS>(t, Ts, ws, 32, 0, rmax, rmax2, dist, argmin, lane, lt_mask);
+    }
+    const uint32_t rest = n_q - r0;
+    float4 cc = make_float4(0.f, 0.f, 0.f, 0.f);
+    unsigned long long ii = 0;
+    if (lane < rest) {
+        cc = ws->nq[r0 + lane];
+        ii = ws->ni[r0 + lane];
+    }
+    __syncwarp();
+    if (lane < rest) {
+        ws->nq[lane] = cc;
+        ws->ni[lane] = ii;
+    }
+    n_q = rest;
+    __syncwarp();
+}
+
+// The cost term of one waypoint: sphere s = lane + 32 m (distances a for s = lane, b
+// for s = lane + 32) summed by its lane, then a butterfly (every lane ends with it).
+__device__ __forceinline__ float waypoint_term(float a, float b, int S, float rm0, float rm1, uint32_t lane) {
+    float term = 0.f;
+    if (lane < (uint32_t)S) {
+        const float hh = fmaxf(0.f, __fsub_rn(rm0, a));
+        term = __fadd_rn(term, __fmul_rn(hh, hh));
+    }
+    if (lane + 32 < (uint32_t)S) {
+        const float hh = fmaxf(0.f, __fsub_rn(rm1, b));
+        term = __fadd_rn(term, __fmul_rn(hh, hh));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) term = __fadd_rn(term, __shfl_xor_sync(0xffffffffu, term, o));
+    return term;
+}
+
+// Cost of one trajectory from its distances d[w S + s], in a fixed order: per waypoint,
+// sphere s = lane + 32 m summed by its lane, then a butterfly; the waypoints are added
+// in order (every lane ends with the same value).  Four waypoints' loads at a time.  NC:
+// the distances were written by an earlier launch (read-only path); else by this warp.
+template <bool NC>
+__device__ __forceinline__ float trajectory_cost(const float* d, int W, int S, float rm0, float rm1, uint32_t lane) {
+    float acc = 0.f;
+    for (int w0 = 0; w0 < W; w0 += 4) {
+        float a[4], b[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            a[k] = b[k] = 0.f;
+            const int w = w0 + k;
+            if (w < W) {
+                const float* dw = d + (uint64_t)w * (uint64_t)S;
+                if (lane < (uint32_t)S) a[k] = NC ? __ldg(dw + lane) : dw[lane];
+                if (lane + 32 < (uint32_t)S) b[k] = NC ? __ldg(dw + lane + 32) : dw[lane + 32];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            if (w0 + k >= W) break;
+            acc = __fadd_rn(acc, waypoint_term(a[k], b[k], S, rm0, rm1, lane));
+        }
+    }
+    return acc;
+}
+
+// With COST the block also sums its trajectory's cost once every distance is written:
+// after a block barrier each warp forms the terms of its waypoints (trajectory_cost's
+// per-waypoint arithmetic) into shared memory, and after a second one thread adds them
+// in waypoint order, so the cost is bitwise that of k_clearance_cost.
+template <bool STAGE, bool LISTS, bool COST>
 __global__ void __launch_bounds__(512, 2) k_clearance_dist(DevArgs t, const float* __restrict__ centers, int W,
                                                            int S, float* __restrict__ dist,
-                                                           int32_t* __restrict__ argmin, uint32_t pf_blocks) {
+                                                           int32_t* __restrict__ argmin, uint32_t pf_blocks,
+                                                           const float* __restrict__ radii, float margin,
+                                                           float* __restrict__ cost) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t bar;
     // blocks start in about index order as earlier ones finish, so trajectory
@@ -231,87 +366,37 @@ __global__ void __launch_bounds__(512, 2) k_clearance_dist(DevArgs t, const floa
     const uint32_t s_lo = w_lo * (uint32_t)S, s_hi = w_hi * (uint32_t)S;   // this warp's spheres
     uint32_t n_q = 0;
     for (uint32_t p0 = s_lo; p0 < s_hi; p0 += 128) {
-        const uint64_t i0 = tbase + p0 + 4 * lane;
-        const uint32_t nv = p0 + 4 * lane < s_hi ? min(4u, s_hi - (p0 + 4 * lane)) : 0u;
-        const float* src = centers + 3 * i0;
-        float v[12];
-        if (nv == 4 && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0)) {
-            const float4* q = reinterpret_cast<const float4*>(src);
-            const float4 a = __ldg(q), b = __ldg(q + 1), cc = __ldg(q + 2);
-            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-            v[8] = cc.x; v[9] = cc.y; v[10] = cc.z; v[11] = cc.w;
-        } else {
-#pragma unroll
-            for (int k = 0; k < 12; k++) v[k] = (uint32_t)(k / 3) < nv ? __ldg(src + k) : 0.f;
-        }
-        // farther than r_max from the cloud's box: farther than r_max from every point
-        bool nr[4];
-#pragma unroll
-        for (int k = 0; k < 4; k++)
-            nr[k] = (uint32_t)k < nv && box_dist2(v[3 * k], v[3 * k + 1], v[3 * k + 2], rlo, rhi) <= rmax2;
-        // the common case, four spheres all far: one 16-byte store for each output
-        const bool all_far = nv == 4 && !(nr[0] | nr[1] | nr[2] | nr[3]) &&
-                             ((reinterpret_cast<uintptr_t>(dist + i0) | reinterpret_cast<uintptr_t>(argmin + i0)) &
-                              15u) == 0;
-        if (all_far) {
-            *reinterpret_cast<float4*>(dist + i0) = make_float4(rmax, rmax, rmax, rmax);
-            *reinterpret_cast<int4*>(argmin + i0) = make_int4(-1, -1, -1, -1);
-        }
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const bool near = nr[k];
-            if ((uint32_t)k < nv && !near && !all_far) {
-                dist[i0 + k] = rmax;
-                argmin[i0 + k] = -1;
-            }
-            const uint32_t mask = __ballot_sync(0xffffffffu, near);
-            if (near) {
-                const uint32_t pos = n_q + __popc(mask & lt_mask);
-                ws->nq[pos] = make_float4(v[3 * k], v[3 * k + 1], v[3 * k + 2], 0.f);
-                ws->ni[pos] = i0 + k;
-            }
-            n_q += __popc(mask);
-        }
-        if (n_q >= 32) {
-            __syncwarp();
-            uint32_t r0 = 0;
-            for (; n_q - r0 >= 32; r0 += 32) {
-                if (r0) {
-                    const float4 cc = ws->nq[r0 + lane];
-                    const unsigned long long ii = ws->ni[r0 + lane];
-                    __syncwarp();
-                    ws->nq[lane] = cc;
-                    ws->ni[lane] = ii;
-                    __syncwarp();
-                }
-                clearance_round<LISTS>(t, Ts, ws, 32, 0, rmax, rmax2, dist, argmin, lane, lt_mask);
-            }
-            const uint32_t rest = n_q - r0;
-            float4 cc = make_float4(0.f, 0.f, 0.f, 0.f);
-            unsigned long long ii = 0;
-            if (lane < rest) {
-                cc = ws->nq[r0 + lane];
-                ii = ws->ni[r0 + lane];
-            }
-            __syncwarp();
-            if (lane < rest) {
-                ws->nq[lane] = cc;
-                ws->ni[lane] = ii;
-            }
-            n_q = rest;
-            __syncwarp();
-        }
+        clearance_pass(centers, tbase, p0, s_hi, rlo, rhi, rmax, rmax2, dist, argmin, ws, n_q, lane, lt_mask);
+        if (n_q >= 32) clearance_drain<LISTS>(t, Ts, ws, n_q, rmax, rmax2, dist, argmin, lane, lt_mask);
     }
     if (n_q) {
         __syncwarp();
         clearance_round<LISTS>(t, Ts, ws, n_q, 0, rmax, rmax2, dist, argmin, lane, lt_mask);
     }
+    if constexpr (COST) {
+        float* wterm = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(ws - warp) +
+                                                sizeof(ClearScratch) * (size_t)nw);
+        __syncthreads();   // every distance of the trajectory written and visible to the block
+        float rm0 = 0.f, rm1 = 0.f;
+        if (lane < (uint32_t)S) rm0 = __fadd_rn(radii[lane], margin);
+        if (lane + 32 < (uint32_t)S) rm1 = __fadd_rn(radii[lane + 32], margin);
+        for (uint32_t w = w_lo; w < w_hi; w++) {
+            const float* dw = dist + tbase + (uint64_t)w * (uint64_t)S;
+            const float term = waypoint_term(lane < (uint32_t)S ? dw[lane] : 0.f,
+                                             lane + 32 < (uint32_t)S ? dw[lane + 32] : 0.f, S, rm0, rm1, lane);
+            if (lane == 0) wterm[w] = term;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float acc = 0.f;
+            for (int w = 0; w < W; w++) acc = __fadd_rn(acc, wterm[w]);
+            cost[traj] = acc;
+        }
+    }
 }
 
-// Cost per trajectory from the written distances, one warp per trajectory, in a fixed
-// order: per waypoint, sphere s = lane + 32 m summed by its lane, then a butterfly; lane 0
-// adds the waypoints in order.  The result does not depend on the launch configuration.
+// Cost per trajectory from the written distances, one warp per trajectory, in the order
+// of trajectory_cost.  The result does not depend on the launch configuration.
 __global__ void k_clearance_cost(const float* __restrict__ radii, const float* __restrict__ dist, uint64_t T, int W,
                                  int S, float margin, float* __restrict__ cost) {
     const uint32_t lane = lane_id();
@@ -320,23 +405,8 @@ __global__ void k_clearance_cost(const float* __restrict__ radii, const float* _
     if (lane < (uint32_t)S) rm0 = __fadd_rn(radii[lane], margin);
     if (lane + 32 < (uint32_t)S) rm1 = __fadd_rn(radii[lane + 32], margin);
     for (uint64_t traj = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); traj < T; traj += nwarps) {
-        const float* d = dist + traj * (uint64_t)W * (uint64_t)S;
-        float acc = 0.f;
-        for (int w = 0; w < W; w++) {
-            float term = 0.f;
-            if (lane < (uint32_t)S) {
-                const float hh = fmaxf(0.f, __fsub_rn(rm0, __ldg(d + (uint64_t)w * S + lane)));
-                term = __fadd_rn(term, __fmul_rn(hh, hh));
-            }
-            if (lane + 32 < (uint32_t)S) {
-                const float hh = fmaxf(0.f, __fsub_rn(rm1, __ldg(d + (uint64_t)w * S + lane + 32)));
-                term = __fadd_rn(term, __fmul_rn(hh, hh));
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) term = __fadd_rn(term, __shfl_xor_sync(0xffffffffu, term, o));
-            acc = __fadd_rn(acc, term);
-        }
-        if (lane == 0) cost[traj] = acc;
+        const float c = trajectory_cost<true>(dist + traj * (uint64_t)W * (uint64_t)S, W, S, rm0, rm1, lane);
+        if (lane == 0) cost[traj] = c;
     }
 }
 
@@ -433,6 +503,9 @@ int launch_count_clearance(const DevArgs& t, const float* centers, uint64_t m, b
     return CAPT_OK;
 }
 
+// Trajectories of at most this many waypoints get their cost in the distance kernel.
+constexpr int kFusedCostMaxW = 1024;
+
 int launch_clearance_fwd(const DevArgs& t, const float* centers, const float* radii, uint64_t T, int W, int S,
                          float margin, float* cost, float* dist, int32_t* argmin, const capt_launch_cfg& cfg,
                          cudaStream_t st, std::string& err) {
@@ -441,10 +514,16 @@ int launch_clearance_fwd(const DevArgs& t, const float* centers, const float* ra
     if (T > 0x7fffffffull) { err = "too many trajectories for one launch"; return CAPT_E_ARG; }
     const bool stage = cfg.staging == CAPT_STAGE_SMEM && t.stage_floats > 0;
     const bool lists = cfg.grid && t.nl_cell;
-    auto fn = stage ? (lists ? k_clearance_dist<true, true> : k_clearance_dist<true, false>)
-                    : (lists ? k_clearance_dist<false, true> : k_clearance_dist<false, false>);
+    const bool fused = W <= kFusedCostMaxW;
+    using Fn = void (*)(DevArgs, const float*, int, int, float*, int32_t*, uint32_t, const float*, float, float*);
+    static const Fn table[8] = {k_clearance_dist<false, false, false>, k_clearance_dist<false, false, true>,
+                                k_clearance_dist<false, true, false>,  k_clearance_dist<false, true, true>,
+                                k_clearance_dist<true, false, false>,  k_clearance_dist<true, false, true>,
+                                k_clearance_dist<true, true, false>,   k_clearance_dist<true, true, true>};
+    const Fn fn = table[(stage ? 4 : 0) + (lists ? 2 : 0) + (fused ? 1 : 0)];
     const int warps = std::max(1, std::min(16, std::min((int)cfg.warps_per_block, W)));
-    const size_t smem = (stage ? stage_offset(t) : 0u) + sizeof(ClearScratch) * (size_t)warps;
+    const size_t smem = (stage ? stage_offset(t) : 0u) + sizeof(ClearScratch) * (size_t)warps +
+                        (fused ? 4 * (size_t)W : 0u);
     cudaError_t ce = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (ce != cudaSuccess) { err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
     uint32_t pf_blocks = 0;
@@ -453,9 +532,11 @@ int launch_clearance_fwd(const DevArgs& t, const float* centers, const float* ra
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)fn, warps * 32, smem);
         pf_blocks = (uint32_t)std::max(1, occ) * (uint32_t)sm_count() * (uint32_t)cfg.prefetch;
     }
-    fn<<<(unsigned)T, warps * 32, smem, st>>>(t, centers, W, S, dist, argmin, pf_blocks);
-    const uint64_t cost_blocks = std::min<uint64_t>((T + 7) / 8, (uint64_t)sm_count() * 16);
-    k_clearance_cost<<<(unsigned)cost_blocks, 256, 0, st>>>(radii, dist, T, W, S, margin, cost);
+    fn<<<(unsigned)T, warps * 32, smem, st>>>(t, centers, W, S, dist, argmin, pf_blocks, radii, margin, cost);
+    if (!fused) {
+        const uint64_t cost_blocks = std::min<uint64_t>((T + 7) / 8, (uint64_t)sm_count() * 16);
+        k_clearance_cost<<<(unsigned)cost_blocks, 256, 0, st>>>(radii, dist, T, W, S, margin, cost);
+    }
     ce = cudaGetLastError();
     if (ce != cudaSuccess) { err = std::string("clearance launch: ") + cudaGetErrorString(ce); return CAPT_E_CUDA; }
     return CAPT_OK;

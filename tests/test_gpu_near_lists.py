@@ -248,3 +248,44 @@ def test_lists_full_size(scene, orc, capt_lib, torch_):
     a, b = _both(capt_lib, torch_, t, cen, scene["arm"].sphere_radius)
     _equal(a, b)
     _check_oracle(orc, scene["pts"], cen, b[1], b[2], 0.08, n=30000, seed=4)
+
+
+def _cost_fixed_order(d, r, margin):
+    """The cost's fixed FP32 order, in numpy: per waypoint, lane l forms
+    (0 + h(l)^2) + h(l + 32)^2 (absent spheres add nothing), the 32 lane terms meet in a
+    butterfly (xor 16, 8, 4, 2, 1), and the waypoints are added in order."""
+    f = np.float32
+    T, Wn, S = d.shape
+    rm = (r.astype(np.float32) + f(margin)).astype(np.float32)
+    h = np.maximum(f(0), (rm[None, None, :] - d).astype(np.float32))
+    sq = (h * h).astype(np.float32)
+    lanes = np.zeros((T, Wn, 32), np.float32)
+    lanes[..., :min(S, 32)] = (f(0) + sq[..., :min(S, 32)]).astype(np.float32)
+    if S > 32:
+        lanes[..., :S - 32] = (lanes[..., :S - 32] + sq[..., 32:]).astype(np.float32)
+    for o in (16, 8, 4, 2, 1):
+        lanes = (lanes + lanes[..., np.arange(32) ^ o]).astype(np.float32)
+    acc = np.zeros(T, np.float32)
+    for w in range(Wn):
+        acc = (acc + lanes[:, w, 0]).astype(np.float32)
+    return acc
+
+
+@pytest.mark.parametrize("Wn,S", [(32, 60), (7, 33), (1024, 5), (1100, 5)])
+def test_cost_is_the_fixed_order_sum(scene, capt_lib, torch_, Wn, S):
+    """The trajectory cost is the fixed-order FP32 sum of its hinge terms, bit for bit,
+    whether the distance kernel sums it (W <= 1024) or the separate cost kernel does,
+    on both paths."""
+    t = _tree(capt_lib, scene["pts"])
+    capt_lib.capt_build_grid(t, 1 << 20)
+    capt_lib.capt_build_near_lists(t)
+    rng = np.random.default_rng(Wn + S)
+    T = max(3, 4096 // Wn)
+    pts = scene["pts"]
+    cen = (pts[rng.integers(0, len(pts), (T, Wn, S))] + rng.normal(0, 0.04, (T, Wn, S, 3))).astype(np.float32)
+    r = rng.uniform(0.02, 0.08, S).astype(np.float32)
+    a, b = _both(capt_lib, torch_, t, cen, r, margin=0.01)
+    _equal(a, b)
+    want = _cost_fixed_order(b[1].reshape(T, Wn, S), r, 0.01)
+    assert np.array_equal(b[0].view(np.uint32), want.view(np.uint32))
+    assert (want > 0).mean() > 0.5
