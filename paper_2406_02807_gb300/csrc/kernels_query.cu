@@ -301,6 +301,7 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs(DevArgs t, cons
     const uint32_t lt_mask = (1u << lane) - 1u;
     const float4 rlo = make_float4(t.lo[0], t.lo[1], t.lo[2], 0.f);
     const float4 rhi = make_float4(t.hi[0], t.hi[1], t.hi[2], 0.f);
+    const BoxPairs bp(rlo, rhi, t.nzero);
     const uint32_t inv_s = (1u << 20) / (uint32_t)S + 1u;   // i / S = (i * inv_s) >> 20 for i < 4096
     const bool s4 = (S & 3) == 0;
 
@@ -361,10 +362,12 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs(DevArgs t, cons
                 const float4 q2 = reinterpret_cast<const float4*>(r2s)[sidx >> 2];
                 const float r2k[4] = {q2.x, q2.y, q2.z, q2.w};
                 const bool open = nv > 0 && !((resolved >> (g & 31u)) & 1u);
+                float bd2[4];
+                box_dist2_x4(v, bp, bd2);
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
                     const float x = v[3 * k], y = v[3 * k + 1], z = v[3 * k + 2];
-                    const bool near = open && (uint32_t)k < nv && box_dist2(x, y, z, rlo, rhi) <= r2k[k];
+                    const bool near = open && (uint32_t)k < nv && bd2[k] <= r2k[k];
                     const uint32_t mask = __ballot_sync(0xffffffffu, near);
                     if (near) {
                         const uint32_t pos = n_near + __popc(mask & lt_mask);
@@ -479,6 +482,7 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs_grid(DevArgs t,
     const uint32_t lt_mask = (1u << lane) - 1u;
     const float4 rlo = make_float4(t.lo[0], t.lo[1], t.lo[2], 0.f);
     const float4 rhi = make_float4(t.hi[0], t.hi[1], t.hi[2], 0.f);
+    const BoxPairs bp(rlo, rhi, t.nzero);
     const uint32_t inv_s = (1u << 20) / (uint32_t)S + 1u;   // i / S = (i * inv_s) >> 20 for i < 4096
     const bool s4 = (S & 3) == 0;
 
@@ -609,10 +613,12 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs_grid(DevArgs t,
                 const float r2k[4] = {q2.x, q2.y, q2.z, q2.w};
                 const float rk[4] = {qr.x, qr.y, qr.z, qr.w};
                 const bool open = nv > 0 && !((resolved >> (g & 31u)) & 1u);
+                float bd2[4];
+                box_dist2_x4(v, bp, bd2);
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
                     const float x = v[3 * k], y = v[3 * k + 1], z = v[3 * k + 2];
-                    const bool near = open && (uint32_t)k < nv && box_dist2(x, y, z, rlo, rhi) <= r2k[k];
+                    const bool near = open && (uint32_t)k < nv && bd2[k] <= r2k[k];
                     const uint32_t mask = __ballot_sync(0xffffffffu, near);
                     if (near) {
                         const uint32_t pos = n1 + __popc(mask & lt_mask);

@@ -70,6 +70,57 @@ __device__ __forceinline__ void block_d2(const float4* __restrict__ blocks, uint
     s23 = f2_add(f2_add(f2_mulz(x23, x23, z), f2_mulz(y23, y23, z)), f2_mulz(z23, z23, z));
 }
 
+// max(a, b, c), NaN if any input is NaN (one instruction on sm_100 and later).
+__device__ __forceinline__ float max3_nan(float a, float b, float c) {
+    float d;
+    asm("max.NaN.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// The bounds of a box arranged for the interleaved coordinates of four consecutive
+// centres, loaded as three float4 {x0 y0 z0 x1} {y1 z1 x2 y2} {z2 x3 y3 z3}: as register
+// pairs these are (x, y), (z, x), (y, z) twice, so the box's lower and upper corners
+// come in those three orders.
+struct BoxPairs {
+    uint64_t lxy, lzx, lyz, hxy, hzx, hyz, z;   // z: f2_dup(t.nzero)
+    __device__ __forceinline__ BoxPairs(const float4& lo, const float4& hi, float nzero) {
+        asm("mov.b64 %0, {%1, %2};" : "=l"(lxy) : "f"(lo.x), "f"(lo.y));
+        asm("mov.b64 %0, {%1, %2};" : "=l"(lzx) : "f"(lo.z), "f"(lo.x));
+        asm("mov.b64 %0, {%1, %2};" : "=l"(lyz) : "f"(lo.y), "f"(lo.z));
+        asm("mov.b64 %0, {%1, %2};" : "=l"(hxy) : "f"(hi.x), "f"(hi.y));
+        asm("mov.b64 %0, {%1, %2};" : "=l"(hzx) : "f"(hi.z), "f"(hi.x));
+        asm("mov.b64 %0, {%1, %2};" : "=l"(hyz) : "f"(hi.y), "f"(hi.z));
+        z = f2_dup(nzero);
+    }
+};
+
+// Squared gaps of one coordinate pair to the box: per element max(lo - x, x - hi, 0)
+// (the magnitude of x - clamp(x, lo, hi), the same bits once squared; NaN stays NaN),
+// squared exactly.
+__device__ __forceinline__ float2 box_gap2(float x0, float x1, uint64_t lo, uint64_t hi, uint64_t z) {
+    uint64_t x;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(x0), "f"(x1));
+    const float2 a = f2_split(f2_sub(lo, x)), b = f2_split(f2_sub(x, hi));
+    uint64_t g;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(g) : "f"(max3_nan(a.x, b.x, 0.f)), "f"(max3_nan(a.y, b.y, 0.f)));
+    return f2_split(f2_mulz(g, g, z));
+}
+
+// box_dist2 of four consecutive centres v[0..11] (x0 y0 z0 x1 y1 z1 ...), bit for bit:
+// ((gx^2 + gy^2) + gz^2) per centre, the differences and squares two at a time.
+__device__ __forceinline__ void box_dist2_x4(const float v[12], const BoxPairs& bp, float d2[4]) {
+    const float2 p0 = box_gap2(v[0], v[1], bp.lxy, bp.hxy, bp.z);    // x0 y0
+    const float2 p1 = box_gap2(v[2], v[3], bp.lzx, bp.hzx, bp.z);    // z0 x1
+    const float2 p2 = box_gap2(v[4], v[5], bp.lyz, bp.hyz, bp.z);    // y1 z1
+    const float2 p3 = box_gap2(v[6], v[7], bp.lxy, bp.hxy, bp.z);    // x2 y2
+    const float2 p4 = box_gap2(v[8], v[9], bp.lzx, bp.hzx, bp.z);    // z2 x3
+    const float2 p5 = box_gap2(v[10], v[11], bp.lyz, bp.hyz, bp.z);  // y3 z3
+    d2[0] = __fadd_rn(__fadd_rn(p0.x, p0.y), p1.x);
+    d2[1] = __fadd_rn(__fadd_rn(p1.y, p2.x), p2.y);
+    d2[2] = __fadd_rn(__fadd_rn(p3.x, p3.y), p4.x);
+    d2[3] = __fadd_rn(__fadd_rn(p4.y, p5.x), p5.y);
+}
+
 // Per-warp storage of one round.
 struct RoundEntries {
     float4 c[32];       // entry: centre and r^2
