@@ -344,7 +344,9 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs(DevArgs t, cons
             const uint32_t i0 = p0 + 4 * lane;
             const uint32_t nv = i0 < nsph ? min(4u, nsph - i0) : 0u;
             float v[12];
-            if (vec && nv == 4) {
+            // every lane with four aligned centres (all passes but a tile's ragged last):
+            // a warp-uniform branch, so the per-element path costs the others nothing
+            if (__all_sync(0xffffffffu, vec && nv == 4)) {
                 const float4* q = reinterpret_cast<const float4*>(base + 3 * (size_t)i0);
                 const float4 a = __ldg(q), b = __ldg(q + 1), cc = __ldg(q + 2);
                 v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
@@ -364,17 +366,23 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs(DevArgs t, cons
                 const bool open = nv > 0 && !((resolved >> (g & 31u)) & 1u);
                 float bd2[4];
                 box_dist2_x4(v, bp, bd2);
+                bool nk[4];
 #pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    const float x = v[3 * k], y = v[3 * k + 1], z = v[3 * k + 2];
-                    const bool near = open && (uint32_t)k < nv && bd2[k] <= r2k[k];
-                    const uint32_t mask = __ballot_sync(0xffffffffu, near);
-                    if (near) {
-                        const uint32_t pos = n_near + __popc(mask & lt_mask);
-                        ws->nc[pos] = make_float4(x, y, z, r2k[k]);
-                        ws->ng[pos] = g;
+                for (int k = 0; k < 4; k++) nk[k] = open && (uint32_t)k < nv && bd2[k] <= r2k[k];
+                // most passes have no sphere near the cloud's box at all: one vote skips
+                // the four queue appends
+                if (__any_sync(0xffffffffu, nk[0] | nk[1] | nk[2] | nk[3])) {
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        const bool near = nk[k];
+                        const uint32_t mask = __ballot_sync(0xffffffffu, near);
+                        if (near) {
+                            const uint32_t pos = n_near + __popc(mask & lt_mask);
+                            ws->nc[pos] = make_float4(v[3 * k], v[3 * k + 1], v[3 * k + 2], r2k[k]);
+                            ws->ng[pos] = g;
+                        }
+                        n_near += __popc(mask);
                     }
-                    n_near += __popc(mask);
                 }
             } else {
 #pragma unroll
@@ -595,7 +603,9 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs_grid(DevArgs t,
             const uint32_t i0 = p0 + 4 * lane;
             const uint32_t nv = i0 < nsph ? min(4u, nsph - i0) : 0u;
             float v[12];
-            if (vec && nv == 4) {
+            // every lane with four aligned centres (all passes but a tile's ragged last):
+            // a warp-uniform branch, so the per-element path costs the others nothing
+            if (__all_sync(0xffffffffu, vec && nv == 4)) {
                 const float4* q = reinterpret_cast<const float4*>(base + 3 * (size_t)i0);
                 const float4 a = __ldg(q), b = __ldg(q + 1), cc = __ldg(q + 2);
                 v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
@@ -615,17 +625,23 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs_grid(DevArgs t,
                 const bool open = nv > 0 && !((resolved >> (g & 31u)) & 1u);
                 float bd2[4];
                 box_dist2_x4(v, bp, bd2);
+                bool nk[4];
 #pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    const float x = v[3 * k], y = v[3 * k + 1], z = v[3 * k + 2];
-                    const bool near = open && (uint32_t)k < nv && bd2[k] <= r2k[k];
-                    const uint32_t mask = __ballot_sync(0xffffffffu, near);
-                    if (near) {
-                        const uint32_t pos = n1 + __popc(mask & lt_mask);
-                        ws->nc[pos] = make_float4(x, y, z, rk[k]);
-                        ws->ng[pos] = (uint8_t)g;
+                for (int k = 0; k < 4; k++) nk[k] = open && (uint32_t)k < nv && bd2[k] <= r2k[k];
+                // most passes have no sphere near the cloud's box at all: one vote skips
+                // the four queue appends
+                if (__any_sync(0xffffffffu, nk[0] | nk[1] | nk[2] | nk[3])) {
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        const bool near = nk[k];
+                        const uint32_t mask = __ballot_sync(0xffffffffu, near);
+                        if (near) {
+                            const uint32_t pos = n1 + __popc(mask & lt_mask);
+                            ws->nc[pos] = make_float4(v[3 * k], v[3 * k + 1], v[3 * k + 2], rk[k]);
+                            ws->ng[pos] = (uint8_t)g;
+                        }
+                        n1 += __popc(mask);
                     }
-                    n1 += __popc(mask);
                 }
             } else {
 #pragma unroll
