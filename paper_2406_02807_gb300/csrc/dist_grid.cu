@@ -286,30 +286,54 @@ __global__ void __launch_bounds__(kNearThreads) k_near_lists(DevArgs t, GridShap
             __syncwarp();
             uint32_t n = 0;
             if (!over) {
-                // their points within R_C of m, leaf by leaf
+                // their points within R_C of m, leaf by leaf: the set's 32-slot chunks
+                // are tested by their boxes first (one chunk per lane; a box holds its
+                // points, so a chunk whose box is farther than R_C has none), then the
+                // slots of the chunks that pass, in slot order
                 for (uint32_t k = 0; k < nl; k++) {
                     if (lane == 0) s.seg[k] = n;
                     float4 a, b;
                     load_leaf(t.leaves, s.leaf[k], a, b);
                     const uint32_t b0 = __float_as_uint(a.w), cnt = __float_as_uint(b.w);
-                    for (uint32_t j0 = 0; j0 < cnt; j0 += 32) {
-                        const uint32_t j = j0 + lane;
-                        bool in = false;
-                        uint32_t id = 0;
-                        if (j < cnt) {
-                            const float* p = t.blocks + 4ull * b0 + j;
-                            float l0, h0, l1, h1, l2, h2;
-                            abs_diff_bounds(m[0], __ldg(p), l0, h0);
-                            abs_diff_bounds(m[1], __ldg(p + pl), l1, h1);
-                            abs_diff_bounds(m[2], __ldg(p + 2 * pl), l2, h2);
-                            const float lo2 = __fadd_rd(__fadd_rd(__fmul_rd(l0, l0), __fmul_rd(l1, l1)), __fmul_rd(l2, l2));
-                            in = lo2 <= R2;
-                            id = __ldg(t.ids + 4ull * b0 + j);
+                    if (cnt == 0) continue;
+                    const uint64_t s_lo = 4ull * b0, s_hi = s_lo + cnt;   // the set's slots
+                    const uint64_t c_lo = b0 / kChunkBlocks, c_hi = (b0 + (cnt + 3u) / 4u - 1u) / kChunkBlocks;
+                    for (uint64_t c0 = c_lo; c0 <= c_hi; c0 += 32) {
+                        bool reach = false;
+                        if (c0 + lane <= c_hi) {
+                            const float4* cb = reinterpret_cast<const float4*>(t.cbox) + 2 * (c0 + lane);
+                            const float4 lo = __ldg(cb), hi = __ldg(cb + 1);
+                            float g2 = 0.f;
+                            const float lv[3] = {lo.x, lo.y, lo.z}, hv[3] = {hi.x, hi.y, hi.z};
+#pragma unroll
+                            for (int d = 0; d < 3; d++) {
+                                const float gd = fmaxf(fmaxf(__fsub_rd(lv[d], m[d]), __fsub_rd(m[d], hv[d])), 0.f);
+                                g2 = __fadd_rd(g2, __fmul_rd(gd, gd));
+                            }
+                            reach = g2 <= R2;
                         }
-                        const uint32_t mask = __ballot_sync(0xffffffffu, in);
-                        const uint32_t pos = n + __popc(mask & lt);
-                        if (in && pos < kNearMaxCand) s.cand[pos] = id;
-                        n += __popc(mask);
+                        uint32_t pm = __ballot_sync(0xffffffffu, reach);
+                        while (pm) {
+                            const uint64_t slot = 32ull * (c0 + (uint32_t)(__ffs(pm) - 1)) + lane;
+                            pm &= pm - 1u;
+                            bool in = false;
+                            uint32_t id = 0;
+                            if (slot >= s_lo && slot < s_hi) {
+                                const float* p = t.blocks + slot;
+                                float l0, h0, l1, h1, l2, h2;
+                                abs_diff_bounds(m[0], __ldg(p), l0, h0);
+                                abs_diff_bounds(m[1], __ldg(p + pl), l1, h1);
+                                abs_diff_bounds(m[2], __ldg(p + 2 * pl), l2, h2);
+                                const float lo2 =
+                                    __fadd_rd(__fadd_rd(__fmul_rd(l0, l0), __fmul_rd(l1, l1)), __fmul_rd(l2, l2));
+                                in = lo2 <= R2;
+                                id = __ldg(t.ids + slot);
+                            }
+                            const uint32_t mask = __ballot_sync(0xffffffffu, in);
+                            const uint32_t pos = n + __popc(mask & lt);
+                            if (in && pos < kNearMaxCand) s.cand[pos] = id;
+                            n += __popc(mask);
+                        }
                     }
                 }
                 if (lane == 0) s.seg[nl] = n;
