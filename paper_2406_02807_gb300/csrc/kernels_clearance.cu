@@ -5,21 +5,24 @@
 // cloud point whenever it is within r_max.  The forward pass therefore scans the whole
 // set (no early exit), keeping the minimum FP32 squared distance and its slot.
 //
-// Forward, two kernels:
+// Forward:
 //  1. Distances (k_clearance_dist): one block per trajectory, each warp owning a
 //     contiguous range of its waypoints (close in space, so the block's warps share set
 //     blocks in L1); passes of 128 consecutive spheres (4 per lane, three 16-byte
 //     loads): a sphere farther than r_max from the cloud's bounding box is farther than
 //     r_max from every point, so it gets d = r_max, argmin = -1 at once (one 16-byte
 //     store per output when all four of a lane's spheres are that far); the others are
-//     queued.  No block barrier: a warp leaves as soon as its range is done.  Rounds
-//     of 32 queued spheres: descent and leaf box test against r_max; each set of a
-//     sphere that passes is scanned in full by the whole warp in packed FP32x2
-//     arithmetic, every lane keeping a running minimum of (d^2, slot) keys, reduced by
-//     two warp-wide 32-bit minimum reductions per set.
-//  2. Costs (k_clearance_cost): one warp per trajectory sums each waypoint's terms in a
-//     fixed order (lane-strided, then a butterfly) and adds the waypoints in order, so
-//     the cost is bitwise reproducible whatever the launch configuration.
+//     queued.  Rounds of 32 queued spheres: descent and leaf box test against r_max;
+//     each set of a sphere that passes is scanned in full by the whole warp in packed
+//     FP32x2 arithmetic, every lane keeping a running minimum of (d^2, slot) keys,
+//     reduced by two warp-wide 32-bit minimum reductions per set.  With the tree's
+//     nearest-candidate lists (LISTS) a queued sphere first looks up its grid cell's
+//     list and only the spheres of fallback cells take the descent and the set scan.
+//  2. Costs, in a fixed order (lane-strided over the spheres, a butterfly, then the
+//     waypoints in order), so the cost is bitwise reproducible whatever the launch
+//     configuration: summed by the distance kernel's block after a block barrier (COST,
+//     trajectories of at most kFusedCostMaxW waypoints), else by k_clearance_cost, one
+//     warp per trajectory.
 // Backward: elementwise, one thread per sphere, from the saved distance and argmin.
 #include <algorithm>
 
