@@ -42,7 +42,7 @@ R_MIN, R_MAX, R_FILTER = 0.02, 0.08, 0.01
 SM_MAX_MHZ = 2070.0
 # DRAM bytes (read + write) per launch of the configuration-query kernel from an ncu
 # capture, keyed by the hash of the kernel source it was taken on (null when stale).
-TRAFFIC = {"dec607f970aa69c1": 848848640 + 4063232}   # k_configs_grid<32, 0>, tabletop, 1M configurations
+TRAFFIC = {"87fc78282cd4552d": 805148672 + 4087296}   # k_configs_grid<32, 0>, tabletop, 1M configurations
 HBM_FALLBACK_GBS = 6800.0   # used only when MEASURED_PEAKS.json is absent
 PARITY_SAMPLE = 32768       # configurations of the timed run checked against the oracle
 GRID_CELLS = 1 << 24        # cells of the distance-bound grid of the tabletop tree (32 MB)

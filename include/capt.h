@@ -380,14 +380,13 @@ typedef struct capt_launch_cfg {
     int32_t chunk;             /* edges: configurations per work item (1..1024, rounded
                                   up to a multiple of 32).  Spheres and configurations:
                                   the affordance scan, CAPT_SCAN_* */
-    int32_t prefetch;          /* configurations: 0..CAPT_MAX_PREFETCH.  With k > 0 a warp
-                                  asks the copy engine to bring the centres k passes (of
-                                  128 spheres) ahead of the pass it tests into L2
-                                  (cp.async.bulk.prefetch), and at the start of a tile the
-                                  first k passes of the tile some warp takes about one
-                                  tile-time later, so the loads of the root box test hit
-                                  L2.  Clearance: a trajectory k x (resident blocks) ahead
-                                  per block.  0 = none.  Other kernels: must be 0. */
+    int32_t prefetch;          /* configurations: 0..CAPT_MAX_PREFETCH.  With k > 0 every
+                                  lane asks L2 for its centres of the pass (of 128
+                                  spheres) k passes ahead of the one it tests
+                                  (prefetch.global.L2), so the loads of the root box test
+                                  find them there.  Clearance: a trajectory k x (resident
+                                  blocks) ahead per block (cp.async.bulk.prefetch).
+                                  0 = none.  Other kernels: must be 0. */
     int32_t grid;              /* sphere, configuration, edge and joint-angle queries:
                                   1 = classify each sphere that reaches the cloud's
                                   bounding box by the tree's distance-bound grid

@@ -202,6 +202,11 @@ __device__ __forceinline__ void prefetch_l2(const void* p, uint64_t bytes) {
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(e - a)) : "memory");
 }
 
+// Ask L2 for the line holding p (a hint: no data returned, no fault).
+__device__ __forceinline__ void prefetch_l2_line(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p) : "memory");
+}
+
 // Distance-bound grid (dist_grid.cu): 0 when the grid proves that the sphere (x, r)
 // misses every cloud point under the FP32 test, 1 when it proves that it hits one, 2
 // when it cannot tell.

@@ -320,12 +320,6 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs(DevArgs t, cons
          tile = sched.next(tile)) {
         const uint64_t first = tile * CPT;
         const uint32_t ncfg = (uint32_t)min((uint64_t)CPT, C - first);
-        if (pf && lane == 0 && tile + nwarps < n_tiles) {
-            // the first pf passes of the tile some warp takes about one tile-time from now
-            const uint64_t pfirst = (tile + nwarps) * CPT;
-            const uint64_t pn = min((uint64_t)CPT, C - pfirst) * (uint64_t)S;
-            prefetch_l2(centers + 3 * pfirst * (uint64_t)S, min(pn, (uint64_t)128u * pf) * 12u);
-        }
         const uint32_t nsph = ncfg * (uint32_t)S;
         const float* base = centers + 3 * first * (uint64_t)S;
         const bool vec = (reinterpret_cast<uintptr_t>(base) & 15u) == 0;
@@ -337,11 +331,12 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs(DevArgs t, cons
         const uint32_t all_cfg = ncfg >= 32u ? 0xffffffffu : ((1u << ncfg) - 1u);
         uint32_t n_near = 0;
         for (uint32_t p0 = 0; p0 < nsph; p0 += 128) {
-            // the pass pf passes ahead in this tile, into L2 while this one is tested
-            if (pf && lane == 0 && p0 + 128 * pf < nsph)
-                prefetch_l2(base + 3 * (size_t)(p0 + 128 * pf), (uint64_t)min(128u, nsph - (p0 + 128 * pf)) * 12u);
             // ---- root box test of 4 consecutive spheres per lane ----
             const uint32_t i0 = p0 + 4 * lane;
+            // the lane's centres pf passes ahead in this tile, asked of L2 while this pass
+            // is tested (each lane's 48 bytes start in a different 128-byte line or share
+            // one with a neighbour, so the lanes together cover the whole pass)
+            if (pf && i0 + 128 * pf < nsph) prefetch_l2_line(base + 3 * (size_t)(i0 + 128 * pf));
             const uint32_t nv = i0 < nsph ? min(4u, nsph - i0) : 0u;
             float v[12];
             // every lane with four aligned centres (all passes but a tile's ragged last):
@@ -581,12 +576,6 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs_grid(DevArgs t,
          tile = sched.next(tile)) {
         first = tile * CPT;
         ncfg = (uint32_t)min((uint64_t)CPT, C - first);
-        if (pf && lane == 0 && tile + nwarps < n_tiles) {
-            // the first pf passes of the tile some warp takes about one tile-time from now
-            const uint64_t pfirst = (tile + nwarps) * CPT;
-            const uint64_t pn = min((uint64_t)CPT, C - pfirst) * (uint64_t)S;
-            prefetch_l2(centers + 3 * pfirst * (uint64_t)S, min(pn, (uint64_t)128u * pf) * 12u);
-        }
         const uint32_t nsph = ncfg * (uint32_t)S;
         const float* base = centers + 3 * first * (uint64_t)S;
         const bool vec = (reinterpret_cast<uintptr_t>(base) & 15u) == 0;
@@ -596,11 +585,12 @@ __global__ void __launch_bounds__(512, CFG_MIN_BLOCKS) k_configs_grid(DevArgs t,
         const uint32_t all_cfg = ncfg >= 32u ? 0xffffffffu : ((1u << ncfg) - 1u);
         n1 = 0;
         for (uint32_t p0 = 0; p0 < nsph; p0 += 128) {
-            // the pass pf passes ahead in this tile, into L2 while this one is tested
-            if (pf && lane == 0 && p0 + 128 * pf < nsph)
-                prefetch_l2(base + 3 * (size_t)(p0 + 128 * pf), (uint64_t)min(128u, nsph - (p0 + 128 * pf)) * 12u);
             // ---- root box test of 4 consecutive spheres per lane ----
             const uint32_t i0 = p0 + 4 * lane;
+            // the lane's centres pf passes ahead in this tile, asked of L2 while this pass
+            // is tested (each lane's 48 bytes start in a different 128-byte line or share
+            // one with a neighbour, so the lanes together cover the whole pass)
+            if (pf && i0 + 128 * pf < nsph) prefetch_l2_line(base + 3 * (size_t)(i0 + 128 * pf));
             const uint32_t nv = i0 < nsph ? min(4u, nsph - i0) : 0u;
             float v[12];
             // every lane with four aligned centres (all passes but a tile's ragged last):
