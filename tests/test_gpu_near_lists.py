@@ -289,3 +289,24 @@ def test_cost_is_the_fixed_order_sum(scene, capt_lib, torch_, Wn, S):
     want = _cost_fixed_order(b[1].reshape(T, Wn, S), r, 0.01)
     assert np.array_equal(b[0].view(np.uint32), want.view(np.uint32))
     assert (want > 0).mean() > 0.5
+
+
+def test_lists_on_a_device_built_tree(scene, capt_lib, torch_):
+    """The lists of a tree built on the device (capt_build_device) are those of the host
+    build of the same points, so the two trees' clearance outputs are equal, and equal
+    to the leaf-set path."""
+    pts = scene["pts"]
+    th = _tree(capt_lib, pts)
+    td = capt_lib.capt_build_device(_cuda(torch_, pts), 0.0, 0.08)
+    for t in (th, td):
+        capt_lib.capt_build_grid(t, 1 << 20)
+        capt_lib.capt_build_near_lists(t)
+    sh, sd = capt_lib.capt_stats(th), capt_lib.capt_stats(td)
+    assert sh["near_entries"] == sd["near_entries"] and sh["near_fallback_cells"] == sd["near_fallback_cells"]
+    q = W.random_trajectories(256, 32, 1006)
+    cen = W.fk_centers(scene["arm"], q.reshape(-1, 7)).reshape(256, 32, 60, 3)
+    r = scene["arm"].sphere_radius
+    a, b = _both(capt_lib, torch_, td, cen, r)
+    _equal(a, b)
+    _, bh = _both(capt_lib, torch_, th, cen, r)
+    _equal(b, bh)
