@@ -251,3 +251,21 @@ def test_binding_structs_match_the_c_header(capt_lib, tmp_path):
         assert int(got[cname]) == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, f"{cname}.{f}"
+
+
+def test_near_lists_and_clearance_autotuner_reject_bad_state_without_gpu(capt_lib):
+    """capt_build_near_lists and capt_autotune_clearance check the tree and their
+    arguments on the host before any CUDA call."""
+    t = capt_lib.capt_build(W.uniform_cloud(50, 3), 0.0, 0.08)
+    L = capt_lib._load()
+    assert L.capt_build_near_lists(t.h, None) == -8               # not uploaded
+    assert L.capt_build_near_lists(None, None) == -1
+    cfg, ms = capt_lib._LaunchCfg(), ctypes.c_float()
+    assert L.capt_autotune_clearance(t.h, None, None, 1, 1, 1, 0.01, None, None, None, None,
+                                     ctypes.byref(cfg), ctypes.byref(ms)) == -8
+    assert L.capt_autotune_clearance(None, None, None, 1, 1, 1, 0.01, None, None, None, None,
+                                     ctypes.byref(cfg), ctypes.byref(ms)) == -1
+    st = capt_lib.capt_stats(t)
+    assert st["near_entries"] == st["near_bytes"] == st["near_fallback_cells"] == 0
+    # the clearance launch defaults to the lists (used once they exist)
+    assert capt_lib.capt_get_launch_cfg(t, capt_lib.CAPT_KERNEL_CLEARANCE)["grid"] == 1
